@@ -1,0 +1,221 @@
+/*
+ * fhe.h -- C ABI of the GB300 (sm_103a) RNS-CKKS hybrid key-switching library.
+ *
+ * The library implements the key-switching hot path studied in "Theodosian:
+ * A Deep Dive into Memory-Hierarchy-Centric FHE Acceleration" (arXiv
+ * 2512.18345): INTT -> ModUp BConv -> NTT -> key inner product -> INTT ->
+ * ModDown BConv -> NTT (+ combine), Section IV and Fig. "keysw", and the CKKS
+ * operations built on it (HMult relinearisation, HRotate, rescale, hoisted
+ * rotations, plaintext multiply).  All work runs in hand-written CUDA kernels
+ * on one GPU; there is no CPU fallback.
+ *
+ * Data conventions (Section II-A: a polynomial is an L x N matrix of 32-bit
+ * residues, row i reduced modulo its own prime):
+ *   - polynomial at level l: uint32 [l][N], limb-major, limb i modulo q_i,
+ *     every residue fully reduced to [0, q_i), NTT (evaluation) form in
+ *     bit-reversed slot order: slot i holds the value at psi^(2 brv(i) + 1);
+ *   - ciphertext: uint32 [2][l][N] = (c0, c1), decrypting as c0 + c1 s;
+ *   - switching key: uint32 [dnum][2][L + K][N] = (b_j, a_j) per digit j with
+ *     b_j = -a_j s + e_j + g_j s', g_j = [P]_{q_i} on digit j's limbs, 0
+ *     elsewhere; rows 0..L-1 are q-limbs, rows L..L+K-1 the special primes;
+ *   - digits: alpha = ceil(L / dnum) limbs each, digit j = limbs
+ *     [j alpha, min((j + 1) alpha, l)); beta(l) = ceil(l / alpha);
+ *   - psi (primitive 2N-th root per prime) = g^((q-1)/2N) for the smallest
+ *     integer g >= 2 with psi^N = -1 (mod q).
+ *
+ * Pointers: polynomial, ciphertext and output arguments are DEVICE pointers
+ * owned by the caller, 16-byte aligned, on the context's device.  Key and
+ * prime-list arguments may be host or device pointers (copied).  Outputs must
+ * not overlap inputs unless a function says so (FHE_EALIAS otherwise).
+ *
+ * Streams: every call is asynchronous on the given stream (a cudaStream_t,
+ * e.g. torch.cuda.Stream().cuda_stream; 0 = legacy default stream).  A
+ * context owns one scratch workspace; consecutive calls on one context are
+ * ordered by the library even across different streams (each call waits for
+ * the previous call's stream through an event), so calls on one context never
+ * run concurrently.  Use one context per concurrent stream.
+ *
+ * Errors: every function returns FHE_OK (0) or a negative status; argument
+ * errors are detected on the host before anything is enqueued.  The library
+ * never prints, exits or throws.  fhe_last_error() returns a thread-local
+ * message for the last non-OK status.
+ */
+#ifndef FHE_GB300_H
+#define FHE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(FHE_BUILD)
+#define FHE_API __attribute__((visibility("default")))
+#else
+#define FHE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FHE_OK 0
+#define FHE_EINVAL (-1)       /* bad argument (null pointer, size, alignment, count) */
+#define FHE_ELEVEL (-2)       /* level outside [1, L] (or < 2 for rescale) */
+#define FHE_ENOKEY (-3)       /* the needed switching key was never set */
+#define FHE_EPRIME (-4)       /* a prime is not prime, not 1 mod 2N, >= 2^31, <= 2^20, or repeated */
+#define FHE_ENOMEM (-5)       /* device allocation failed */
+#define FHE_ECUDA (-6)        /* a CUDA runtime call failed (message in fhe_last_error) */
+#define FHE_EALIAS (-7)       /* output overlaps an input */
+#define FHE_ETIMEOUT (-8)     /* a bounded device-side wait expired */
+#define FHE_EUNSUPPORTED (-9) /* valid but not supported (e.g. N outside 2^12..2^16) */
+
+#define FHE_MAX_PRIMES 64
+#define FHE_RELIN_KEY INT32_MIN /* key_id of the relinearisation key in fhe_keyswitch */
+
+typedef struct fhe_ctx fhe_ctx;
+typedef struct fhe_plan fhe_plan;
+typedef void *fhe_stream;
+
+typedef struct {
+  uint32_t N;
+  int L, K, dnum, alpha;
+  int device;
+  size_t limb_bytes;      /* 4 N */
+  size_t key_bytes;       /* dnum * 2 * (L + K) * limb_bytes, one switching key */
+  size_t workspace_bytes; /* device scratch the context owns */
+  size_t table_bytes;     /* device twiddle / base-conversion tables */
+  int n_rot_keys;         /* rotation keys currently set */
+  int bconv_mode;         /* FHE_BCONV_SCALAR or FHE_BCONV_TC */
+  uint32_t psi[FHE_MAX_PRIMES]; /* psi of q_0..q_{L-1}, p_0..p_{K-1} */
+} fhe_info;
+
+/* BConv implementation selector (fhe_ctx_set_bconv).  Both give identical bits. */
+#define FHE_BCONV_SCALAR 0 /* CUDA-core 64-bit multiply-accumulate, one final reduction */
+#define FHE_BCONV_TC 1     /* tensor cores: 8-bit digit split, exact fp32 accumulation */
+
+/*
+ * Create a context for ring degree N (a power of two, 2^12..2^16), ciphertext
+ * primes q[0..L) and special primes p[0..K) (host pointers), dnum digits, on
+ * CUDA device `device`.  Validates the primes (FHE_EPRIME), computes psi per
+ * prime and every device table (twiddles with their Shoup companions, the
+ * base-conversion tables of Section III-C for every digit and for ModDown,
+ * the rescale constants) and allocates the workspace for one key switch at
+ * level L.  *out is NULL on error.
+ */
+FHE_API int fhe_ctx_create(fhe_ctx **out, uint32_t N, const uint32_t *q, int L, const uint32_t *p, int K, int dnum,
+                   int device);
+FHE_API int fhe_ctx_destroy(fhe_ctx *ctx);
+FHE_API int fhe_ctx_info(const fhe_ctx *ctx, fhe_info *out);
+/* Select the BConv implementation for later calls (FHE_BCONV_SCALAR / FHE_BCONV_TC). */
+FHE_API int fhe_ctx_set_bconv(fhe_ctx *ctx, int mode);
+/* Fuse stage epilogues (1, default) or run the plain per-kernel pipeline (0).  Same bits. */
+FHE_API int fhe_ctx_set_fused(fhe_ctx *ctx, int fused);
+
+/*
+ * Switching keys ([dnum][2][L + K][N] uint32, NTT form, host or device
+ * pointer).  The context copies the key (it owns the copy); the copy is
+ * enqueued on `stream`.  A rotation key is stored under its Galois element
+ * 5^rot mod 2N, so rot and rot + N/2 share one key.  Setting a key again
+ * replaces it.
+ */
+FHE_API int fhe_set_relin_key(fhe_ctx *ctx, const uint32_t *key, fhe_stream stream);
+FHE_API int fhe_set_rot_key(fhe_ctx *ctx, int32_t rot, const uint32_t *key, fhe_stream stream);
+
+/*
+ * Hybrid key switching of d ([level][N], NTT form) with the relinearisation
+ * key (key_id = FHE_RELIN_KEY) or the rotation key of index key_id (Section
+ * IV, Fig. "keysw"): out = (out_0, out_1) [2][level][N] with
+ * out_0 + out_1 s = d s' + small.  ModDown is floor type.
+ */
+FHE_API int fhe_keyswitch(fhe_ctx *ctx, const uint32_t *d, int level, int32_t key_id, uint32_t *out, fhe_stream stream);
+
+/*
+ * HRotate: ct [2][level][N] -> out [2][level][N], rotation of the slots by
+ * rot (new slot j = old slot j + rot): with k = 5^rot mod 2N,
+ * out = (sigma_k(c0) + KS(sigma_k(c1))_0, KS(sigma_k(c1))_1).  The
+ * automorphism is applied in NTT form inside the first kernels (Section II-B,
+ * "The rest": automorphism is index math).  rot = 0 (mod N/2) copies.
+ */
+FHE_API int fhe_rotate(fhe_ctx *ctx, const uint32_t *ct, int level, int32_t rot, uint32_t *out, fhe_stream stream);
+
+/*
+ * HMult with relinearisation: a, b [2][level][N] -> out [2][level][N]:
+ * (d0, d1, d2) = (a0 b0, a0 b1 + a1 b0, a1 b1), out = (d0, d1) + KS(d2).
+ * No rescale (call fhe_rescale).
+ */
+FHE_API int fhe_hmult(fhe_ctx *ctx, const uint32_t *a, const uint32_t *b, int level, uint32_t *out, fhe_stream stream);
+
+/*
+ * Floor rescale: ct [2][level][N] -> out [2][level-1][N],
+ * out_i = (c_i - NTT_{q_i}(INTT_{q_last}(c_last))) q_last^-1 mod q_i.
+ */
+FHE_API int fhe_rescale(fhe_ctx *ctx, const uint32_t *ct, int level, uint32_t *out, fhe_stream stream);
+
+/*
+ * Hoisted rotations of one ciphertext by rots[0..n): one shared ModUp of c1,
+ * then per rotation sigma_k applied to the extended digits (a permutation in
+ * NTT form), the inner product with that rotation's key, ModDown and the
+ * addition of sigma_k(c0).  outs[i] is a device pointer to [2][level][N].
+ * A rotation by 0 copies ct.
+ */
+FHE_API int fhe_rotate_hoisted(fhe_ctx *ctx, const uint32_t *ct, int level, const int32_t *rots, int n,
+                       uint32_t *const *outs, fhe_stream stream);
+
+/* Plaintext multiply: out_c = ct_c * pt ([level][N] NTT form), c = 0, 1. out may equal ct. */
+FHE_API int fhe_pmult(fhe_ctx *ctx, const uint32_t *ct, const uint32_t *pt, int level, uint32_t *out, fhe_stream stream);
+/* Addition of two [npoly][level][N] arrays (npoly = 2 for ciphertexts). out may equal a or b. */
+FHE_API int fhe_add(fhe_ctx *ctx, const uint32_t *a, const uint32_t *b, int npoly, int level, uint32_t *out,
+            fhe_stream stream);
+
+/*
+ * Stage-level entry points (the individual steps of Fig. "keysw"; used by the
+ * parity tests and by callers composing their own pipelines).
+ *   fhe_ntt / fhe_intt: in-place transform of n limbs whose primes are
+ *     prime_idx[0..n) (indices into q_0..q_{L-1}, p_0..p_{K-1}; host array).
+ *   fhe_modup: d [level][N] (NTT form) -> ext [beta][level + K][N] (NTT form),
+ *     digit j's own limbs copied from d.
+ *   fhe_moddown: u [level + K][N] (NTT form, extended basis) -> out [level][N].
+ *   fhe_bconv: coefficient-form fast base conversion of in [n_in][N] (primes
+ *     in_idx) to out [n_out][N] (primes out_idx), Section II-B "BConv" with the
+ *     table T[i][j] = (Qstar / q_j) mod p_i of Section III-C and the
+ *     [(Qstar / q_j)^-1]_{q_j} pre-multiplication; n_in <= 32, n_out <= 64.
+ */
+FHE_API int fhe_ntt(fhe_ctx *ctx, uint32_t *a, const int *prime_idx, int n, fhe_stream stream);
+FHE_API int fhe_intt(fhe_ctx *ctx, uint32_t *a, const int *prime_idx, int n, fhe_stream stream);
+FHE_API int fhe_modup(fhe_ctx *ctx, const uint32_t *d, int level, uint32_t *ext, fhe_stream stream);
+FHE_API int fhe_moddown(fhe_ctx *ctx, const uint32_t *u, int level, uint32_t *out, fhe_stream stream);
+FHE_API int fhe_bconv(fhe_ctx *ctx, const uint32_t *in, const int *in_idx, int n_in, uint32_t *out, const int *out_idx,
+              int n_out, fhe_stream stream);
+
+/*
+ * Batched key switching (Section IV-A multi-polynomial caching and batching,
+ * Section IV-C CUDA Graphs): a plan holds a list of independent operations
+ * at uneven levels; fhe_batch_plan validates them, sizes the item groups so
+ * each group's working set stays in L2, and captures the whole batch into
+ * one CUDA graph; fhe_batch_launch replays it on `stream`.  Every item's
+ * result is bit-identical to the same operation run alone.  The buffers
+ * named by the items must stay valid while the plan is used.
+ */
+#define FHE_OP_KS 0     /* out = KS(in) with key_id = rot (FHE_RELIN_KEY or a rotation index) */
+#define FHE_OP_ROTATE 1 /* out = HRotate(in, rot) */
+#define FHE_OP_RELIN 2  /* out = HMult(in, in2) with relinearisation */
+typedef struct {
+  int op;
+  int level;
+  int32_t rot;
+  const uint32_t *in;
+  const uint32_t *in2;
+  uint32_t *out;
+} fhe_ks_item;
+
+#define FHE_PLAN_GRAPH 1 /* capture into a CUDA graph (otherwise launch kernels directly) */
+FHE_API int fhe_batch_plan(fhe_ctx *ctx, const fhe_ks_item *items, int n, int flags, fhe_plan **out);
+FHE_API int fhe_batch_launch(fhe_plan *plan, fhe_stream stream);
+FHE_API int fhe_plan_destroy(fhe_plan *plan);
+/* number of kernel launches one fhe_batch_launch performs (graph nodes or direct launches) */
+FHE_API int fhe_plan_kernel_count(const fhe_plan *plan);
+
+FHE_API const char *fhe_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FHE_GB300_H */

@@ -1,0 +1,308 @@
+"""Thin ctypes binding of the C ABI in include/fhe.h (argument marshalling only).
+
+Device buffers are torch tensors (dtype int32 or uint32, contiguous, on the
+context's device) holding the uint32 residues; the binding passes their
+data_ptr() and the current torch stream's handle.  Every computation runs in
+libfhe_gb300.so; there is no Python or CPU fallback: if the library is not
+built, `lib()` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Iterable, List, Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+FHE_OK = 0
+FHE_EINVAL, FHE_ELEVEL, FHE_ENOKEY, FHE_EPRIME, FHE_ENOMEM = -1, -2, -3, -4, -5
+FHE_ECUDA, FHE_EALIAS, FHE_ETIMEOUT, FHE_EUNSUPPORTED = -6, -7, -8, -9
+FHE_RELIN_KEY = -(2 ** 31)
+FHE_BCONV_SCALAR, FHE_BCONV_TC = 0, 1
+FHE_OP_KS, FHE_OP_ROTATE, FHE_OP_RELIN = 0, 1, 2
+FHE_PLAN_GRAPH = 1
+
+# every entry point declared in include/fhe.h
+EXPORTS = (
+    "fhe_ctx_create", "fhe_ctx_destroy", "fhe_ctx_info", "fhe_ctx_set_bconv", "fhe_ctx_set_fused",
+    "fhe_set_relin_key", "fhe_set_rot_key", "fhe_keyswitch", "fhe_rotate", "fhe_hmult", "fhe_rescale",
+    "fhe_rotate_hoisted", "fhe_pmult", "fhe_add", "fhe_ntt", "fhe_intt", "fhe_modup", "fhe_moddown",
+    "fhe_bconv", "fhe_batch_plan", "fhe_batch_launch", "fhe_plan_destroy", "fhe_plan_kernel_count",
+    "fhe_last_error",
+)
+
+
+class FheError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class FheInfo(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_uint32), ("L", ctypes.c_int), ("K", ctypes.c_int), ("dnum", ctypes.c_int),
+                ("alpha", ctypes.c_int), ("device", ctypes.c_int), ("limb_bytes", ctypes.c_size_t),
+                ("key_bytes", ctypes.c_size_t), ("workspace_bytes", ctypes.c_size_t),
+                ("table_bytes", ctypes.c_size_t), ("n_rot_keys", ctypes.c_int), ("bconv_mode", ctypes.c_int),
+                ("psi", ctypes.c_uint32 * 64)]
+
+
+class KsItem(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("level", ctypes.c_int), ("rot", ctypes.c_int32),
+                ("in_", ctypes.c_void_p), ("in2", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+_lib = None
+vp = ctypes.c_void_p
+ip = ctypes.POINTER(ctypes.c_int)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """Load libfhe_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build the CUDA library first "
+                          "(paper_2512_18345_gb300.build.build_library() or __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    sig = {
+        "fhe_ctx_create": [ctypes.POINTER(vp), ctypes.c_uint32, u32p, ctypes.c_int, u32p, ctypes.c_int, ctypes.c_int,
+                           ctypes.c_int],
+        "fhe_ctx_destroy": [vp],
+        "fhe_ctx_info": [vp, ctypes.POINTER(FheInfo)],
+        "fhe_ctx_set_bconv": [vp, ctypes.c_int],
+        "fhe_ctx_set_fused": [vp, ctypes.c_int],
+        "fhe_set_relin_key": [vp, vp, vp],
+        "fhe_set_rot_key": [vp, ctypes.c_int32, vp, vp],
+        "fhe_keyswitch": [vp, vp, ctypes.c_int, ctypes.c_int32, vp, vp],
+        "fhe_rotate": [vp, vp, ctypes.c_int, ctypes.c_int32, vp, vp],
+        "fhe_hmult": [vp, vp, vp, ctypes.c_int, vp, vp],
+        "fhe_rescale": [vp, vp, ctypes.c_int, vp, vp],
+        "fhe_rotate_hoisted": [vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_int,
+                               ctypes.POINTER(vp), vp],
+        "fhe_pmult": [vp, vp, vp, ctypes.c_int, vp, vp],
+        "fhe_add": [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp, vp],
+        "fhe_ntt": [vp, vp, ip, ctypes.c_int, vp],
+        "fhe_intt": [vp, vp, ip, ctypes.c_int, vp],
+        "fhe_modup": [vp, vp, ctypes.c_int, vp, vp],
+        "fhe_moddown": [vp, vp, ctypes.c_int, vp, vp],
+        "fhe_bconv": [vp, vp, ip, ctypes.c_int, vp, ip, ctypes.c_int, vp],
+        "fhe_batch_plan": [vp, ctypes.POINTER(KsItem), ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)],
+        "fhe_batch_launch": [vp, vp],
+        "fhe_plan_destroy": [vp],
+        "fhe_plan_kernel_count": [vp],
+        "fhe_last_error": [],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_char_p if name == "fhe_last_error" else ctypes.c_int
+    _lib = L
+    return L
+
+
+def check(rc: int) -> None:
+    if rc != FHE_OK:
+        raise FheError(rc, lib().fhe_last_error().decode())
+
+
+def _ptr(t) -> vp:
+    """Device pointer of a torch tensor (int32 / uint32, contiguous)."""
+    if t is None:
+        return vp(0)
+    assert t.is_contiguous(), "buffers must be contiguous"
+    return vp(t.data_ptr())
+
+
+def _stream(stream) -> vp:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return vp(s.cuda_stream)
+
+
+def _idx(xs: Sequence[int]):
+    return (ctypes.c_int * len(xs))(*xs)
+
+
+def to_device(a: np.ndarray, device: int = 0):
+    """uint32 numpy array -> contiguous int32 torch tensor on cuda:device (bit copy)."""
+    import torch
+    a = np.ascontiguousarray(a, dtype=np.uint32)
+    return torch.from_numpy(a.view(np.int32)).to(f"cuda:{device}")
+
+
+def to_numpy(t) -> np.ndarray:
+    return t.detach().cpu().numpy().view(np.uint32)
+
+
+def empty(shape, device: int = 0):
+    import torch
+    return torch.empty(tuple(shape), dtype=torch.int32, device=f"cuda:{device}")
+
+
+class Plan:
+    def __init__(self, ctx: "Context", handle: vp, keep: list):
+        self.ctx, self.h, self._keep = ctx, handle, keep
+
+    def launch(self, stream=None) -> None:
+        check(lib().fhe_batch_launch(self.h, _stream(stream)))
+
+    @property
+    def kernel_count(self) -> int:
+        return lib().fhe_plan_kernel_count(self.h)
+
+    def close(self) -> None:
+        if self.h:
+            check(lib().fhe_plan_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    """An fhe_ctx: parameters, device tables, keys and workspace on one GPU."""
+
+    def __init__(self, N: int, q: Sequence[int], p: Sequence[int], dnum: int, device: int = 0):
+        self.N, self.q, self.p, self.dnum, self.device = N, list(q), list(p), dnum, device
+        qa = (ctypes.c_uint32 * len(q))(*q)
+        pa = (ctypes.c_uint32 * len(p))(*p)
+        h = vp()
+        check(lib().fhe_ctx_create(ctypes.byref(h), N, qa, len(q), pa, len(p), dnum, device))
+        self.h = h
+
+    @classmethod
+    def from_params(cls, P, device: int = 0) -> "Context":
+        return cls(P.N, P.q, P.p, P.dnum, device)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            check(lib().fhe_ctx_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def L(self):
+        return len(self.q)
+
+    @property
+    def K(self):
+        return len(self.p)
+
+    def info(self) -> dict:
+        i = FheInfo()
+        check(lib().fhe_ctx_info(self.h, ctypes.byref(i)))
+        d = {f: getattr(i, f) for f, _ in FheInfo._fields_ if f != "psi"}
+        d["psi"] = list(i.psi)[: i.L + i.K]
+        return d
+
+    def set_bconv(self, mode: int) -> None:
+        check(lib().fhe_ctx_set_bconv(self.h, mode))
+
+    def set_fused(self, fused: bool) -> None:
+        check(lib().fhe_ctx_set_fused(self.h, int(bool(fused))))
+
+    def set_relin_key(self, key, stream=None) -> None:
+        check(lib().fhe_set_relin_key(self.h, _ptr(key), _stream(stream)))
+
+    def set_rot_key(self, rot: int, key, stream=None) -> None:
+        check(lib().fhe_set_rot_key(self.h, rot, _ptr(key), _stream(stream)))
+
+    def _out(self, out, shape):
+        return out if out is not None else empty(shape, self.device)
+
+    def keyswitch(self, d, level: int, key_id: int = FHE_RELIN_KEY, out=None, stream=None):
+        out = self._out(out, (2, level, self.N))
+        check(lib().fhe_keyswitch(self.h, _ptr(d), level, key_id, _ptr(out), _stream(stream)))
+        return out
+
+    def rotate(self, ct, level: int, rot: int, out=None, stream=None):
+        out = self._out(out, (2, level, self.N))
+        check(lib().fhe_rotate(self.h, _ptr(ct), level, rot, _ptr(out), _stream(stream)))
+        return out
+
+    def hmult(self, a, b, level: int, out=None, stream=None):
+        out = self._out(out, (2, level, self.N))
+        check(lib().fhe_hmult(self.h, _ptr(a), _ptr(b), level, _ptr(out), _stream(stream)))
+        return out
+
+    def rescale(self, ct, level: int, out=None, stream=None):
+        out = self._out(out, (2, level - 1, self.N))
+        check(lib().fhe_rescale(self.h, _ptr(ct), level, _ptr(out), _stream(stream)))
+        return out
+
+    def rotate_hoisted(self, ct, level: int, rots: Sequence[int], outs=None, stream=None):
+        outs = outs if outs is not None else [empty((2, level, self.N), self.device) for _ in rots]
+        n = len(rots)
+        r = (ctypes.c_int32 * n)(*rots)
+        o = (vp * n)(*[o.data_ptr() for o in outs])
+        check(lib().fhe_rotate_hoisted(self.h, _ptr(ct), level, r, n, o, _stream(stream)))
+        return outs
+
+    def pmult(self, ct, pt, level: int, out=None, stream=None):
+        out = self._out(out, (2, level, self.N))
+        check(lib().fhe_pmult(self.h, _ptr(ct), _ptr(pt), level, _ptr(out), _stream(stream)))
+        return out
+
+    def add(self, a, b, level: int, npoly: int = 2, out=None, stream=None):
+        out = self._out(out, (npoly, level, self.N))
+        check(lib().fhe_add(self.h, _ptr(a), _ptr(b), npoly, level, _ptr(out), _stream(stream)))
+        return out
+
+    def ntt(self, a, prime_idx: Sequence[int], stream=None):
+        check(lib().fhe_ntt(self.h, _ptr(a), _idx(prime_idx), len(prime_idx), _stream(stream)))
+        return a
+
+    def intt(self, a, prime_idx: Sequence[int], stream=None):
+        check(lib().fhe_intt(self.h, _ptr(a), _idx(prime_idx), len(prime_idx), _stream(stream)))
+        return a
+
+    def beta(self, level: int) -> int:
+        alpha = -(-self.L // self.dnum)
+        return -(-level // alpha)
+
+    def modup(self, d, level: int, ext=None, stream=None):
+        ext = self._out(ext, (self.beta(level), level + self.K, self.N))
+        check(lib().fhe_modup(self.h, _ptr(d), level, _ptr(ext), _stream(stream)))
+        return ext
+
+    def moddown(self, u, level: int, out=None, stream=None):
+        out = self._out(out, (level, self.N))
+        check(lib().fhe_moddown(self.h, _ptr(u), level, _ptr(out), _stream(stream)))
+        return out
+
+    def bconv(self, x, in_idx: Sequence[int], out_idx: Sequence[int], out=None, stream=None):
+        out = self._out(out, (len(out_idx), self.N))
+        check(lib().fhe_bconv(self.h, _ptr(x), _idx(in_idx), len(in_idx), _ptr(out), _idx(out_idx), len(out_idx),
+                              _stream(stream)))
+        return out
+
+    def batch_plan(self, items: Iterable[dict], flags: int = FHE_PLAN_GRAPH) -> Plan:
+        items = list(items)
+        arr = (KsItem * max(1, len(items)))()
+        keep = []
+        for i, it in enumerate(items):
+            arr[i].op, arr[i].level, arr[i].rot = it["op"], it["level"], it.get("rot", 0)
+            arr[i].in_ = it["in"].data_ptr()
+            arr[i].in2 = it["in2"].data_ptr() if it.get("in2") is not None else 0
+            arr[i].out = it["out"].data_ptr()
+            keep += [it["in"], it.get("in2"), it["out"]]
+        h = vp()
+        check(lib().fhe_batch_plan(self.h, arr, len(items), flags, ctypes.byref(h)))
+        return Plan(self, h, keep)

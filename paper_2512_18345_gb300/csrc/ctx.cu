@@ -1,0 +1,430 @@
+// Host side of the C ABI (include/fhe.h): parameter validation, the device
+// tables (twiddles, base-conversion tables), switching keys, the workspace
+// and the key-switching pipelines built from the kernels in kernels.cu.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/fhe.h"
+#include "elementwise.cuh"
+#include "internal.h"
+#include "ctx.h"
+
+using namespace fhe;
+
+// ---------------------------------------------------------------- errors
+static thread_local std::string g_err;
+
+int fhe_fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+extern "C" const char *fhe_last_error(void) { return g_err.c_str(); }
+
+#define CUDA_OR_FAIL(call)                                                                     \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return fhe_fail(e_ == cudaErrorMemoryAllocation ? FHE_ENOMEM : FHE_ECUDA, "%s: %s (%s:%d)", \
+                      #call, cudaGetErrorString(e_), __FILE__, __LINE__);                      \
+  } while (0)
+
+// ---------------------------------------------------------------- host number theory
+static uint32_t h_mul(uint32_t a, uint32_t b, uint32_t q) { return (uint32_t)((uint64_t)a * b % q); }
+static uint32_t h_pow(uint32_t a, uint64_t e, uint32_t q) {
+  uint64_t r = 1 % q, b = a % q;
+  for (; e; e >>= 1) {
+    if (e & 1) r = r * b % q;
+    b = b * b % q;
+  }
+  return (uint32_t)r;
+}
+static uint32_t h_inv(uint32_t a, uint32_t q) { return h_pow(a, q - 2, q); }
+static bool h_is_prime(uint32_t n) {  // deterministic Miller-Rabin for 32-bit n (bases 2, 7, 61)
+  if (n < 2) return false;
+  for (uint32_t p : {2u, 3u, 5u, 7u, 11u, 13u, 61u})
+    if (n % p == 0) return n == p;
+  uint32_t d = n - 1;
+  int s = 0;
+  while (!(d & 1)) d >>= 1, s++;
+  for (uint32_t a : {2u, 7u, 61u}) {
+    uint32_t x = h_pow(a, d, n);
+    if (x == 1 || x == n - 1) continue;
+    bool comp = true;
+    for (int i = 1; i < s && comp; i++) {
+      x = h_mul(x, x, n);
+      if (x == n - 1) comp = false;
+    }
+    if (comp) return false;
+  }
+  return true;
+}
+// psi = g^((q-1)/2N) for the smallest g >= 2 with psi^N = -1
+static uint32_t h_psi(uint32_t q, uint32_t N) {
+  for (uint32_t g = 2; g < q; g++) {
+    const uint32_t psi = h_pow(g, (q - 1) / (2ull * N), q);
+    if (h_pow(psi, N, q) == q - 1) return psi;
+  }
+  return 0;
+}
+static uint32_t h_shoup(uint32_t w, uint32_t q) { return (uint32_t)(((uint64_t)w << 32) / q); }
+static uint2 h_pair(uint32_t w, uint32_t q) { return make_uint2(w, h_shoup(w, q)); }
+static uint32_t h_brv(uint32_t x, int bits) {
+  uint32_t r = 0;
+  for (int i = 0; i < bits; i++) r |= ((x >> i) & 1u) << (bits - 1 - i);
+  return r;
+}
+
+static int ceil_div(int a, int b) { return (a + b - 1) / b; }
+uint32_t h_mulmod_pub(uint32_t a, uint32_t b, uint32_t q) { return h_mul(a, b, q); }
+uint32_t h_invmod_pub(uint32_t a, uint32_t q) { return h_inv(a, q); }
+
+// ---------------------------------------------------------------- context
+
+int fhe_ctx::beta(int level) const { return ceil_div(level, alpha); }
+
+int fhe_ctx::ext_prime(int level, int t) const { return t < level ? t : L + (t - level); }
+
+void fhe_ctx::order_stream(cudaStream_t s) {
+  if (capturing) return;
+  if (have_last && s != last_stream) {
+    cudaEventRecord(order_ev, last_stream);
+    cudaStreamWaitEvent(s, order_ev, 0);
+  }
+  last_stream = s;
+  have_last = true;
+}
+
+template <class T>
+static cudaError_t upload(T **dptr, const std::vector<T> &v) {
+  cudaError_t e = cudaMalloc((void **)dptr, sizeof(T) * (v.empty() ? 1 : v.size()));
+  if (e != cudaSuccess) return e;
+  if (!v.empty()) e = cudaMemcpy(*dptr, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+  return e;
+}
+
+static int build_tables(fhe_ctx *c) {
+  const uint32_t N = c->N;
+  const int NP = c->L + c->K;
+  const std::vector<uint32_t> &pr = c->primes;
+  // per-prime constants
+  std::vector<PrimeC> pcs(NP);
+  for (int i = 0; i < NP; i++) {
+    const uint32_t q = pr[i];
+    PrimeC p{};
+    p.q = q;
+    p.r32 = (uint32_t)((1ull << 32) % q);
+    p.r32s = h_shoup(p.r32, q);
+    p.div32 = (uint32_t)((1ull << 32) / q);
+    p.r64 = h_mul(p.r32, p.r32, q);
+    p.r64s = h_shoup(p.r64, q);
+    pcs[i] = p;
+    c->psi[i] = h_psi(q, N);
+  }
+  CUDA_OR_FAIL(upload(&c->d_pc, pcs));
+  // twiddles: tw[k] = psi^brv(k), itw[k] = psi^-brv(k), with Shoup companions
+  std::vector<uint2> tw((size_t)NP * N), itw((size_t)NP * N), ninv(NP);
+  std::vector<uint32_t> pw(N), ipw(N);
+  for (int i = 0; i < NP; i++) {
+    const uint32_t q = pr[i], psi = c->psi[i], ipsi = h_inv(psi, q);
+    pw[0] = ipw[0] = 1;
+    for (uint32_t k = 1; k < N; k++) {
+      pw[k] = h_mul(pw[k - 1], psi, q);
+      ipw[k] = h_mul(ipw[k - 1], ipsi, q);
+    }
+    for (uint32_t k = 0; k < N; k++) {
+      const uint32_t b = h_brv(k, c->logn);
+      tw[(size_t)i * N + k] = h_pair(pw[b], q);
+      itw[(size_t)i * N + k] = h_pair(ipw[b], q);
+    }
+    ninv[i] = h_pair(h_inv(N % q, q), q);
+  }
+  CUDA_OR_FAIL(upload(&c->d_tw, tw));
+  CUDA_OR_FAIL(upload(&c->d_itw, itw));
+  CUDA_OR_FAIL(upload(&c->d_ninv, ninv));
+
+  // ModUp tables per level: pre-factor of each q-limb ((D/q_t)^-1 mod q_t, with and
+  // without N^-1) and the BConv table of every digit (rows in ext-limb order).
+  const int L = c->L, K = c->K, A = c->alpha;
+  std::vector<uint2> mu_scale((size_t)L * L), mu_qhinv((size_t)L * L);
+  c->modup_T.assign((size_t)L * c->dnum, nullptr);
+  c->modup_map.assign((size_t)L * c->dnum, nullptr);
+  for (int level = 1; level <= L; level++) {
+    const int beta = c->beta(level);
+    for (int j = 0; j < beta; j++) {
+      const int lo = j * A, hi = std::min((j + 1) * A, level), a = hi - lo;
+      for (int t = lo; t < hi; t++) {
+        const uint32_t q = pr[t];
+        uint32_t prod = 1;
+        for (int k = lo; k < hi; k++)
+          if (k != t) prod = h_mul(prod, pr[k] % q, q);
+        const uint32_t qh = h_inv(prod, q);
+        mu_qhinv[(size_t)(level - 1) * L + t] = h_pair(qh, q);
+        mu_scale[(size_t)(level - 1) * L + t] = h_pair(h_mul(qh, h_inv(N % q, q), q), q);
+      }
+      std::vector<uint32_t> T;
+      std::vector<int2> om;
+      for (int t = 0; t < level + K; t++) {
+        if (t >= lo && t < hi) continue;
+        const int pi = c->ext_prime(level, t);
+        const uint32_t p = pr[pi];
+        for (int k = lo; k < hi; k++) {
+          uint32_t prod = 1;
+          for (int m = lo; m < hi; m++)
+            if (m != k) prod = h_mul(prod, pr[m] % p, p);
+          T.push_back(prod);
+        }
+        om.push_back(make_int2(t, pi));
+      }
+      (void)a;
+      CUDA_OR_FAIL(upload(&c->modup_T[(size_t)(level - 1) * c->dnum + j], T));
+      CUDA_OR_FAIL(upload(&c->modup_map[(size_t)(level - 1) * c->dnum + j], om));
+    }
+  }
+  CUDA_OR_FAIL(upload(&c->d_mu_scale, mu_scale));
+  CUDA_OR_FAIL(upload(&c->d_mu_qhinv, mu_qhinv));
+
+  // ModDown: pre-factor (P/p_k)^-1 mod p_k (with / without N^-1), table [P/p_k]_{q_i},
+  // P^-1 mod q_i.
+  std::vector<uint2> md_scale(K), md_phinv(K), pinv(L);
+  std::vector<uint32_t> mdT((size_t)L * K);
+  std::vector<int2> mdmap(L);
+  for (int k = 0; k < K; k++) {
+    const uint32_t p = pr[L + k];
+    uint32_t prod = 1;
+    for (int m = 0; m < K; m++)
+      if (m != k) prod = h_mul(prod, pr[L + m] % p, p);
+    const uint32_t ph = h_inv(prod, p);
+    md_phinv[k] = h_pair(ph, p);
+    md_scale[k] = h_pair(h_mul(ph, h_inv(N % p, p), p), p);
+  }
+  for (int i = 0; i < L; i++) {
+    const uint32_t q = pr[i];
+    uint32_t P = 1;
+    for (int m = 0; m < K; m++) P = h_mul(P, pr[L + m] % q, q);
+    pinv[i] = h_pair(h_inv(P, q), q);
+    for (int k = 0; k < K; k++) {
+      uint32_t prod = 1;
+      for (int m = 0; m < K; m++)
+        if (m != k) prod = h_mul(prod, pr[L + m] % q, q);
+      mdT[(size_t)i * K + k] = prod;
+    }
+    mdmap[i] = make_int2(i, i);
+  }
+  CUDA_OR_FAIL(upload(&c->d_md_scale, md_scale));
+  CUDA_OR_FAIL(upload(&c->d_md_phinv, md_phinv));
+  CUDA_OR_FAIL(upload(&c->d_pinv, pinv));
+  CUDA_OR_FAIL(upload(&c->d_mdT, mdT));
+  CUDA_OR_FAIL(upload(&c->d_mdmap, mdmap));
+
+  // rescale: q_{l-1}^-1 mod q_i for every level l and i < l-1
+  std::vector<uint2> rs((size_t)L * L, make_uint2(0, 0));
+  for (int level = 2; level <= L; level++)
+    for (int i = 0; i < level - 1; i++) rs[(size_t)(level - 1) * L + i] = h_pair(h_inv(pr[level - 1] % pr[i], pr[i]), pr[i]);
+  CUDA_OR_FAIL(upload(&c->d_rs_qinv, rs));
+
+  c->table_bytes = sizeof(PrimeC) * NP + 2 * sizeof(uint2) * (size_t)NP * N + sizeof(uint2) * (size_t)(4 * L * L + 3 * K + 2 * L) +
+                   sizeof(uint32_t) * (size_t)L * K;
+  c->tabs.ntt.pc = c->d_pc;
+  c->tabs.ntt.tw_fwd = c->d_tw;
+  c->tabs.ntt.tw_inv = c->d_itw;
+  c->tabs.ntt.ninv = c->d_ninv;
+  c->tabs.pc = c->d_pc;
+  c->tabs.logn = c->logn;
+  return FHE_OK;
+}
+
+static int alloc_workspace(fhe_ctx *c) {
+  const size_t N = c->N;
+  const int L = c->L, K = c->K, B = c->beta(L);
+  size_t off = 0;
+  auto take = [&](size_t limbs) {
+    size_t o = off;
+    off += limbs * N;
+    return o;
+  };
+  const size_t oY = take(L), oEXT = take((size_t)B * (L + K)), oUC = take(2 * K), oR = take(2 * L),
+               oD = take(3 * L), oU = take(2 * (L + K)), oTMP = take(2 * L), oV = take(2);
+  CUDA_OR_FAIL(cudaMalloc(&c->ws, off * sizeof(uint32_t)));
+  c->ws_bytes = off * sizeof(uint32_t);
+  c->wY = c->ws + oY;
+  c->wEXT = c->ws + oEXT;
+  c->wUC = c->ws + oUC;
+  c->wR = c->ws + oR;
+  c->wD = c->ws + oD;
+  c->wU = c->ws + oU;
+  c->wTMP = c->ws + oTMP;
+  c->wV = c->ws + oV;
+  return FHE_OK;
+}
+
+fhe_ctx::~fhe_ctx() {
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(device);
+  cudaFree(d_pc);
+  cudaFree(d_tw);
+  cudaFree(d_itw);
+  cudaFree(d_ninv);
+  cudaFree(d_mu_scale);
+  cudaFree(d_mu_qhinv);
+  for (auto p : modup_T) cudaFree(p);
+  for (auto p : modup_map) cudaFree(p);
+  cudaFree(d_md_scale);
+  cudaFree(d_md_phinv);
+  cudaFree(d_pinv);
+  cudaFree(d_mdT);
+  cudaFree(d_mdmap);
+  cudaFree(d_rs_qinv);
+  cudaFree(ws);
+  cudaFree(relin_key);
+  for (auto &kv : rot_keys) cudaFree(kv.second);
+  for (auto p : scratch_tabs) cudaFree(p);
+  if (order_ev) cudaEventDestroy(order_ev);
+  if (prev >= 0) cudaSetDevice(prev);
+}
+
+extern "C" int fhe_ctx_create(fhe_ctx **out, uint32_t N, const uint32_t *q, int L, const uint32_t *p, int K, int dnum,
+                              int device) {
+  if (!out) return fhe_fail(FHE_EINVAL, "fhe_ctx_create: out is null");
+  *out = nullptr;
+  if (!q || !p) return fhe_fail(FHE_EINVAL, "fhe_ctx_create: null prime list");
+  if (N != 4096u && N != 65536u)
+    return fhe_fail(FHE_EUNSUPPORTED, "fhe_ctx_create: N=%u (supported: 2^12, 2^16)", N);
+  if (L < 1 || K < 1 || L + K > FHE_MAX_PRIMES)
+    return fhe_fail(FHE_EINVAL, "fhe_ctx_create: L=%d K=%d (need L,K >= 1, L+K <= %d)", L, K, FHE_MAX_PRIMES);
+  if (dnum < 1 || dnum > L) return fhe_fail(FHE_EINVAL, "fhe_ctx_create: dnum=%d outside [1, L=%d]", dnum, L);
+  const int alpha = ceil_div(L, dnum);
+  if (alpha > 32 || K > 32)
+    return fhe_fail(FHE_EUNSUPPORTED, "fhe_ctx_create: alpha=%d, K=%d (base conversion supports <= 32 inputs)", alpha, K);
+  if (ceil_div(L, alpha) > 4)
+    return fhe_fail(FHE_EUNSUPPORTED, "fhe_ctx_create: beta=%d digits (inner product supports <= 4)", ceil_div(L, alpha));
+  if (L + K - 1 > 64 || L > 64) return fhe_fail(FHE_EUNSUPPORTED, "fhe_ctx_create: too many limbs");
+  std::vector<uint32_t> pr(q, q + L);
+  pr.insert(pr.end(), p, p + K);
+  for (int i = 0; i < L + K; i++) {
+    const uint32_t x = pr[i];
+    if (x >= (1u << 31) || x <= (1u << 20) || x % (2u * N) != 1 || !h_is_prime(x))
+      return fhe_fail(FHE_EPRIME, "fhe_ctx_create: prime %d = %u is not a prime = 1 mod 2N in (2^20, 2^31)", i, x);
+    for (int k = 0; k < i; k++)
+      if (pr[k] == x) return fhe_fail(FHE_EPRIME, "fhe_ctx_create: prime %u repeated", x);
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return fhe_fail(FHE_ECUDA, "fhe_ctx_create: no CUDA device %d", device);
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (cudaSetDevice(device) != cudaSuccess) return fhe_fail(FHE_ECUDA, "fhe_ctx_create: cudaSetDevice(%d)", device);
+  fhe_ctx *c = new fhe_ctx();
+  c->device = device;
+  c->N = N;
+  c->logn = N == 4096u ? 12 : 16;
+  c->L = L;
+  c->K = K;
+  c->dnum = dnum;
+  c->alpha = alpha;
+  c->primes = pr;
+  int rc = build_tables(c);
+  if (rc == FHE_OK) rc = alloc_workspace(c);
+  if (rc == FHE_OK && cudaEventCreateWithFlags(&c->order_ev, cudaEventDisableTiming) != cudaSuccess)
+    rc = fhe_fail(FHE_ECUDA, "fhe_ctx_create: event");
+  if (rc == FHE_OK) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) rc = fhe_fail(FHE_ECUDA, "fhe_ctx_create: %s", cudaGetErrorString(e));
+  }
+  if (rc != FHE_OK) {
+    delete c;
+  } else {
+    *out = c;
+  }
+  if (prev >= 0) cudaSetDevice(prev);
+  return rc;
+}
+
+extern "C" int fhe_ctx_destroy(fhe_ctx *ctx) {
+  if (!ctx) return fhe_fail(FHE_EINVAL, "fhe_ctx_destroy: null");
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  delete ctx;
+  return FHE_OK;
+}
+
+extern "C" int fhe_ctx_info(const fhe_ctx *c, fhe_info *o) {
+  if (!c || !o) return fhe_fail(FHE_EINVAL, "fhe_ctx_info: null");
+  memset(o, 0, sizeof *o);
+  o->N = c->N;
+  o->L = c->L;
+  o->K = c->K;
+  o->dnum = c->dnum;
+  o->alpha = c->alpha;
+  o->device = c->device;
+  o->limb_bytes = (size_t)4 * c->N;
+  o->key_bytes = (size_t)c->dnum * 2 * (c->L + c->K) * o->limb_bytes;
+  o->workspace_bytes = c->ws_bytes;
+  o->table_bytes = c->table_bytes;
+  o->n_rot_keys = (int)c->rot_keys.size();
+  o->bconv_mode = c->bconv_mode;
+  for (int i = 0; i < c->L + c->K; i++) o->psi[i] = c->psi[i];
+  return FHE_OK;
+}
+
+extern "C" int fhe_ctx_set_bconv(fhe_ctx *c, int mode) {
+  if (!c) return fhe_fail(FHE_EINVAL, "fhe_ctx_set_bconv: null");
+  if (mode != FHE_BCONV_SCALAR && mode != FHE_BCONV_TC) return fhe_fail(FHE_EINVAL, "fhe_ctx_set_bconv: mode %d", mode);
+  if (mode == FHE_BCONV_TC && !fhe_tc_available())
+    return fhe_fail(FHE_EUNSUPPORTED, "fhe_ctx_set_bconv: tensor-core base conversion not built");
+  c->bconv_mode = mode;
+  return FHE_OK;
+}
+
+extern "C" int fhe_ctx_set_fused(fhe_ctx *c, int fused) {
+  if (!c) return fhe_fail(FHE_EINVAL, "fhe_ctx_set_fused: null");
+  c->fused = fused ? 1 : 0;
+  return FHE_OK;
+}
+
+// ---------------------------------------------------------------- keys
+uint32_t fhe_galois_elt(int32_t rot, uint32_t N) {
+  const int64_t half = N / 2;
+  int64_t r = rot % half;
+  if (r < 0) r += half;
+  return h_pow(5, (uint64_t)r, 2 * N);
+}
+
+static int set_key(fhe_ctx *c, uint32_t **slot, const uint32_t *key, cudaStream_t s) {
+  const size_t bytes = (size_t)c->dnum * 2 * (c->L + c->K) * c->N * sizeof(uint32_t);
+  if (!*slot) CUDA_OR_FAIL(cudaMalloc(slot, bytes));
+  c->order_stream(s);
+  CUDA_OR_FAIL(cudaMemcpyAsync(*slot, key, bytes, cudaMemcpyDefault, s));
+  return FHE_OK;
+}
+
+extern "C" int fhe_set_relin_key(fhe_ctx *c, const uint32_t *key, fhe_stream stream) {
+  if (!c || !key) return fhe_fail(FHE_EINVAL, "fhe_set_relin_key: null argument");
+  cudaSetDevice(c->device);
+  return set_key(c, &c->relin_key, key, (cudaStream_t)stream);
+}
+
+extern "C" int fhe_set_rot_key(fhe_ctx *c, int32_t rot, const uint32_t *key, fhe_stream stream) {
+  if (!c || !key) return fhe_fail(FHE_EINVAL, "fhe_set_rot_key: null argument");
+  const uint32_t k = fhe_galois_elt(rot, c->N);
+  if (k == 1) return fhe_fail(FHE_EINVAL, "fhe_set_rot_key: rotation %d is the identity", rot);
+  cudaSetDevice(c->device);
+  uint32_t *&slot = c->rot_keys[k];
+  return set_key(c, &slot, key, (cudaStream_t)stream);
+}
+
+const uint32_t *fhe_ctx::find_key(int32_t key_id) const {
+  if (key_id == FHE_RELIN_KEY) return relin_key;
+  auto it = rot_keys.find(fhe_galois_elt(key_id, N));
+  return it == rot_keys.end() ? nullptr : it->second;
+}

@@ -1,0 +1,606 @@
+// Key-switching pipelines (Section IV, Fig. "keysw") and the CKKS operations
+// built on them, enqueued on the caller's stream.
+//
+// Stage 1 (ModUp): INTT of the input limbs, scaled by N^-1 (D_j/q_t)^-1 (the
+//   BConv pre-factor folded into the INTT output), base conversion of every
+//   digit to the limbs it lacks, NTT of the converted limbs.
+// Stage 2 + 3 (inner product, ModDown): the inner product with the key is
+//   computed for the K special limbs inside the INTT that starts ModDown, and
+//   for the l ciphertext limbs inside the epilogue of ModDown's last NTT,
+//   which also subtracts, multiplies by P^-1 and adds the pass-through
+//   polynomial (Section III-D: NTT(a1) + a2 + ... is fusable).  The inner
+//   product's (2, l) part thus never touches memory as a separate array.
+// The plain (unfused) pipeline runs every step as its own kernel.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "../../include/fhe.h"
+#include "ctx.h"
+#include "elementwise.cuh"
+#include "internal.h"
+
+using namespace fhe;
+
+#define LAUNCH_OR_FAIL(call)                                                                          \
+  do {                                                                                                \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess) return fhe_fail(FHE_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));      \
+  } while (0)
+
+static Seg mkseg(const uint32_t *src, uint32_t *dst, int n, int prime) {
+  Seg s;
+  memset(&s, 0, sizeof s);
+  s.src = src;
+  s.dst = dst;
+  s.n = n;
+  s.prime = prime;
+  s.src_stride = 1;
+  s.src_prime = -1;
+  s.digit = -1;
+  return s;
+}
+
+struct SegBuilder {
+  SegList l;
+  SegBuilder() {
+    memset(&l, 0, sizeof l);
+  }
+  void add(const Seg &s) {
+    if (s.n <= 0) return;
+    l.seg[l.nseg++] = s;
+    l.total += s.n;
+  }
+};
+
+static bool overlaps(const void *a, size_t abytes, const void *b, size_t bbytes) {
+  const char *x = (const char *)a, *y = (const char *)b;
+  return x < y + bbytes && y < x + abytes;
+}
+
+// ------------------------------------------------------------------ stage 1: ModUp
+// d: [level][N] NTT form, read through sigma_{galois_d}.  Writes ext [beta][level+K][N]
+// (NTT form) except each digit's own limbs.
+int run_modup(fhe_ctx *c, const uint32_t *d, int level, uint32_t galois_d, uint32_t *ext, cudaStream_t s) {
+  const size_t N = c->N;
+  const int L = c->L, K = c->K, A = c->alpha, beta = c->beta(level), n_ext = level + K;
+  KsArgs ks;
+  memset(&ks, 0, sizeof ks);
+  ks.galois_own = galois_d;
+  ks.galois_ext = ks.galois_add = 1;
+  if (c->fused) {
+    SegBuilder first, second;
+    first.add(mkseg(d, c->wY, level, 0));
+    Seg s2 = mkseg(c->wY, c->wY, level, 0);
+    s2.scale = c->d_mu_scale + (size_t)(level - 1) * L;
+    second.add(s2);
+    LAUNCH_OR_FAIL(launch_ntt(c->tabs, false, galois_d != 1u ? PRO_GATHER : PRO_PLAIN, EPI_SCALE, first.l, second.l,
+                              ks, s));
+  } else {
+    const uint32_t *src = d;
+    if (galois_d != 1u) {
+      SegBuilder g;
+      g.add(mkseg(d, c->wTMP, level, 0));
+      LAUNCH_OR_FAIL(launch_ew(c->tabs, EW_GATHER, g.l, ks, s));
+      src = c->wTMP;
+    }
+    SegBuilder first, second, sc;
+    first.add(mkseg(src, c->wY, level, 0));
+    second.add(mkseg(c->wY, c->wY, level, 0));
+    LAUNCH_OR_FAIL(launch_ntt(c->tabs, false, PRO_PLAIN, EPI_SCALE, first.l, second.l, ks, s));
+    Seg s3 = mkseg(c->wY, c->wY, level, 0);
+    s3.scale = c->d_mu_qhinv + (size_t)(level - 1) * L;
+    sc.add(s3);
+    LAUNCH_OR_FAIL(launch_ew(c->tabs, EW_SCALE, sc.l, ks, s));
+  }
+  // base conversion of every digit
+  BconvArgs ba;
+  memset(&ba, 0, sizeof ba);
+  int max_in = 0;
+  for (int j = 0; j < beta; j++) {
+    const int lo = j * A, hi = std::min((j + 1) * A, level);
+    BconvGroup &g = ba.g[ba.ngroups++];
+    g.in = c->wY + (size_t)lo * N;
+    g.out = ext + (size_t)j * n_ext * N;
+    g.T = c->modup_T[(size_t)(level - 1) * c->dnum + j];
+    g.omap = c->modup_map[(size_t)(level - 1) * c->dnum + j];
+    g.n_in = hi - lo;
+    g.n_out = n_ext - (hi - lo);
+    max_in = std::max(max_in, hi - lo);
+  }
+  if (c->bconv_mode == FHE_BCONV_TC)
+    LAUNCH_OR_FAIL(launch_bconv_tc(c->tabs, ba, max_in, s));
+  else
+    LAUNCH_OR_FAIL(launch_bconv(c->tabs, ba, max_in, s));
+  // NTT of the converted limbs of every digit (runs of consecutive primes)
+  SegBuilder nt;
+  for (int j = 0; j < beta; j++) {
+    const int lo = j * A, hi = std::min((j + 1) * A, level);
+    uint32_t *e = ext + (size_t)j * n_ext * N;
+    nt.add(mkseg(e, e, lo, 0));
+    nt.add(mkseg(e + (size_t)hi * N, e + (size_t)hi * N, level - hi, hi));
+    nt.add(mkseg(e + (size_t)level * N, e + (size_t)level * N, K, L));
+  }
+  LAUNCH_OR_FAIL(launch_ntt(c->tabs, true, PRO_PLAIN, EPI_PLAIN, nt.l, nt.l, ks, s));
+  return FHE_OK;
+}
+
+// ------------------------------------------------------------------ stages 2 + 3: inner product, ModDown
+// ks carries ext, own (+ galois), key, addp (+ galois, add_c1).  Writes out [2][level][N].
+int run_moddown(fhe_ctx *c, KsArgs ks, int level, uint32_t *out, cudaStream_t s) {
+  const size_t N = c->N;
+  const int L = c->L, K = c->K, n_ext = level + K;
+  ks.level = level;
+  ks.n_ext = n_ext;
+  ks.beta = c->beta(level);
+  ks.alpha = c->alpha;
+  ks.L = L;
+  ks.K = K;
+  ks.pinv = c->d_pinv;
+  BconvArgs ba;
+  memset(&ba, 0, sizeof ba);
+  for (int cc = 0; cc < 2; cc++) {
+    BconvGroup &g = ba.g[ba.ngroups++];
+    g.in = c->wUC + (size_t)cc * K * N;
+    g.out = c->wR + (size_t)cc * level * N;
+    g.T = c->d_mdT;
+    g.omap = c->d_mdmap;
+    g.n_in = K;
+    g.n_out = level;
+  }
+  if (c->fused) {
+    SegBuilder first, second;
+    for (int cc = 0; cc < 2; cc++) {
+      Seg a = mkseg(nullptr, c->wUC + (size_t)cc * K * N, K, L);
+      a.t0 = level;
+      a.key_row0 = L;
+      a.c = cc;
+      first.add(a);
+      Seg b = mkseg(c->wUC + (size_t)cc * K * N, c->wUC + (size_t)cc * K * N, K, L);
+      b.scale = c->d_md_scale;
+      second.add(b);
+    }
+    LAUNCH_OR_FAIL(launch_ntt(c->tabs, false, PRO_IP, EPI_SCALE, first.l, second.l, ks, s));
+    if (c->bconv_mode == FHE_BCONV_TC)
+      LAUNCH_OR_FAIL(launch_bconv_tc(c->tabs, ba, K, s));
+    else
+      LAUNCH_OR_FAIL(launch_bconv(c->tabs, ba, K, s));
+    SegBuilder na, nb;
+    for (int cc = 0; cc < 2; cc++) {
+      uint32_t *r = c->wR + (size_t)cc * level * N;
+      na.add(mkseg(r, r, level, 0));
+      Seg b = mkseg(r, out + (size_t)cc * level * N, level, 0);
+      b.t0 = 0;
+      b.key_row0 = 0;
+      b.c = cc;
+      nb.add(b);
+    }
+    LAUNCH_OR_FAIL(launch_ntt(c->tabs, true, PRO_PLAIN, EPI_COMBINE, na.l, nb.l, ks, s));
+    return FHE_OK;
+  }
+  // plain: full inner product into U, then separate kernels
+  SegBuilder ip;
+  for (int cc = 0; cc < 2; cc++) {
+    uint32_t *u = c->wU + (size_t)cc * n_ext * N;
+    Seg a = mkseg(nullptr, u, level, 0);
+    a.t0 = 0;
+    a.key_row0 = 0;
+    a.c = cc;
+    ip.add(a);
+    Seg b = mkseg(nullptr, u + (size_t)level * N, K, L);
+    b.t0 = level;
+    b.key_row0 = L;
+    b.c = cc;
+    ip.add(b);
+  }
+  LAUNCH_OR_FAIL(launch_ew(c->tabs, EW_IP, ip.l, ks, s));
+  SegBuilder first, second, sc;
+  for (int cc = 0; cc < 2; cc++) {
+    uint32_t *uc = c->wUC + (size_t)cc * K * N;
+    first.add(mkseg(c->wU + ((size_t)cc * n_ext + level) * N, uc, K, L));
+    second.add(mkseg(uc, uc, K, L));
+    Seg x = mkseg(uc, uc, K, L);
+    x.scale = c->d_md_phinv;
+    sc.add(x);
+  }
+  LAUNCH_OR_FAIL(launch_ntt(c->tabs, false, PRO_PLAIN, EPI_SCALE, first.l, second.l, ks, s));
+  LAUNCH_OR_FAIL(launch_ew(c->tabs, EW_SCALE, sc.l, ks, s));
+  if (c->bconv_mode == FHE_BCONV_TC)
+    LAUNCH_OR_FAIL(launch_bconv_tc(c->tabs, ba, K, s));
+  else
+    LAUNCH_OR_FAIL(launch_bconv(c->tabs, ba, K, s));
+  SegBuilder nr, cb;
+  for (int cc = 0; cc < 2; cc++) {
+    uint32_t *r = c->wR + (size_t)cc * level * N;
+    nr.add(mkseg(r, r, level, 0));
+    Seg x = mkseg(c->wU + (size_t)cc * n_ext * N, out + (size_t)cc * level * N, level, 0);
+    x.src2 = r;
+    x.t0 = 0;
+    x.c = cc;
+    cb.add(x);
+  }
+  LAUNCH_OR_FAIL(launch_ntt(c->tabs, true, PRO_PLAIN, EPI_PLAIN, nr.l, nr.l, ks, s));
+  LAUNCH_OR_FAIL(launch_ew(c->tabs, EW_COMBINE, cb.l, ks, s));
+  return FHE_OK;
+}
+
+static KsArgs ks_base(const uint32_t *own, const uint32_t *ext, const uint32_t *key) {
+  KsArgs ks;
+  memset(&ks, 0, sizeof ks);
+  ks.own = own;
+  ks.ext = ext;
+  ks.key = key;
+  ks.galois_own = ks.galois_ext = ks.galois_add = 1;
+  return ks;
+}
+
+static int check_level(const fhe_ctx *c, int level, const char *fn) {
+  if (level < 1 || level > c->L) return fhe_fail(FHE_ELEVEL, "%s: level %d outside [1, %d]", fn, level, c->L);
+  return FHE_OK;
+}
+
+static int check_ptr(const void *p, const char *fn, const char *name) {
+  if (!p) return fhe_fail(FHE_EINVAL, "%s: %s is null", fn, name);
+  if ((uintptr_t)p & 15) return fhe_fail(FHE_EINVAL, "%s: %s is not 16-byte aligned", fn, name);
+  return FHE_OK;
+}
+
+#define CHECK(x)            \
+  do {                      \
+    int rc_ = (x);          \
+    if (rc_ != FHE_OK) return rc_; \
+  } while (0)
+
+extern "C" int fhe_keyswitch(fhe_ctx *c, const uint32_t *d, int level, int32_t key_id, uint32_t *out,
+                             fhe_stream stream) {
+  if (!c) return fhe_fail(FHE_EINVAL, "fhe_keyswitch: null ctx");
+  CHECK(check_level(c, level, "fhe_keyswitch"));
+  CHECK(check_ptr(d, "fhe_keyswitch", "d"));
+  CHECK(check_ptr(out, "fhe_keyswitch", "out"));
+  const size_t poly = (size_t)level * c->N * 4;
+  if (overlaps(d, poly, out, 2 * poly)) return fhe_fail(FHE_EALIAS, "fhe_keyswitch: out overlaps d");
+  const uint32_t *key = c->find_key(key_id);
+  if (!key) return fhe_fail(FHE_ENOKEY, "fhe_keyswitch: no key for id %d", key_id);
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->order_stream(s);
+  CHECK(run_modup(c, d, level, 1u, c->wEXT, s));
+  return run_moddown(c, ks_base(d, c->wEXT, key), level, out, s);
+}
+
+extern "C" int fhe_rotate(fhe_ctx *c, const uint32_t *ct, int level, int32_t rot, uint32_t *out, fhe_stream stream) {
+  if (!c) return fhe_fail(FHE_EINVAL, "fhe_rotate: null ctx");
+  CHECK(check_level(c, level, "fhe_rotate"));
+  CHECK(check_ptr(ct, "fhe_rotate", "ct"));
+  CHECK(check_ptr(out, "fhe_rotate", "out"));
+  const size_t poly = (size_t)level * c->N;
+  if (overlaps(ct, 8 * poly, out, 8 * poly)) return fhe_fail(FHE_EALIAS, "fhe_rotate: out overlaps ct");
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint32_t k = fhe_galois_elt(rot, c->N);
+  if (k == 1u) {
+    c->order_stream(s);
+    if (cudaMemcpyAsync(out, ct, 8 * poly, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return fhe_fail(FHE_ECUDA, "fhe_rotate: copy");
+    return FHE_OK;
+  }
+  const uint32_t *key = c->find_key(rot);
+  if (!key) return fhe_fail(FHE_ENOKEY, "fhe_rotate: no rotation key for %d", rot);
+  c->order_stream(s);
+  CHECK(run_modup(c, ct + poly, level, k, c->wEXT, s));
+  KsArgs ks = ks_base(ct + poly, c->wEXT, key);
+  ks.galois_own = k;
+  ks.addp = ct;
+  ks.galois_add = k;
+  return run_moddown(c, ks, level, out, s);
+}
+
+extern "C" int fhe_hmult(fhe_ctx *c, const uint32_t *a, const uint32_t *b, int level, uint32_t *out,
+                         fhe_stream stream) {
+  if (!c) return fhe_fail(FHE_EINVAL, "fhe_hmult: null ctx");
+  CHECK(check_level(c, level, "fhe_hmult"));
+  CHECK(check_ptr(a, "fhe_hmult", "a"));
+  CHECK(check_ptr(b, "fhe_hmult", "b"));
+  CHECK(check_ptr(out, "fhe_hmult", "out"));
+  if (!c->relin_key) return fhe_fail(FHE_ENOKEY, "fhe_hmult: relinearisation key not set");
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->order_stream(s);
+  const size_t poly = (size_t)level * c->N;
+  LAUNCH_OR_FAIL(launch_tensor(c->tabs, a, b, c->wD, level, s));
+  CHECK(run_modup(c, c->wD + 2 * poly, level, 1u, c->wEXT, s));
+  KsArgs ks = ks_base(c->wD + 2 * poly, c->wEXT, c->relin_key);
+  ks.addp = c->wD;
+  ks.add_c1 = 1;
+  return run_moddown(c, ks, level, out, s);
+}
+
+extern "C" int fhe_rescale(fhe_ctx *c, const uint32_t *ct, int level, uint32_t *out, fhe_stream stream) {
+  if (!c) return fhe_fail(FHE_EINVAL, "fhe_rescale: null ctx");
+  if (level < 2 || level > c->L) return fhe_fail(FHE_ELEVEL, "fhe_rescale: level %d outside [2, %d]", level, c->L);
+  CHECK(check_ptr(ct, "fhe_rescale", "ct"));
+  CHECK(check_ptr(out, "fhe_rescale", "out"));
+  const size_t N = c->N, poly = (size_t)level * N;
+  if (overlaps(ct, 8 * poly, out, 8 * (poly - N))) return fhe_fail(FHE_EALIAS, "fhe_rescale: out overlaps ct");
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->order_stream(s);
+  KsArgs ks = ks_base(nullptr, nullptr, nullptr);
+  SegBuilder f1, f2, g1, g2;
+  for (int cc = 0; cc < 2; cc++) {
+    f1.add(mkseg(ct + cc * poly + (size_t)(level - 1) * N, c->wV + cc * N, 1, level - 1));
+    f2.add(mkseg(c->wV + cc * N, c->wV + cc * N, 1, level - 1));
+  }
+  LAUNCH_OR_FAIL(launch_ntt(c->tabs, false, PRO_PLAIN, EPI_SCALE, f1.l, f2.l, ks, s));
+  for (int cc = 0; cc < 2; cc++) {
+    uint32_t *o = out + (size_t)cc * (level - 1) * N;
+    Seg a = mkseg(c->wV + cc * N, o, level - 1, 0);
+    a.src_stride = 0;
+    a.src_prime = level - 1;
+    g1.add(a);
+    Seg b = mkseg(o, o, level - 1, 0);
+    b.src2 = ct + cc * poly;
+    b.scale = c->d_rs_qinv + (size_t)(level - 1) * c->L;
+    g2.add(b);
+  }
+  LAUNCH_OR_FAIL(launch_ntt(c->tabs, true, PRO_REDUCE, EPI_RESCALE, g1.l, g2.l, ks, s));
+  return FHE_OK;
+}
+
+extern "C" int fhe_rotate_hoisted(fhe_ctx *c, const uint32_t *ct, int level, const int32_t *rots, int n,
+                                  uint32_t *const *outs, fhe_stream stream) {
+  if (!c) return fhe_fail(FHE_EINVAL, "fhe_rotate_hoisted: null ctx");
+  CHECK(check_level(c, level, "fhe_rotate_hoisted"));
+  CHECK(check_ptr(ct, "fhe_rotate_hoisted", "ct"));
+  if (n < 0 || (n > 0 && (!rots || !outs))) return fhe_fail(FHE_EINVAL, "fhe_rotate_hoisted: bad rotation list");
+  const size_t poly = (size_t)level * c->N;
+  std::vector<const uint32_t *> keys(n);
+  for (int r = 0; r < n; r++) {
+    CHECK(check_ptr(outs[r], "fhe_rotate_hoisted", "outs[i]"));
+    if (overlaps(ct, 8 * poly, outs[r], 8 * poly)) return fhe_fail(FHE_EALIAS, "fhe_rotate_hoisted: output overlaps ct");
+    if (fhe_galois_elt(rots[r], c->N) != 1u) {
+      keys[r] = c->find_key(rots[r]);
+      if (!keys[r]) return fhe_fail(FHE_ENOKEY, "fhe_rotate_hoisted: no rotation key for %d", rots[r]);
+    }
+  }
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->order_stream(s);
+  bool need_modup = false;
+  for (int r = 0; r < n; r++) need_modup |= fhe_galois_elt(rots[r], c->N) != 1u;
+  if (need_modup) CHECK(run_modup(c, ct + poly, level, 1u, c->wEXT, s));
+  for (int r = 0; r < n; r++) {
+    const uint32_t k = fhe_galois_elt(rots[r], c->N);
+    if (k == 1u) {
+      if (cudaMemcpyAsync(outs[r], ct, 8 * poly, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return fhe_fail(FHE_ECUDA, "fhe_rotate_hoisted: copy");
+      continue;
+    }
+    KsArgs ks = ks_base(ct + poly, c->wEXT, keys[r]);
+    ks.galois_own = ks.galois_ext = ks.galois_add = k;
+    ks.addp = ct;
+    CHECK(run_moddown(c, ks, level, outs[r], s));
+  }
+  return FHE_OK;
+}
+
+static int elementwise2(fhe_ctx *c, int op, const uint32_t *a, const uint32_t *b, int npoly, int level,
+                        uint32_t *out, bool b_per_poly, cudaStream_t s) {
+  const size_t poly = (size_t)level * c->N;
+  SegBuilder sb;
+  for (int p = 0; p < npoly; p++) {
+    Seg x = mkseg(a + p * poly, out + p * poly, level, 0);
+    x.src2 = b_per_poly ? b + p * poly : b;
+    sb.add(x);
+  }
+  c->order_stream(s);
+  LAUNCH_OR_FAIL(launch_ew(c->tabs, op, sb.l, ks_base(nullptr, nullptr, nullptr), s));
+  return FHE_OK;
+}
+
+extern "C" int fhe_pmult(fhe_ctx *c, const uint32_t *ct, const uint32_t *pt, int level, uint32_t *out,
+                         fhe_stream stream) {
+  if (!c) return fhe_fail(FHE_EINVAL, "fhe_pmult: null ctx");
+  CHECK(check_level(c, level, "fhe_pmult"));
+  CHECK(check_ptr(ct, "fhe_pmult", "ct"));
+  CHECK(check_ptr(pt, "fhe_pmult", "pt"));
+  CHECK(check_ptr(out, "fhe_pmult", "out"));
+  cudaSetDevice(c->device);
+  return elementwise2(c, EW_MUL, ct, pt, 2, level, out, false, (cudaStream_t)stream);
+}
+
+extern "C" int fhe_add(fhe_ctx *c, const uint32_t *a, const uint32_t *b, int npoly, int level, uint32_t *out,
+                       fhe_stream stream) {
+  if (!c) return fhe_fail(FHE_EINVAL, "fhe_add: null ctx");
+  CHECK(check_level(c, level, "fhe_add"));
+  if (npoly < 1 || npoly > 8) return fhe_fail(FHE_EINVAL, "fhe_add: npoly %d outside [1, 8]", npoly);
+  CHECK(check_ptr(a, "fhe_add", "a"));
+  CHECK(check_ptr(b, "fhe_add", "b"));
+  CHECK(check_ptr(out, "fhe_add", "out"));
+  cudaSetDevice(c->device);
+  return elementwise2(c, EW_ADD, a, b, npoly, level, out, true, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------ stage-level entry points
+
+static int transform(fhe_ctx *c, uint32_t *a, const int *idx, int n, bool fwd, fhe_stream stream, const char *fn) {
+  if (!c) return fhe_fail(FHE_EINVAL, "%s: null ctx", fn);
+  CHECK(check_ptr(a, fn, "a"));
+  if (n < 0 || (n > 0 && !idx)) return fhe_fail(FHE_EINVAL, "%s: bad prime list", fn);
+  for (int i = 0; i < n; i++)
+    if (idx[i] < 0 || idx[i] >= c->L + c->K) return fhe_fail(FHE_EINVAL, "%s: prime index %d out of range", fn, idx[i]);
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->order_stream(s);
+  const size_t N = c->N;
+  int i = 0;
+  while (i < n) {
+    SegBuilder sb;
+    while (i < n && sb.l.nseg < kMaxSeg) {
+      int j = i + 1;
+      while (j < n && idx[j] == idx[j - 1] + 1) j++;
+      sb.add(mkseg(a + (size_t)i * N, a + (size_t)i * N, j - i, idx[i]));
+      i = j;
+    }
+    LAUNCH_OR_FAIL(launch_ntt(c->tabs, fwd, PRO_PLAIN, fwd ? EPI_PLAIN : EPI_SCALE, sb.l, sb.l,
+                              ks_base(nullptr, nullptr, nullptr), s));
+  }
+  return FHE_OK;
+}
+
+extern "C" int fhe_ntt(fhe_ctx *c, uint32_t *a, const int *idx, int n, fhe_stream stream) {
+  return transform(c, a, idx, n, true, stream, "fhe_ntt");
+}
+extern "C" int fhe_intt(fhe_ctx *c, uint32_t *a, const int *idx, int n, fhe_stream stream) {
+  return transform(c, a, idx, n, false, stream, "fhe_intt");
+}
+
+extern "C" int fhe_modup(fhe_ctx *c, const uint32_t *d, int level, uint32_t *ext, fhe_stream stream) {
+  if (!c) return fhe_fail(FHE_EINVAL, "fhe_modup: null ctx");
+  CHECK(check_level(c, level, "fhe_modup"));
+  CHECK(check_ptr(d, "fhe_modup", "d"));
+  CHECK(check_ptr(ext, "fhe_modup", "ext"));
+  const size_t N = c->N;
+  const int n_ext = level + c->K, beta = c->beta(level);
+  if (overlaps(d, 4 * N * level, ext, 4 * N * (size_t)beta * n_ext)) return fhe_fail(FHE_EALIAS, "fhe_modup: ext overlaps d");
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->order_stream(s);
+  CHECK(run_modup(c, d, level, 1u, ext, s));
+  for (int j = 0; j < beta; j++) {
+    const int lo = j * c->alpha, hi = std::min((j + 1) * c->alpha, level);
+    if (cudaMemcpyAsync(ext + ((size_t)j * n_ext + lo) * N, d + (size_t)lo * N, 4 * N * (hi - lo),
+                        cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return fhe_fail(FHE_ECUDA, "fhe_modup: copy");
+  }
+  return FHE_OK;
+}
+
+extern "C" int fhe_moddown(fhe_ctx *c, const uint32_t *u, int level, uint32_t *out, fhe_stream stream) {
+  if (!c) return fhe_fail(FHE_EINVAL, "fhe_moddown: null ctx");
+  CHECK(check_level(c, level, "fhe_moddown"));
+  CHECK(check_ptr(u, "fhe_moddown", "u"));
+  CHECK(check_ptr(out, "fhe_moddown", "out"));
+  const size_t N = c->N;
+  const int K = c->K, L = c->L;
+  if (overlaps(u, 4 * N * (level + K), out, 4 * N * level)) return fhe_fail(FHE_EALIAS, "fhe_moddown: out overlaps u");
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->order_stream(s);
+  KsArgs ks = ks_base(nullptr, nullptr, nullptr);
+  ks.pinv = c->d_pinv;
+  ks.level = level;
+  SegBuilder first, second, nr, cb;
+  first.add(mkseg(u + (size_t)level * N, c->wUC, K, L));
+  Seg b = mkseg(c->wUC, c->wUC, K, L);
+  b.scale = c->d_md_scale;
+  second.add(b);
+  LAUNCH_OR_FAIL(launch_ntt(c->tabs, false, PRO_PLAIN, EPI_SCALE, first.l, second.l, ks, s));
+  BconvArgs ba;
+  memset(&ba, 0, sizeof ba);
+  BconvGroup &g = ba.g[ba.ngroups++];
+  g.in = c->wUC;
+  g.out = c->wR;
+  g.T = c->d_mdT;
+  g.omap = c->d_mdmap;
+  g.n_in = K;
+  g.n_out = level;
+  if (c->bconv_mode == FHE_BCONV_TC)
+    LAUNCH_OR_FAIL(launch_bconv_tc(c->tabs, ba, K, s));
+  else
+    LAUNCH_OR_FAIL(launch_bconv(c->tabs, ba, K, s));
+  nr.add(mkseg(c->wR, c->wR, level, 0));
+  LAUNCH_OR_FAIL(launch_ntt(c->tabs, true, PRO_PLAIN, EPI_PLAIN, nr.l, nr.l, ks, s));
+  Seg x = mkseg(u, out, level, 0);
+  x.src2 = c->wR;
+  cb.add(x);
+  LAUNCH_OR_FAIL(launch_ew(c->tabs, EW_COMBINE, cb.l, ks, s));
+  return FHE_OK;
+}
+
+extern "C" int fhe_bconv(fhe_ctx *c, const uint32_t *in, const int *in_idx, int n_in, uint32_t *out,
+                         const int *out_idx, int n_out, fhe_stream stream) {
+  if (!c) return fhe_fail(FHE_EINVAL, "fhe_bconv: null ctx");
+  CHECK(check_ptr(in, "fhe_bconv", "in"));
+  CHECK(check_ptr(out, "fhe_bconv", "out"));
+  if (n_in < 1 || n_in > 32 || n_out < 1 || n_out > 64 || !in_idx || !out_idx)
+    return fhe_fail(FHE_EINVAL, "fhe_bconv: n_in=%d (1..32), n_out=%d (1..64)", n_in, n_out);
+  const int NP = c->L + c->K;
+  for (int i = 0; i < n_in; i++)
+    if (in_idx[i] < 0 || in_idx[i] >= NP) return fhe_fail(FHE_EINVAL, "fhe_bconv: in prime index");
+  for (int i = 0; i < n_out; i++)
+    if (out_idx[i] < 0 || out_idx[i] >= NP) return fhe_fail(FHE_EINVAL, "fhe_bconv: out prime index");
+  const size_t N = c->N;
+  if (overlaps(in, 4 * N * n_in, out, 4 * N * n_out)) return fhe_fail(FHE_EALIAS, "fhe_bconv: out overlaps in");
+  const std::vector<uint32_t> &pr = c->primes;
+  // host tables: pre-factor (Qstar/q_j)^-1 mod q_j and T[o][j] = (Qstar/q_j) mod p_o
+  std::vector<uint2> pre(n_in);
+  for (int j = 0; j < n_in; j++) {
+    const uint32_t q = pr[in_idx[j]];
+    uint32_t prod = 1;
+    for (int k = 0; k < n_in; k++)
+      if (k != j) prod = h_mulmod_pub(prod, pr[in_idx[k]] % q, q);
+    pre[j] = make_uint2(h_invmod_pub(prod, q), (uint32_t)(((uint64_t)h_invmod_pub(prod, q) << 32) / q));
+  }
+  std::vector<uint32_t> T((size_t)n_out * n_in);
+  std::vector<int2> om(n_out);
+  for (int o = 0; o < n_out; o++) {
+    const uint32_t p = pr[out_idx[o]];
+    for (int j = 0; j < n_in; j++) {
+      uint32_t prod = 1;
+      for (int k = 0; k < n_in; k++)
+        if (k != j) prod = h_mulmod_pub(prod, pr[in_idx[k]] % p, p);
+      T[(size_t)o * n_in + j] = prod;
+    }
+    om[o] = make_int2(o, out_idx[o]);
+  }
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->order_stream(s);
+  uint32_t *dT = nullptr, *y = nullptr;
+  int2 *dM = nullptr;
+  uint2 *dPre = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(dT);
+    cudaFree(dM);
+    cudaFree(dPre);
+    cudaFree(y);
+  };
+  if (cudaMalloc(&dT, 4 * T.size()) != cudaSuccess || cudaMalloc(&dM, 8 * om.size()) != cudaSuccess ||
+      cudaMalloc(&dPre, 8 * pre.size()) != cudaSuccess || cudaMalloc(&y, 4 * N * n_in) != cudaSuccess) {
+    cleanup();
+    return fhe_fail(FHE_ENOMEM, "fhe_bconv: temporary tables");
+  }
+  cudaMemcpy(dT, T.data(), 4 * T.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(dM, om.data(), 8 * om.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(dPre, pre.data(), 8 * pre.size(), cudaMemcpyHostToDevice);
+  // pre-multiply limb by limb (each limb its own prime: one segment per limb)
+  int rc = FHE_OK;
+  for (int j0 = 0; j0 < n_in && rc == FHE_OK; j0 += kMaxSeg) {
+    SegBuilder sb;
+    for (int j = j0; j < std::min(n_in, j0 + kMaxSeg); j++) {
+      Seg x = mkseg(in + (size_t)j * N, y + (size_t)j * N, 1, in_idx[j]);
+      x.scale = dPre + j;
+      sb.add(x);
+    }
+    if (launch_ew(c->tabs, EW_SCALE, sb.l, ks_base(nullptr, nullptr, nullptr), s) != cudaSuccess)
+      rc = fhe_fail(FHE_ECUDA, "fhe_bconv: scale");
+  }
+  BconvArgs ba;
+  memset(&ba, 0, sizeof ba);
+  BconvGroup &g = ba.g[ba.ngroups++];
+  g.in = y;
+  g.out = out;
+  g.T = dT;
+  g.omap = dM;
+  g.n_in = n_in;
+  g.n_out = n_out;
+  if (rc == FHE_OK) {
+    cudaError_t e = c->bconv_mode == FHE_BCONV_TC ? launch_bconv_tc(c->tabs, ba, n_in, s) : launch_bconv(c->tabs, ba, n_in, s);
+    if (e != cudaSuccess) rc = fhe_fail(FHE_ECUDA, "fhe_bconv: %s", cudaGetErrorString(e));
+  }
+  // the temporary tables are released once the stream has consumed them
+  if (cudaStreamSynchronize(s) != cudaSuccess && rc == FHE_OK) rc = fhe_fail(FHE_ECUDA, "fhe_bconv: sync");
+  cleanup();
+  return rc;
+}
