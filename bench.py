@@ -1,0 +1,375 @@
+#!/usr/bin/env python3
+"""Benchmark: hybrid key switches per second for HRotate at N = 2^16, L = 24.
+
+Workload (one "step"): a batch of B independent HRotates at N = 2^16, level
+24, K = 8 special primes, dnum = 3, each on its own ciphertext with its own
+rotation key (uniform residues, rotation index uniform in [1, 2^15)).  The B
+distinct ciphertext + key pairs (~503 MB at B = 8) are larger than the 129 MB
+L2, so every step streams its keys from HBM.  The headline `value` replays the
+batch as one captured CUDA graph (fused pipeline); the plain per-kernel
+pipeline and the fused pipeline without a graph are timed on the same inputs
+and reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+N > 1 runs one process per GPU under torchrun (each rank its own batch: the
+key switches are independent, so ranks share nothing; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "hrotate_N65536_L24_plain"
+METRIC = "key-switches/s at N=2^16,L=24 (HRotate, batched+graph)"
+UNIT = "key-switches/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device, self.proc, self.lines = device, None, []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            v = [x.strip() for x in ln.split(",")]
+            if len(v) < 9:
+                continue
+            try:
+                sm.append(float(v[1]))
+                mx = max(mx, float(v[2]))
+            except ValueError:
+                continue
+            for n, flag in zip(names, v[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- reference arm: the CPU oracle
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from paper_2512_18345_gb300 import inputs
+    P = inputs.workload_params(WORKLOAD)
+    OP = oracle.OracleParams.from_params(P)
+    cores = os.cpu_count() or 1
+    oracle.set_num_threads(cores)
+    g = inputs.rng(inputs.WORKLOADS[WORKLOAD]["seed"])
+    level = P.L
+    ct = np.stack([inputs.uniform_residues(g, P.q, P.N) for _ in range(2)])
+    key = np.stack([np.stack([inputs.uniform_residues(g, P.primes, P.N) for _ in range(2)]) for _ in range(P.dnum)])
+    rot = inputs.rotation_index(g)
+    for _ in range(min(args.warmup, 1)):
+        oracle.rotate(OP, ct, level, rot, key)
+    budget, done, t0 = 120.0, 0, time.perf_counter()
+    while done < args.steps:
+        oracle.rotate(OP, ct, level, rot, key)
+        done += 1
+        if time.perf_counter() - t0 > budget:
+            break
+    dt = time.perf_counter() - t0
+    value = done / dt
+    sample = f"{done} full HRotates (N=2^16, L=24, K=8, dnum=3) of {args.steps} requested, {cores} threads"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": done,
+        "warmup": min(args.warmup, 1), "ms_per_step": dt / done * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "HRotate N=2^16 L=24 K=8 dnum=3 (CPU oracle)", "N": P.N, "L": P.L, "K": P.K,
+                   "dnum": P.dnum, "batch": 1},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(P, ct_np, key_np, rot, budget_s=12.0):
+    """The oracle as it stands, one HRotate at a time on all host cores, ~budget_s of work."""
+    import oracle
+    OP = oracle.OracleParams.from_params(P)
+    cores = os.cpu_count() or 1
+    oracle.set_num_threads(cores)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        oracle.rotate(OP, ct_np, P.L, rot, key_np)
+        done += 1
+        if time.perf_counter() - t0 > budget_s or done >= 50:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{done} HRotates at N=2^16, L=24 (one workload item each), {dt:.1f} s"}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    import numpy as np
+    import torch
+    from paper_2512_18345_gb300 import binding, build, inputs, roofline
+
+    build.build_library()
+    dev = local
+    torch.cuda.set_device(dev)
+    P = inputs.workload_params(WORKLOAD)
+    level, B = P.L, args.batch
+    g = inputs.rng(inputs.WORKLOADS[WORKLOAD]["seed"] + 1000 * rank)
+    ctx = binding.Context.from_params(P, device=dev)
+    cts_np, keys_np, rots = [], [], []
+    used = set()
+    for b in range(B):
+        r = inputs.rotation_index(g)
+        while pow(5, r % (P.N // 2), 2 * P.N) in used:
+            r = inputs.rotation_index(g)
+        used.add(pow(5, r % (P.N // 2), 2 * P.N))
+        rots.append(r)
+        cts_np.append(np.stack([inputs.uniform_residues(g, P.q, P.N) for _ in range(2)]))
+        keys_np.append(np.stack([np.stack([inputs.uniform_residues(g, P.primes, P.N) for _ in range(2)])
+                                 for _ in range(P.dnum)]))
+    cts = [binding.to_device(c, dev) for c in cts_np]
+    for r, k in zip(rots, keys_np):
+        ctx.set_rot_key(r, binding.to_device(k, dev))
+    outs = [binding.empty((2, level, P.N), dev) for _ in range(B)]
+    items = [dict(op=binding.FHE_OP_ROTATE, level=level, rot=r, **{"in": c}, out=o) for r, c, o in zip(rots, cts, outs)]
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps):
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        ms = e0.elapsed_time(e1)
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms], device=f"cuda:{dev}")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    # --- headline: fused pipeline, batch captured in one CUDA graph
+    ctx.set_fused(True)
+    plan = ctx.batch_plan(items, binding.FHE_PLAN_GRAPH)
+    for _ in range(max(3, args.warmup)):
+        plan.launch()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.15)
+    ms = timed(plan.launch, args.steps)
+    clk = clocks.stop()
+    ks_total = B * args.steps * ws
+    value = ks_total / (ms / 1e3)
+    graph_kernels = plan.kernel_count
+
+    # --- comparison paths on the same inputs (fewer steps)
+    cmp_steps = max(3, min(args.steps, 50))
+
+    def direct():
+        for it in items:
+            ctx.rotate(it["in"], level, it["rot"], out=it["out"])
+
+    for _ in range(3):
+        direct()
+    ms_fused = timed(direct, cmp_steps)
+    ctx.set_fused(False)
+    for _ in range(3):
+        direct()
+    ms_plain = timed(direct, cmp_steps)
+    ctx.set_fused(True)
+    plain_ks = B * cmp_steps * ws / (ms_plain / 1e3)
+    fused_ks = B * cmp_steps * ws / (ms_fused / 1e3)
+
+    # --- per-kernel times (CUDA events around each launch on its stream), fused direct path
+    ctx.trace(True)
+    for _ in range(cmp_steps):
+        direct()
+    stats = ctx.trace_read()
+    ctx.trace(False)
+    total_ms = sum(v[1] for v in stats.values())
+    top_name, (top_n, top_ms) = max(stats.items(), key=lambda kv: kv[1][1])
+    per_launch_ms = top_ms / top_n
+
+    # --- L2 bandwidth (read + write of a 32 MB block, as in the paper's method) and peaks
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    blk = torch.empty(8 << 20, dtype=torch.int32, device=f"cuda:{dev}")
+    blk2 = torch.empty_like(blk)
+    for _ in range(5):
+        blk2.copy_(blk)
+    l2_ms = timed(lambda: blk2.copy_(blk), 200)
+    l2_gbs = 2 * blk.numel() * 4 * 200 / (l2_ms / 1e3) / 1e9
+
+    # algorithmic bytes of the headline step and its L2-roofline fraction (paper's definition)
+    bks = roofline.ks_bytes(P.N, level, P.K, P.alpha)
+    l2_frac = (bks / (l2_gbs * 1e9)) / ((ms / 1e3) / (B * args.steps))
+
+    # dominant kernel: algorithmic bytes per launch and butterflies per launch
+    W = 4 * P.N
+    beta = P.beta(level)
+    conv = beta * (level + P.K) - level
+    # limbs one launch of each kernel transforms (ModUp and ModDown launches of one name averaged)
+    limbs = {"intt_blk+gather": level, "intt_col+scale": (level + 2 * P.K) / 2.0, "ntt_col": (conv + 2 * level) / 2.0,
+             "ntt_blk": conv, "intt_blk+ip": 2 * P.K, "ntt_blk+combine": 2 * level}
+    n_l = limbs.get(top_name, level)
+    half = 8 if top_name.endswith(("blk", "blk+gather", "blk+ip", "blk+combine")) else P.N.bit_length() - 1 - 8
+    bfly = n_l * (P.N // 2) * half
+    traffic_bytes = 2 * n_l * W
+    achieved_gbs = traffic_bytes / (per_launch_ms / 1e3) / 1e9
+    sm_clock_ghz = (clk["sm_mhz"] if clk else 1900.0) / 1e3
+    # ALU peak: a Shoup radix-2 butterfly needs >= 4 IMAD-pipe issue cycles (IMAD.HI is half rate),
+    # 64 IMAD lanes per SM per clock -> 16 butterflies / clock / SM
+    alu_peak = 16 * 152 * 2.07e9 / 1e12  # T butterflies/s at the maximum SM clock
+    alu_ach = bfly / (per_launch_ms / 1e3) / 1e12
+    if alu_ach / alu_peak >= achieved_gbs / hbm_peak:
+        roof = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "Tbutterfly/s",
+                "frac": alu_ach / alu_peak, "traffic": None, "kernel": top_name,
+                "peak_source": "derived: 16 Shoup butterflies/clk/SM x 152 SMs x 2.07 GHz",
+                "achieved_l2_gbs": achieved_gbs}
+    else:
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved_gbs / hbm_peak, "traffic": None, "kernel": top_name, "peak_source": "measured"}
+    roof["launch_ms"] = per_launch_ms
+    roof["share"] = top_ms / total_ms if total_ms else None
+
+    # --- e2e: host pinned buffers, copies inside the timed region, same public API
+    h_in = [torch.from_numpy(c.view(np.int32)).pin_memory() for c in cts_np]
+    h_out = [torch.empty((2, level, P.N), dtype=torch.int32).pin_memory() for _ in range(B)]
+
+    def e2e_step():
+        for hi, di in zip(h_in, cts):
+            di.copy_(hi, non_blocking=True)
+        plan.launch()
+        for ho, do in zip(h_out, outs):
+            ho.copy_(do, non_blocking=True)
+
+    e2e_steps = max(3, min(args.steps, 50))
+    for _ in range(2):
+        e2e_step()
+    ms_e2e = timed(e2e_step, e2e_steps)
+    e2e_val = B * e2e_steps * ws / (ms_e2e / 1e3)
+    bytes_io = B * 2 * level * P.N * 4
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_baseline(P, cts_np[0], keys_np[0], rots[0])
+        except Exception as ex:  # the oracle is optional on a box without a C compiler
+            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {ex}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"HRotate x{B} per step, N=2^16 L=24 K=8 dnum=3", "N": P.N, "L": level,
+                       "K": P.K, "dnum": P.dnum, "batch_per_gpu": B,
+                       "l2": f"inputs larger than L2: {B} distinct ciphertext+key pairs, "
+                             f"{B * (2 * level + 2 * P.dnum * (P.L + P.K)) * P.N * 4 / 1e6:.0f} MB per step",
+                       "path": "fused pipeline, batch captured in one CUDA graph"},
+            "gpu_launches": graph_kernels * args.steps,
+            "clocks": clk,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "l2_roofline": {"bytes_per_ks": bks, "l2_gbs_measured": l2_gbs, "frac": l2_frac,
+                            "definition": "B_KS(l) / measured L2 read+write bandwidth / time per key switch"},
+            "paths": {"graph_fused": value, "direct_fused": fused_ks, "plain_per_kernel": plain_ks},
+            "kernels": {k: {"launches": v[0], "ms": v[1], "share": v[1] / total_ms} for k, v in
+                        sorted(stats.items(), key=lambda kv: -kv[1][1])},
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -176,7 +176,7 @@ FHE_API int fhe_add(fhe_ctx *ctx, const uint32_t *a, const uint32_t *b, int npol
  *   fhe_bconv: coefficient-form fast base conversion of in [n_in][N] (primes
  *     in_idx) to out [n_out][N] (primes out_idx), Section II-B "BConv" with the
  *     table T[i][j] = (Qstar / q_j) mod p_i of Section III-C and the
- *     [(Qstar / q_j)^-1]_{q_j} pre-multiplication; n_in <= 32, n_out <= 64.
+ *     [(Qstar / q_j)^-1]_{q_j} pre-multiplication; n_in <= 16, n_out <= 64.
  */
 FHE_API int fhe_ntt(fhe_ctx *ctx, uint32_t *a, const int *prime_idx, int n, fhe_stream stream);
 FHE_API int fhe_intt(fhe_ctx *ctx, uint32_t *a, const int *prime_idx, int n, fhe_stream stream);
@@ -212,6 +212,21 @@ FHE_API int fhe_batch_launch(fhe_plan *plan, fhe_stream stream);
 FHE_API int fhe_plan_destroy(fhe_plan *plan);
 /* number of kernel launches one fhe_batch_launch performs (graph nodes or direct launches) */
 FHE_API int fhe_plan_kernel_count(const fhe_plan *plan);
+
+/*
+ * Kernel tracing (measurement support): while enabled, every kernel the
+ * context launches outside a captured plan is bracketed by two CUDA events on
+ * its stream.  fhe_trace_read synchronizes the device, returns per-kernel-name
+ * launch counts and summed event times (at most `max` entries, *n = number of
+ * distinct names) and clears the record.
+ */
+typedef struct {
+  char name[48];
+  int launches;
+  double total_ms;
+} fhe_kernel_stat;
+FHE_API int fhe_trace_enable(fhe_ctx *ctx, int on);
+FHE_API int fhe_trace_read(fhe_ctx *ctx, fhe_kernel_stat *out, int max, int *n);
 
 FHE_API const char *fhe_last_error(void);
 

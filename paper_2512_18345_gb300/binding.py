@@ -30,7 +30,7 @@ EXPORTS = (
     "fhe_set_relin_key", "fhe_set_rot_key", "fhe_keyswitch", "fhe_rotate", "fhe_hmult", "fhe_rescale",
     "fhe_rotate_hoisted", "fhe_pmult", "fhe_add", "fhe_ntt", "fhe_intt", "fhe_modup", "fhe_moddown",
     "fhe_bconv", "fhe_batch_plan", "fhe_batch_launch", "fhe_plan_destroy", "fhe_plan_kernel_count",
-    "fhe_last_error",
+    "fhe_trace_enable", "fhe_trace_read", "fhe_last_error",
 )
 
 
@@ -46,6 +46,10 @@ class FheInfo(ctypes.Structure):
                 ("key_bytes", ctypes.c_size_t), ("workspace_bytes", ctypes.c_size_t),
                 ("table_bytes", ctypes.c_size_t), ("n_rot_keys", ctypes.c_int), ("bconv_mode", ctypes.c_int),
                 ("psi", ctypes.c_uint32 * 64)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int), ("total_ms", ctypes.c_double)]
 
 
 class KsItem(ctypes.Structure):
@@ -99,6 +103,8 @@ def lib() -> ctypes.CDLL:
         "fhe_batch_launch": [vp, vp],
         "fhe_plan_destroy": [vp],
         "fhe_plan_kernel_count": [vp],
+        "fhe_trace_enable": [vp, ctypes.c_int],
+        "fhe_trace_read": [vp, ctypes.POINTER(KernelStat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
         "fhe_last_error": [],
     }
     for name, args in sig.items():
@@ -217,6 +223,16 @@ class Context:
 
     def set_fused(self, fused: bool) -> None:
         check(lib().fhe_ctx_set_fused(self.h, int(bool(fused))))
+
+    def trace(self, on: bool) -> None:
+        check(lib().fhe_trace_enable(self.h, int(bool(on))))
+
+    def trace_read(self) -> dict:
+        """{kernel name: (launches, total ms)} since the last read (synchronizes)."""
+        arr = (KernelStat * 64)()
+        n = ctypes.c_int()
+        check(lib().fhe_trace_read(self.h, arr, 64, ctypes.byref(n)))
+        return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms) for i in range(min(n.value, 64))}
 
     def set_relin_key(self, key, stream=None) -> None:
         check(lib().fhe_set_relin_key(self.h, _ptr(key), _stream(stream)))

@@ -56,6 +56,8 @@ extern "C" int fhe_batch_plan(fhe_ctx *c, const fhe_ks_item *items, int n, int f
     }
     // the capture must not race with work already queued on this context
     if (c->have_last) cudaStreamSynchronize(c->last_stream);
+    fhe::Tracer *saved_tracer = c->tabs.tracer;
+    c->tabs.tracer = nullptr;  // no trace events inside a captured graph
     c->capturing = true;
     int rc = FHE_OK;
     if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
@@ -64,6 +66,7 @@ extern "C" int fhe_batch_plan(fhe_ctx *c, const fhe_ks_item *items, int n, int f
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &g);
     c->capturing = false;
+    c->tabs.tracer = saved_tracer;
     if (rc == FHE_OK && e != cudaSuccess) rc = fhe_fail(FHE_ECUDA, "fhe_batch_plan: end capture: %s", cudaGetErrorString(e));
     if (rc == FHE_OK && cudaGraphInstantiate(&p->exec, g, 0) != cudaSuccess)
       rc = fhe_fail(FHE_ECUDA, "fhe_batch_plan: instantiate");

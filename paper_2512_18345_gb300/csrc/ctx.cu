@@ -240,6 +240,7 @@ static int build_tables(fhe_ctx *c) {
   c->tabs.ntt.ninv = c->d_ninv;
   c->tabs.pc = c->d_pc;
   c->tabs.logn = c->logn;
+  c->tabs.tracer = nullptr;
   return FHE_OK;
 }
 
@@ -290,6 +291,9 @@ fhe_ctx::~fhe_ctx() {
   for (auto &kv : rot_keys) cudaFree(kv.second);
   for (auto p : scratch_tabs) cudaFree(p);
   if (order_ev) cudaEventDestroy(order_ev);
+  if (ev_fork) cudaEventDestroy(ev_fork);
+  if (ev_join) cudaEventDestroy(ev_join);
+  if (aux) cudaStreamDestroy(aux);
   if (prev >= 0) cudaSetDevice(prev);
 }
 
@@ -304,8 +308,8 @@ extern "C" int fhe_ctx_create(fhe_ctx **out, uint32_t N, const uint32_t *q, int 
     return fhe_fail(FHE_EINVAL, "fhe_ctx_create: L=%d K=%d (need L,K >= 1, L+K <= %d)", L, K, FHE_MAX_PRIMES);
   if (dnum < 1 || dnum > L) return fhe_fail(FHE_EINVAL, "fhe_ctx_create: dnum=%d outside [1, L=%d]", dnum, L);
   const int alpha = ceil_div(L, dnum);
-  if (alpha > 32 || K > 32)
-    return fhe_fail(FHE_EUNSUPPORTED, "fhe_ctx_create: alpha=%d, K=%d (base conversion supports <= 32 inputs)", alpha, K);
+  if (alpha > 16 || K > 16)
+    return fhe_fail(FHE_EUNSUPPORTED, "fhe_ctx_create: alpha=%d, K=%d (base conversion supports <= 16 inputs)", alpha, K);
   if (ceil_div(L, alpha) > 4)
     return fhe_fail(FHE_EUNSUPPORTED, "fhe_ctx_create: beta=%d digits (inner product supports <= 4)", ceil_div(L, alpha));
   if (L + K - 1 > 64 || L > 64) return fhe_fail(FHE_EUNSUPPORTED, "fhe_ctx_create: too many limbs");
@@ -335,8 +339,11 @@ extern "C" int fhe_ctx_create(fhe_ctx **out, uint32_t N, const uint32_t *q, int 
   c->primes = pr;
   int rc = build_tables(c);
   if (rc == FHE_OK) rc = alloc_workspace(c);
-  if (rc == FHE_OK && cudaEventCreateWithFlags(&c->order_ev, cudaEventDisableTiming) != cudaSuccess)
-    rc = fhe_fail(FHE_ECUDA, "fhe_ctx_create: event");
+  if (rc == FHE_OK && (cudaEventCreateWithFlags(&c->order_ev, cudaEventDisableTiming) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+                       cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess))
+    rc = fhe_fail(FHE_ECUDA, "fhe_ctx_create: events / auxiliary stream");
   if (rc == FHE_OK) {
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) rc = fhe_fail(FHE_ECUDA, "fhe_ctx_create: %s", cudaGetErrorString(e));
@@ -383,6 +390,39 @@ extern "C" int fhe_ctx_set_bconv(fhe_ctx *c, int mode) {
   if (mode == FHE_BCONV_TC && !fhe_tc_available())
     return fhe_fail(FHE_EUNSUPPORTED, "fhe_ctx_set_bconv: tensor-core base conversion not built");
   c->bconv_mode = mode;
+  return FHE_OK;
+}
+
+extern "C" int fhe_trace_enable(fhe_ctx *c, int on) {
+  if (!c) return fhe_fail(FHE_EINVAL, "fhe_trace_enable: null");
+  if (c->capturing) return fhe_fail(FHE_EINVAL, "fhe_trace_enable: a plan is being captured");
+  c->tabs.tracer = on ? &c->tracer : nullptr;
+  return FHE_OK;
+}
+
+extern "C" int fhe_trace_read(fhe_ctx *c, fhe_kernel_stat *out, int max, int *n) {
+  if (!c || !n || (max > 0 && !out)) return fhe_fail(FHE_EINVAL, "fhe_trace_read: bad arguments");
+  cudaSetDevice(c->device);
+  CUDA_OR_FAIL(cudaDeviceSynchronize());
+  std::vector<fhe_kernel_stat> agg;
+  for (const auto &r : c->tracer.recs) {
+    float ms = 0.f;
+    CUDA_OR_FAIL(cudaEventElapsedTime(&ms, r.a, r.b));
+    size_t i = 0;
+    for (; i < agg.size(); i++)
+      if (!strncmp(agg[i].name, r.name, sizeof agg[i].name)) break;
+    if (i == agg.size()) {
+      fhe_kernel_stat z;
+      memset(&z, 0, sizeof z);
+      strncpy(z.name, r.name, sizeof z.name - 1);
+      agg.push_back(z);
+    }
+    agg[i].launches++;
+    agg[i].total_ms += ms;
+  }
+  c->tracer.reset();
+  *n = (int)agg.size();
+  for (int i = 0; i < max && i < (int)agg.size(); i++) out[i] = agg[i];
   return FHE_OK;
 }
 

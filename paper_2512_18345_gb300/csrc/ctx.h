@@ -32,6 +32,7 @@ struct fhe_ctx {
   std::vector<void *> scratch_tabs;                    // tables built for fhe_bconv calls
   size_t table_bytes = 0;
   fhe::DevTables tabs{};
+  fhe::Tracer tracer;
 
   // keys
   uint32_t *relin_key = nullptr;
@@ -48,6 +49,8 @@ struct fhe_ctx {
   bool have_last = false;
   bool capturing = false;  // a batched plan is being captured: no cross-stream ordering
   cudaEvent_t order_ev = nullptr;
+  cudaStream_t aux = nullptr;  // concurrent branch of the fused pipeline
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
   int beta(int level) const;
   int ext_prime(int level, int t) const;

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "bconv.cuh"
 #include "common.cuh"
@@ -10,10 +11,28 @@
 
 namespace fhe {
 
+// Optional per-launch timing: each kernel launch is bracketed by two CUDA events
+// on its stream and recorded under the kernel's name.
+struct TraceRec {
+  const char *name;
+  cudaEvent_t a, b;
+};
+struct Tracer {
+  std::vector<TraceRec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  cudaEvent_t get();
+  void begin(const char *name, cudaStream_t s);
+  void end(cudaStream_t s);
+  void reset() { recs.clear(); used = 0; }
+  ~Tracer();
+};
+
 struct DevTables {
   NttTables ntt;
   const PrimeC *pc;
   int logn;
+  Tracer *tracer;  // null: no tracing
 };
 
 // One NTT pass over every limb of `sl` (column or block pass, forward or inverse).
@@ -26,6 +45,8 @@ cudaError_t launch_ntt(const DevTables &t, bool fwd, int pro, int epi, const Seg
 cudaError_t launch_bconv(const DevTables &t, const BconvArgs &a, int max_in, cudaStream_t s);
 cudaError_t launch_bconv_tc(const DevTables &t, const BconvArgs &a, int max_in, cudaStream_t s);
 cudaError_t launch_ew(const DevTables &t, int op, const SegList &sl, const KsArgs &ks, cudaStream_t s);
+// key inner product (both halves) for the ext limbs of sl; seg.dst = u_0[t0]
+cudaError_t launch_ip(const DevTables &t, const SegList &sl, const KsArgs &ks, cudaStream_t s);
 cudaError_t launch_tensor(const DevTables &t, const uint32_t *a, const uint32_t *b, uint32_t *d, int level,
                           cudaStream_t s);
 

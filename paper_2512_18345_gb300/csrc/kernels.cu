@@ -1,5 +1,6 @@
 // Kernel instantiations and launch wrappers.
 #include <atomic>
+#include <cstdio>
 
 #include "bconv.cuh"
 #include "elementwise.cuh"
@@ -37,11 +38,55 @@ __global__ void __launch_bounds__(kEwThreads) k_tensor(const uint32_t *a, const 
 static std::atomic<long long> g_launches{0};
 long long kernel_launches() { return g_launches.load(); }
 
+cudaEvent_t Tracer::get() {
+  if (used == pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    pool.push_back(e);
+  }
+  return pool[used++];
+}
+void Tracer::begin(const char *name, cudaStream_t s) {
+  TraceRec r{name, get(), get()};
+  cudaEventRecord(r.a, s);
+  recs.push_back(r);
+}
+void Tracer::end(cudaStream_t s) { cudaEventRecord(recs.back().b, s); }
+Tracer::~Tracer() {
+  for (auto e : pool) cudaEventDestroy(e);
+}
+
+// bracket one launch with trace events when tracing is on
+struct TraceScope {
+  Tracer *t;
+  cudaStream_t s;
+  TraceScope(const DevTables &tb, const char *name, cudaStream_t st) : t(tb.tracer), s(st) {
+    if (t) t->begin(name, s);
+  }
+  ~TraceScope() {
+    if (t) t->end(s);
+  }
+};
+
+template <int LOGN, bool COLUMN, bool FWD, int PRO, int EPI>
+static const char *ntt_name() {
+  static const char *pro[] = {"", "+gather", "+reduce"};
+  static const char *epi[] = {"", "", "+scale", "+combine", "+rescale"};
+  static char buf[64];
+  static bool init = false;
+  if (!init) {
+    snprintf(buf, sizeof buf, "%s_%s%s%s", FWD ? "ntt" : "intt", COLUMN ? "col" : "blk", pro[PRO], epi[EPI]);
+    init = true;
+  }
+  return buf;
+}
+
 template <int LOGN, bool COLUMN, bool FWD, int PRO, int EPI>
 static cudaError_t ntt_go(const DevTables &t, const SegList &sl, const KsArgs &ks, cudaStream_t s) {
   using G = NttGeom<LOGN, COLUMN>;
   const unsigned grid = (unsigned)(sl.total * G::TILES);
   if (grid == 0) return cudaSuccess;
+  TraceScope ts(t, ntt_name<LOGN, COLUMN, FWD, PRO, EPI>(), s);
   k_ntt<LOGN, COLUMN, FWD, PRO, EPI><<<grid, kNttThreads, 0, s>>>(sl, t.ntt, ks);
   g_launches++;
   return cudaGetLastError();
@@ -60,7 +105,6 @@ static cudaError_t ntt_dispatch(const DevTables &t, bool column, bool fwd, int p
   NTT_CASE(false, true, PRO_PLAIN, EPI_RESCALE)
   NTT_CASE(false, false, PRO_PLAIN, EPI_LAZY)
   NTT_CASE(false, false, PRO_GATHER, EPI_LAZY)
-  NTT_CASE(false, false, PRO_IP, EPI_LAZY)
   NTT_CASE(true, false, PRO_PLAIN, EPI_SCALE)
 #undef NTT_CASE
   return cudaErrorInvalidValue;
@@ -87,13 +131,37 @@ cudaError_t launch_ntt(const DevTables &t, bool fwd, int pro, int epi, const Seg
 }
 
 cudaError_t launch_bconv(const DevTables &t, const BconvArgs &a, int max_in, cudaStream_t s) {
-  const dim3 grid((unsigned)((1u << t.logn) / kBconvThreads), (unsigned)a.ngroups);
   if (a.ngroups == 0) return cudaSuccess;
-  if (max_in <= 4) k_bconv<4><<<grid, kBconvThreads, 0, s>>>(a, t.pc, t.logn);
-  else if (max_in <= 8) k_bconv<8><<<grid, kBconvThreads, 0, s>>>(a, t.pc, t.logn);
-  else if (max_in <= 16) k_bconv<16><<<grid, kBconvThreads, 0, s>>>(a, t.pc, t.logn);
-  else if (max_in <= 32) k_bconv<32><<<grid, kBconvThreads, 0, s>>>(a, t.pc, t.logn);
-  else return cudaErrorInvalidValue;
+  int max_out = 0;
+  for (int i = 0; i < a.ngroups && !a.dev; i++) max_out = a.g[i].n_out > max_out ? a.g[i].n_out : max_out;
+  if (a.dev) max_out = 64;
+  const dim3 grid((unsigned)((1u << t.logn) / (4 * kBconvThreads)), (unsigned)((max_out + kBconvOutChunk - 1) / kBconvOutChunk),
+                  (unsigned)a.ngroups);
+  TraceScope ts(t, "bconv", s);
+  switch (max_in) {
+#define BC(n) \
+  case n: k_bconv<n><<<grid, kBconvThreads, 0, s>>>(a, t.pc, t.logn); break;
+    BC(1) BC(2) BC(3) BC(4) BC(5) BC(6) BC(7) BC(8)
+#undef BC
+    default:
+      if (max_in <= 12) k_bconv<12><<<grid, kBconvThreads, 0, s>>>(a, t.pc, t.logn);
+      else if (max_in <= 16) k_bconv<16><<<grid, kBconvThreads, 0, s>>>(a, t.pc, t.logn);
+      else return cudaErrorInvalidValue;
+  }
+  g_launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ip(const DevTables &t, const SegList &sl, const KsArgs &ks, cudaStream_t s) {
+  const unsigned per_limb = (unsigned)((1u << t.logn) / (4 * kEwThreads));
+  const unsigned grid = (unsigned)sl.total * per_limb;
+  if (grid == 0) return cudaSuccess;
+  TraceScope ts(t, "inner_product", s);
+  const bool go = ks.galois_own != 1u, ge = ks.galois_ext != 1u;
+  if (go && ge) k_ip<true, true><<<grid, kEwThreads, 0, s>>>(sl, t.pc, ks, t.logn);
+  else if (go) k_ip<true, false><<<grid, kEwThreads, 0, s>>>(sl, t.pc, ks, t.logn);
+  else if (ge) k_ip<false, true><<<grid, kEwThreads, 0, s>>>(sl, t.pc, ks, t.logn);
+  else k_ip<false, false><<<grid, kEwThreads, 0, s>>>(sl, t.pc, ks, t.logn);
   g_launches++;
   return cudaGetLastError();
 }
@@ -102,10 +170,11 @@ cudaError_t launch_ew(const DevTables &t, int op, const SegList &sl, const KsArg
   const unsigned per_limb = (unsigned)((1u << t.logn) / (4 * kEwThreads));
   const unsigned grid = (unsigned)sl.total * per_limb;
   if (grid == 0) return cudaSuccess;
+  static const char *names[] = {"ew_gather", "ew_scale", "ew_ip", "ew_combine", "ew_add", "ew_mul", "ew_copy"};
+  TraceScope ts(t, op >= 0 && op < 7 ? names[op] : "ew", s);
   switch (op) {
     case EW_GATHER: k_ew<EW_GATHER><<<grid, kEwThreads, 0, s>>>(sl, t.pc, ks, t.logn); break;
     case EW_SCALE: k_ew<EW_SCALE><<<grid, kEwThreads, 0, s>>>(sl, t.pc, ks, t.logn); break;
-    case EW_IP: k_ew<EW_IP><<<grid, kEwThreads, 0, s>>>(sl, t.pc, ks, t.logn); break;
     case EW_COMBINE: k_ew<EW_COMBINE><<<grid, kEwThreads, 0, s>>>(sl, t.pc, ks, t.logn); break;
     case EW_ADD: k_ew<EW_ADD><<<grid, kEwThreads, 0, s>>>(sl, t.pc, ks, t.logn); break;
     case EW_MUL: k_ew<EW_MUL><<<grid, kEwThreads, 0, s>>>(sl, t.pc, ks, t.logn); break;
@@ -119,6 +188,7 @@ cudaError_t launch_ew(const DevTables &t, int op, const SegList &sl, const KsArg
 cudaError_t launch_tensor(const DevTables &t, const uint32_t *a, const uint32_t *b, uint32_t *d, int level,
                           cudaStream_t s) {
   const unsigned per_limb = (unsigned)((1u << t.logn) / (4 * kEwThreads));
+  TraceScope ts(t, "tensor", s);
   k_tensor<<<per_limb * (unsigned)level, kEwThreads, 0, s>>>(a, b, d, level, t.pc, t.logn);
   g_launches++;
   return cudaGetLastError();

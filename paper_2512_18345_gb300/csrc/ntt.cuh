@@ -32,34 +32,15 @@ enum : int {
   PRO_PLAIN = 0,   // src[j]
   PRO_GATHER = 1,  // src[sigma(j)], sigma = ks.galois_own (NTT form input)
   PRO_REDUCE = 2,  // src[j] reduced from another prime (rescale: src_prime)
-  PRO_IP = 3,      // fused inner product over the beta digits (ModDown special limbs)
 };
 // Epilogue modes (how the last pass writes an element)
 enum : int {
   EPI_LAZY = 0,     // write [0, 2q) (intermediate)
   EPI_PLAIN = 1,    // write reduced
   EPI_SCALE = 2,    // write v * scale (inverse final: N^-1 * constant)
-  EPI_COMBINE = 3,  // ModDown combine: (u - v) P^-1 (+ add), u from the fused inner product
+  EPI_COMBINE = 3,  // ModDown combine: (src2[j] - v) P^-1 (+ add), src2 = inner product u
   EPI_RESCALE = 4,  // (src2[j] - v) * scale
 };
-
-// Inner product of the beta extended digits with the key for extended limb t
-// (prime P) at coefficient j:  sum_jd E_jd[t][j] key[jd][c][row][j] mod q.
-__device__ __forceinline__ uint32_t fused_inner_product(const KsArgs &ks, int t, int row, int c, uint32_t j,
-                                                        const PrimeC &P, int logn) {
-  const size_t N = (size_t)1 << logn;
-  const uint32_t jo = ks.galois_own == 1u ? j : galois_src(j, ks.galois_own, logn);
-  const uint32_t je = ks.galois_ext == 1u ? j : galois_src(j, ks.galois_ext, logn);
-  const size_t kstride = (size_t)2 * (ks.L + ks.K) * N;  // between digits
-  const uint32_t *kp = ks.key + ((size_t)c * (ks.L + ks.K) + row) * N + j;
-  uint64_t acc = 0;  // beta <= 4 products of two 31-bit values: < 2^64
-  for (int jd = 0; jd < ks.beta; jd++) {
-    const bool own = t < ks.level && t >= jd * ks.alpha && t < (jd + 1) * ks.alpha;
-    const uint32_t e = own ? __ldg(ks.own + (size_t)t * N + jo) : __ldg(ks.ext + ((size_t)jd * ks.n_ext + t) * N + je);
-    acc += (uint64_t)e * __ldg(kp + jd * kstride);
-  }
-  return reduce_u64(acc, P);
-}
 
 template <int LOGN, bool COLUMN>
 struct NttGeom {
@@ -127,10 +108,8 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt(const __grid_constant__ Seg
       x = __ldg(src + j);
     } else if (PRO == PRO_GATHER) {
       x = __ldg(src + galois_src(j, ks.galois_own, LOGN));
-    } else if (PRO == PRO_REDUCE) {  // value of another prime's limb, reduced exactly mod q
+    } else {  // PRO_REDUCE: value of another prime's limb, reduced exactly mod q
       x = reduce_u64(__ldg(src + j), P);
-    } else {  // PRO_IP
-      x = fused_inner_product(ks, sg.t0 + within, sg.key_row0 + within, sg.c, j, P, LOGN);
     }
     sm[G::addr(c, k)] = x;
   }
@@ -221,9 +200,9 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt(const __grid_constant__ Seg
     } else if (EPI == EPI_RESCALE) {
       const uint32_t a = __ldg(sg.src2 + (size_t)within * N + j);
       o = shoup(a + q - red2(val, q), scale.x, scale.y, q);
-    } else {  // EPI_COMBINE: limb i = within-run index + t0 is a q-limb (< level)
+    } else {  // EPI_COMBINE: limb t = t0 + within is a q-limb (< level)
       const int t = sg.t0 + within;
-      const uint32_t u = fused_inner_product(ks, t, sg.key_row0 + within, sg.c, j, P, LOGN);
+      const uint32_t u = __ldg(sg.src2 + (size_t)within * N + j);
       o = shoup(u + q - red2(val, q), pinv.x, pinv.y, q);
       if (ks.addp && (sg.c == 0 || ks.add_c1)) {
         const uint32_t ja = ks.galois_add == 1u ? j : galois_src(j, ks.galois_add, LOGN);

@@ -3,14 +3,16 @@
 //
 // Stage 1 (ModUp): INTT of the input limbs, scaled by N^-1 (D_j/q_t)^-1 (the
 //   BConv pre-factor folded into the INTT output), base conversion of every
-//   digit to the limbs it lacks, NTT of the converted limbs.
-// Stage 2 + 3 (inner product, ModDown): the inner product with the key is
-//   computed for the K special limbs inside the INTT that starts ModDown, and
-//   for the l ciphertext limbs inside the epilogue of ModDown's last NTT,
-//   which also subtracts, multiplies by P^-1 and adds the pass-through
-//   polynomial (Section III-D: NTT(a1) + a2 + ... is fusable).  The inner
-//   product's (2, l) part thus never touches memory as a separate array.
-// The plain (unfused) pipeline runs every step as its own kernel.
+//   digit to the limbs it lacks, NTT of the converted limbs.  For a rotation
+//   the automorphism is a gather in the INTT's loads.
+// Stage 2 (inner product): one element-wise kernel per run of extended limbs,
+//   both key halves at once.
+// Stage 3 (ModDown): INTT of the special limbs (scaled by the BConv
+//   pre-factor), BConv to the ciphertext limbs, NTT whose last pass also
+//   subtracts from the inner product, multiplies by P^-1 and adds the
+//   pass-through polynomial (Section III-D: NTT(a1) + a2 + ... is fusable).
+// The plain pipeline runs every step (gather, scaling, combine) as its own
+// kernel on one stream.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -127,6 +129,13 @@ int run_modup(fhe_ctx *c, const uint32_t *d, int level, uint32_t galois_d, uint3
 
 // ------------------------------------------------------------------ stages 2 + 3: inner product, ModDown
 // ks carries ext, own (+ galois), key, addp (+ galois, add_c1).  Writes out [2][level][N].
+//
+// Fused pipeline (complementary pipelining, Section IV-B): the inner product
+// of the K special limbs is computed first and feeds ModDown's INTT / BConv /
+// NTT chain; the inner product of the l ciphertext limbs (the DRAM-bound part:
+// it streams 2 beta l key limbs) runs concurrently on the context's auxiliary
+// stream and is joined only before the last NTT pass, whose epilogue does the
+// combine (u - NTT(r)) P^-1 + add.
 int run_moddown(fhe_ctx *c, KsArgs ks, int level, uint32_t *out, cudaStream_t s) {
   const size_t N = c->N;
   const int L = c->L, K = c->K, n_ext = level + K;
@@ -148,78 +157,71 @@ int run_moddown(fhe_ctx *c, KsArgs ks, int level, uint32_t *out, cudaStream_t s)
     g.n_in = K;
     g.n_out = level;
   }
+  SegBuilder ipq, ipp;
+  {
+    Seg a = mkseg(nullptr, c->wU, level, 0);
+    a.t0 = 0;
+    a.key_row0 = 0;
+    ipq.add(a);
+    Seg b = mkseg(nullptr, c->wU + (size_t)level * N, K, L);
+    b.t0 = level;
+    b.key_row0 = L;
+    ipp.add(b);
+  }
+  SegBuilder first, second, sc, na, nb;
+  for (int cc = 0; cc < 2; cc++) {
+    uint32_t *uc = c->wUC + (size_t)cc * K * N;
+    first.add(mkseg(c->wU + ((size_t)cc * n_ext + level) * N, uc, K, L));
+    Seg b = mkseg(uc, uc, K, L);
+    if (c->fused) b.scale = c->d_md_scale;
+    second.add(b);
+    Seg x = mkseg(uc, uc, K, L);
+    x.scale = c->d_md_phinv;
+    sc.add(x);
+    uint32_t *r = c->wR + (size_t)cc * level * N;
+    na.add(mkseg(r, r, level, 0));
+    Seg y = mkseg(r, out + (size_t)cc * level * N, level, 0);
+    y.src2 = c->wU + (size_t)cc * n_ext * N;
+    y.t0 = 0;
+    y.c = cc;
+    nb.add(y);
+  }
   if (c->fused) {
-    SegBuilder first, second;
-    for (int cc = 0; cc < 2; cc++) {
-      Seg a = mkseg(nullptr, c->wUC + (size_t)cc * K * N, K, L);
-      a.t0 = level;
-      a.key_row0 = L;
-      a.c = cc;
-      first.add(a);
-      Seg b = mkseg(c->wUC + (size_t)cc * K * N, c->wUC + (size_t)cc * K * N, K, L);
-      b.scale = c->d_md_scale;
-      second.add(b);
-    }
-    LAUNCH_OR_FAIL(launch_ntt(c->tabs, false, PRO_IP, EPI_SCALE, first.l, second.l, ks, s));
+    LAUNCH_OR_FAIL(cudaEventRecord(c->ev_fork, s));
+    LAUNCH_OR_FAIL(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
+    LAUNCH_OR_FAIL(launch_ip(c->tabs, ipq.l, ks, c->aux));
+    LAUNCH_OR_FAIL(cudaEventRecord(c->ev_join, c->aux));
+    LAUNCH_OR_FAIL(launch_ip(c->tabs, ipp.l, ks, s));
+    LAUNCH_OR_FAIL(launch_ntt(c->tabs, false, PRO_PLAIN, EPI_SCALE, first.l, second.l, ks, s));
     if (c->bconv_mode == FHE_BCONV_TC)
       LAUNCH_OR_FAIL(launch_bconv_tc(c->tabs, ba, K, s));
     else
       LAUNCH_OR_FAIL(launch_bconv(c->tabs, ba, K, s));
-    SegBuilder na, nb;
-    for (int cc = 0; cc < 2; cc++) {
-      uint32_t *r = c->wR + (size_t)cc * level * N;
-      na.add(mkseg(r, r, level, 0));
-      Seg b = mkseg(r, out + (size_t)cc * level * N, level, 0);
-      b.t0 = 0;
-      b.key_row0 = 0;
-      b.c = cc;
-      nb.add(b);
-    }
-    LAUNCH_OR_FAIL(launch_ntt(c->tabs, true, PRO_PLAIN, EPI_COMBINE, na.l, nb.l, ks, s));
+    LAUNCH_OR_FAIL(launch_ntt_pass(c->tabs, true, true, PRO_PLAIN, EPI_LAZY, na.l, ks, s));
+    LAUNCH_OR_FAIL(cudaStreamWaitEvent(s, c->ev_join, 0));
+    LAUNCH_OR_FAIL(launch_ntt_pass(c->tabs, false, true, PRO_PLAIN, EPI_COMBINE, nb.l, ks, s));
     return FHE_OK;
   }
-  // plain: full inner product into U, then separate kernels
+  // plain: every step its own kernel, in order
   SegBuilder ip;
-  for (int cc = 0; cc < 2; cc++) {
-    uint32_t *u = c->wU + (size_t)cc * n_ext * N;
-    Seg a = mkseg(nullptr, u, level, 0);
-    a.t0 = 0;
-    a.key_row0 = 0;
-    a.c = cc;
-    ip.add(a);
-    Seg b = mkseg(nullptr, u + (size_t)level * N, K, L);
-    b.t0 = level;
-    b.key_row0 = L;
-    b.c = cc;
-    ip.add(b);
-  }
-  LAUNCH_OR_FAIL(launch_ew(c->tabs, EW_IP, ip.l, ks, s));
-  SegBuilder first, second, sc;
-  for (int cc = 0; cc < 2; cc++) {
-    uint32_t *uc = c->wUC + (size_t)cc * K * N;
-    first.add(mkseg(c->wU + ((size_t)cc * n_ext + level) * N, uc, K, L));
-    second.add(mkseg(uc, uc, K, L));
-    Seg x = mkseg(uc, uc, K, L);
-    x.scale = c->d_md_phinv;
-    sc.add(x);
-  }
+  ip.add(ipq.l.seg[0]);
+  ip.add(ipp.l.seg[0]);
+  LAUNCH_OR_FAIL(launch_ip(c->tabs, ip.l, ks, s));
   LAUNCH_OR_FAIL(launch_ntt(c->tabs, false, PRO_PLAIN, EPI_SCALE, first.l, second.l, ks, s));
   LAUNCH_OR_FAIL(launch_ew(c->tabs, EW_SCALE, sc.l, ks, s));
   if (c->bconv_mode == FHE_BCONV_TC)
     LAUNCH_OR_FAIL(launch_bconv_tc(c->tabs, ba, K, s));
   else
     LAUNCH_OR_FAIL(launch_bconv(c->tabs, ba, K, s));
-  SegBuilder nr, cb;
+  LAUNCH_OR_FAIL(launch_ntt(c->tabs, true, PRO_PLAIN, EPI_PLAIN, na.l, na.l, ks, s));
+  SegBuilder cb;
   for (int cc = 0; cc < 2; cc++) {
-    uint32_t *r = c->wR + (size_t)cc * level * N;
-    nr.add(mkseg(r, r, level, 0));
     Seg x = mkseg(c->wU + (size_t)cc * n_ext * N, out + (size_t)cc * level * N, level, 0);
-    x.src2 = r;
+    x.src2 = c->wR + (size_t)cc * level * N;
     x.t0 = 0;
     x.c = cc;
     cb.add(x);
   }
-  LAUNCH_OR_FAIL(launch_ntt(c->tabs, true, PRO_PLAIN, EPI_PLAIN, nr.l, nr.l, ks, s));
   LAUNCH_OR_FAIL(launch_ew(c->tabs, EW_COMBINE, cb.l, ks, s));
   return FHE_OK;
 }
@@ -523,8 +525,8 @@ extern "C" int fhe_bconv(fhe_ctx *c, const uint32_t *in, const int *in_idx, int 
   if (!c) return fhe_fail(FHE_EINVAL, "fhe_bconv: null ctx");
   CHECK(check_ptr(in, "fhe_bconv", "in"));
   CHECK(check_ptr(out, "fhe_bconv", "out"));
-  if (n_in < 1 || n_in > 32 || n_out < 1 || n_out > 64 || !in_idx || !out_idx)
-    return fhe_fail(FHE_EINVAL, "fhe_bconv: n_in=%d (1..32), n_out=%d (1..64)", n_in, n_out);
+  if (n_in < 1 || n_in > 16 || n_out < 1 || n_out > 64 || !in_idx || !out_idx)
+    return fhe_fail(FHE_EINVAL, "fhe_bconv: n_in=%d (1..16), n_out=%d (1..64)", n_in, n_out);
   const int NP = c->L + c->K;
   for (int i = 0; i < n_in; i++)
     if (in_idx[i] < 0 || in_idx[i] >= NP) return fhe_fail(FHE_EINVAL, "fhe_bconv: in prime index");
