@@ -261,12 +261,20 @@ def main():
     plain_ks = B * cmp_steps * ws / (ms_plain / 1e3)
     fused_ks = B * cmp_steps * ws / (ms_fused / 1e3)
 
-    # --- per-kernel times (CUDA events around each launch on its stream), fused direct path
+    # --- per-kernel times (CUDA events around each launch on its stream): the same batched
+    # stage programs as the headline, launched directly instead of through the graph
+    plan_direct = ctx.batch_plan(items, 0)
+    for _ in range(3):
+        plan_direct.launch()
     ctx.trace(True)
     for _ in range(cmp_steps):
-        direct()
+        plan_direct.launch()
     stats = ctx.trace_read()
     ctx.trace(False)
+    ms_batched_direct = timed(plan_direct.launch, cmp_steps)
+    batched_direct_ks = B * cmp_steps * ws / (ms_batched_direct / 1e3)
+    groups = plan.groups
+    plan_direct.close()
     total_ms = sum(v[1] for v in stats.values())
     top_name, (top_n, top_ms) = max(stats.items(), key=lambda kv: kv[1][1])
     per_launch_ms = top_ms / top_n
@@ -293,10 +301,12 @@ def main():
     W = 4 * P.N
     beta = P.beta(level)
     conv = beta * (level + P.K) - level
-    # limbs one launch of each kernel transforms (ModUp and ModDown launches of one name averaged)
+    # limbs one launch of each kernel transforms per item (ModUp and ModDown launches of one name
+    # averaged), times the items of an average group
     limbs = {"intt_blk+gather": level, "intt_col+scale": (level + 2 * P.K) / 2.0, "ntt_col": (conv + 2 * level) / 2.0,
-             "ntt_blk": conv, "intt_blk+ip": 2 * P.K, "ntt_blk+combine": 2 * level}
-    n_l = limbs.get(top_name, level)
+             "ntt_blk": conv, "intt_blk": 2 * P.K, "ntt_blk+combine": 2 * level}
+    items_per_launch = B / max(1, len(groups))
+    n_l = limbs.get(top_name, level) * items_per_launch
     half = 8 if top_name.endswith(("blk", "blk+gather", "blk+ip", "blk+combine")) else P.N.bit_length() - 1 - 8
     bfly = n_l * (P.N // 2) * half
     traffic_bytes = 2 * n_l * W
@@ -359,7 +369,9 @@ def main():
             "cpu_baseline": cpu,
             "l2_roofline": {"bytes_per_ks": bks, "l2_gbs_measured": l2_gbs, "frac": l2_frac,
                             "definition": "B_KS(l) / measured L2 read+write bandwidth / time per key switch"},
-            "paths": {"graph_fused": value, "direct_fused": fused_ks, "plain_per_kernel": plain_ks},
+            "paths": {"graph_fused_batched": value, "direct_fused_batched": batched_direct_ks,
+                      "direct_fused_single": fused_ks, "plain_per_kernel_single": plain_ks},
+            "batch_groups": groups,
             "kernels": {k: {"launches": v[0], "ms": v[1], "share": v[1] / total_ms} for k, v in
                         sorted(stats.items(), key=lambda kv: -kv[1][1])},
         }

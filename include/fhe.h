@@ -212,6 +212,14 @@ FHE_API int fhe_batch_launch(fhe_plan *plan, fhe_stream stream);
 FHE_API int fhe_plan_destroy(fhe_plan *plan);
 /* number of kernel launches one fhe_batch_launch performs (graph nodes or direct launches) */
 FHE_API int fhe_plan_kernel_count(const fhe_plan *plan);
+/* sizes of the plan's item groups (at most max written); returns the number of groups */
+FHE_API int fhe_plan_groups(const fhe_plan *plan, int *sizes, int max);
+/*
+ * Group sizing of later plans: a group's stage-1 working sets (beta(l)(l+K)
+ * limbs per item) stay within l2_budget_bytes (0: 3/4 of the device's L2) and
+ * a group holds at most max_group items (0: 8).  The autotuner sets these.
+ */
+FHE_API int fhe_ctx_set_batch(fhe_ctx *ctx, size_t l2_budget_bytes, int max_group);
 
 /*
  * Kernel tracing (measurement support): while enabled, every kernel the

@@ -30,6 +30,7 @@ EXPORTS = (
     "fhe_set_relin_key", "fhe_set_rot_key", "fhe_keyswitch", "fhe_rotate", "fhe_hmult", "fhe_rescale",
     "fhe_rotate_hoisted", "fhe_pmult", "fhe_add", "fhe_ntt", "fhe_intt", "fhe_modup", "fhe_moddown",
     "fhe_bconv", "fhe_batch_plan", "fhe_batch_launch", "fhe_plan_destroy", "fhe_plan_kernel_count",
+    "fhe_plan_groups", "fhe_ctx_set_batch",
     "fhe_trace_enable", "fhe_trace_read", "fhe_last_error",
 )
 
@@ -103,6 +104,8 @@ def lib() -> ctypes.CDLL:
         "fhe_batch_launch": [vp, vp],
         "fhe_plan_destroy": [vp],
         "fhe_plan_kernel_count": [vp],
+        "fhe_plan_groups": [vp, ip, ctypes.c_int],
+        "fhe_ctx_set_batch": [vp, ctypes.c_size_t, ctypes.c_int],
         "fhe_trace_enable": [vp, ctypes.c_int],
         "fhe_trace_read": [vp, ctypes.POINTER(KernelStat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
         "fhe_last_error": [],
@@ -165,6 +168,14 @@ class Plan:
     def kernel_count(self) -> int:
         return lib().fhe_plan_kernel_count(self.h)
 
+    @property
+    def groups(self) -> List[int]:
+        arr = (ctypes.c_int * 256)()
+        n = lib().fhe_plan_groups(self.h, arr, 256)
+        if n < 0:
+            check(n)
+        return list(arr[: min(n, 256)])
+
     def close(self) -> None:
         if self.h:
             check(lib().fhe_plan_destroy(self.h))
@@ -220,6 +231,9 @@ class Context:
 
     def set_bconv(self, mode: int) -> None:
         check(lib().fhe_ctx_set_bconv(self.h, mode))
+
+    def set_batch(self, l2_budget_bytes: int = 0, max_group: int = 0) -> None:
+        check(lib().fhe_ctx_set_batch(self.h, l2_budget_bytes, max_group))
 
     def set_fused(self, fused: bool) -> None:
         check(lib().fhe_ctx_set_fused(self.h, int(bool(fused))))

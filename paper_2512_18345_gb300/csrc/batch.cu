@@ -1,68 +1,172 @@
-// Batched key switching (Section IV-A batching, Section IV-C CUDA Graphs):
-// a plan captures every item's pipeline into one CUDA graph; launching the
-// plan replays the graph on the caller's stream with one host call.
+// Batched key switching (Section IV-A multi-polynomial caching and batching,
+// Section IV-C CUDA Graphs).
+//
+// A plan splits its items into groups whose stage-1 working sets (beta(l)
+// (l + K) limbs each, the footprint column of Table "ks-param") fit an L2
+// budget, builds one stage program per group (every stage kernel processes
+// all items of the group in one launch, each item in its own workspace slot)
+// and captures all groups into one CUDA graph.  Launching the plan replays
+// the graph on the caller's stream with one host call.
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
 #include "../../include/fhe.h"
 #include "ctx.h"
 #include "internal.h"
+#include "program.h"
 
 struct fhe_plan {
   fhe_ctx *ctx = nullptr;
   std::vector<fhe_ks_item> items;
   int flags = 0;
+  std::vector<Program> progs;
+  std::vector<DevProgram> dev;
+  std::vector<std::vector<std::pair<const uint32_t *, uint32_t *>>> copies;  // identity rotations per group
+  size_t copy_bytes = 0;
+  std::vector<int> group_sizes;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int kernels = 0;
 };
 
-static int enqueue_items(fhe_ctx *c, const std::vector<fhe_ks_item> &items, cudaStream_t s) {
-  for (const fhe_ks_item &it : items) {
-    int rc;
-    switch (it.op) {
-      case FHE_OP_KS: rc = fhe_keyswitch(c, it.in, it.level, it.rot, it.out, s); break;
-      case FHE_OP_ROTATE: rc = fhe_rotate(c, it.in, it.level, it.rot, it.out, s); break;
-      case FHE_OP_RELIN: rc = fhe_hmult(c, it.in, it.in2, it.level, it.out, s); break;
-      default: rc = fhe_fail(FHE_EINVAL, "fhe_batch: op %d", it.op);
-    }
+static int enqueue_plan(fhe_plan *p, cudaStream_t s) {
+  fhe_ctx *c = p->ctx;
+  for (size_t g = 0; g < p->progs.size(); g++) {
+    for (auto &cp : p->copies[g])
+      if (cudaMemcpyAsync(cp.second, cp.first, p->copy_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return fhe_fail(FHE_ECUDA, "fhe_batch: copy");
+    int rc = run_program_dev(c, p->progs[g], p->dev[g], s);
     if (rc != FHE_OK) return rc;
   }
+  return FHE_OK;
+}
+
+static void destroy(fhe_plan *p) {
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  for (auto &d : p->dev) free_program(d);
+  delete p;
+}
+
+extern "C" int fhe_ctx_set_batch(fhe_ctx *c, size_t l2_budget_bytes, int max_group) {
+  if (!c || max_group < 0) return fhe_fail(FHE_EINVAL, "fhe_ctx_set_batch: bad arguments");
+  c->batch_budget = l2_budget_bytes;
+  c->batch_max_group = max_group;
   return FHE_OK;
 }
 
 extern "C" int fhe_batch_plan(fhe_ctx *c, const fhe_ks_item *items, int n, int flags, fhe_plan **out) {
   if (!c || !out || n < 0 || (n > 0 && !items)) return fhe_fail(FHE_EINVAL, "fhe_batch_plan: bad arguments");
   *out = nullptr;
+  const size_t N = c->N;
   for (int i = 0; i < n; i++) {
     const fhe_ks_item &it = items[i];
     if (it.level < 1 || it.level > c->L) return fhe_fail(FHE_ELEVEL, "fhe_batch_plan: item %d level %d", i, it.level);
     if (!it.in || !it.out || (it.op == FHE_OP_RELIN && !it.in2))
       return fhe_fail(FHE_EINVAL, "fhe_batch_plan: item %d has a null buffer", i);
+    if (it.op < FHE_OP_KS || it.op > FHE_OP_RELIN) return fhe_fail(FHE_EINVAL, "fhe_batch_plan: item %d op %d", i, it.op);
     if (it.op == FHE_OP_RELIN && !c->relin_key) return fhe_fail(FHE_ENOKEY, "fhe_batch_plan: no relinearisation key");
     if ((it.op == FHE_OP_ROTATE && fhe_galois_elt(it.rot, c->N) != 1u) || it.op == FHE_OP_KS)
       if (!c->find_key(it.rot)) return fhe_fail(FHE_ENOKEY, "fhe_batch_plan: item %d has no key", i);
   }
+  cudaSetDevice(c->device);
   fhe_plan *p = new fhe_plan();
   p->ctx = c;
   p->items.assign(items, items + n);
   p->flags = flags;
-  if (flags & FHE_PLAN_GRAPH) {
-    cudaSetDevice(c->device);
+  // group items so that each group's stage-1 working set stays within the L2 budget
+  size_t budget = c->batch_budget;
+  if (!budget) {
+    int l2 = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device);
+    budget = (size_t)l2 * 3 / 4;
+  }
+  const int max_group = c->batch_max_group > 0 ? c->batch_max_group : 8;
+  std::vector<std::vector<int>> groups(1);
+  size_t used = 0;
+  for (int i = 0; i < n; i++) {
+    const int lv = items[i].level;
+    const size_t fp = (size_t)c->beta(lv) * (lv + c->K) * 4 * N;
+    if (!groups.back().empty() && (used + fp > budget || (int)groups.back().size() >= max_group)) {
+      groups.emplace_back();
+      used = 0;
+    }
+    groups.back().push_back(i);
+    used += fp;
+  }
+  int rc = FHE_OK;
+  for (auto &grp : groups) {
+    std::vector<Item> its;
+    std::vector<std::pair<const uint32_t *, uint32_t *>> cps;
+    for (int i : grp) {
+      const fhe_ks_item &x = items[i];
+      Item it;
+      it.level = x.level;
+      it.in = x.in;
+      it.in2 = x.in2;
+      it.out = x.out;
+      if (x.op == FHE_OP_KS) {
+        it.kind = IT_KS;
+        it.key = c->find_key(x.rot);
+      } else if (x.op == FHE_OP_RELIN) {
+        it.kind = IT_RELIN;
+        it.key = c->relin_key;
+      } else {
+        const uint32_t k = fhe_galois_elt(x.rot, c->N);
+        if (k == 1u) {  // identity rotation: a copy
+          cps.push_back({x.in, x.out});
+          continue;
+        }
+        it.kind = IT_ROTATE;
+        it.galois = k;
+        it.key = c->find_key(x.rot);
+      }
+      it.slot = (int)its.size();
+      its.push_back(it);
+    }
+    // copies of identity rotations have level-dependent sizes: handle them as one-item groups
+    Program P;
+    if (rc == FHE_OK) rc = build_program(c, its, true, P);
+    DevProgram D;
+    if (rc == FHE_OK) rc = upload_program(c, P, D);
+    p->progs.push_back(P);
+    p->dev.push_back(D);
+    p->copies.push_back({});
+    for (auto &cp : cps) {
+      // find the item's level to size the copy: identity rotations are copied one by one
+      p->copies.back().push_back(cp);
+    }
+    p->group_sizes.push_back((int)its.size());
+    if (rc != FHE_OK) break;
+  }
+  // identity-rotation copies need per-item sizes; record them per copy via a side list
+  p->copy_bytes = 0;
+  if (rc == FHE_OK) {
+    bool mixed = false;
+    size_t bytes = 0;
+    for (int i = 0; i < n; i++)
+      if (items[i].op == FHE_OP_ROTATE && fhe_galois_elt(items[i].rot, c->N) == 1u) {
+        const size_t b = 8 * N * (size_t)items[i].level;
+        if (bytes && b != bytes) mixed = true;
+        bytes = b;
+      }
+    if (mixed) rc = fhe_fail(FHE_EUNSUPPORTED, "fhe_batch_plan: identity rotations at different levels in one plan");
+    p->copy_bytes = bytes;
+  }
+  if (rc == FHE_OK && (flags & FHE_PLAN_GRAPH)) {
     cudaStream_t cs;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
-      delete p;
+      destroy(p);
       return fhe_fail(FHE_ECUDA, "fhe_batch_plan: stream");
     }
-    // the capture must not race with work already queued on this context
     if (c->have_last) cudaStreamSynchronize(c->last_stream);
     fhe::Tracer *saved_tracer = c->tabs.tracer;
     c->tabs.tracer = nullptr;  // no trace events inside a captured graph
     c->capturing = true;
-    int rc = FHE_OK;
     if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       rc = fhe_fail(FHE_ECUDA, "fhe_batch_plan: begin capture");
-    if (rc == FHE_OK) rc = enqueue_items(c, p->items, cs);
+    if (rc == FHE_OK) rc = enqueue_plan(p, cs);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &g);
     c->capturing = false;
@@ -71,25 +175,24 @@ extern "C" int fhe_batch_plan(fhe_ctx *c, const fhe_ks_item *items, int n, int f
     if (rc == FHE_OK && cudaGraphInstantiate(&p->exec, g, 0) != cudaSuccess)
       rc = fhe_fail(FHE_ECUDA, "fhe_batch_plan: instantiate");
     cudaStreamDestroy(cs);
-    if (rc != FHE_OK) {
-      if (g) cudaGraphDestroy(g);
-      delete p;
-      return rc;
-    }
     p->graph = g;
-    size_t nn = 0;
-    cudaGraphGetNodes(g, nullptr, &nn);
-    std::vector<cudaGraphNode_t> nodes(nn);
-    cudaGraphGetNodes(g, nodes.data(), &nn);
-    for (auto nd : nodes) {
-      cudaGraphNodeType t;
-      cudaGraphNodeGetType(nd, &t);
-      p->kernels += t == cudaGraphNodeTypeKernel;
+    if (rc == FHE_OK) {
+      size_t nn = 0;
+      cudaGraphGetNodes(g, nullptr, &nn);
+      std::vector<cudaGraphNode_t> nodes(nn);
+      cudaGraphGetNodes(g, nodes.data(), &nn);
+      for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        cudaGraphNodeGetType(nd, &t);
+        p->kernels += t == cudaGraphNodeTypeKernel;
+      }
     }
-  } else {
-    const long long before = fhe::kernel_launches();
-    (void)before;
+  } else if (rc == FHE_OK) {
     p->kernels = -1;
+  }
+  if (rc != FHE_OK) {
+    destroy(p);
+    return rc;
   }
   *out = p;
   return FHE_OK;
@@ -100,14 +203,14 @@ extern "C" int fhe_batch_launch(fhe_plan *p, fhe_stream stream) {
   fhe_ctx *c = p->ctx;
   cudaSetDevice(c->device);
   cudaStream_t s = (cudaStream_t)stream;
+  c->order_stream(s);
   if (p->exec) {
-    c->order_stream(s);
     cudaError_t e = cudaGraphLaunch(p->exec, s);
     if (e != cudaSuccess) return fhe_fail(FHE_ECUDA, "fhe_batch_launch: %s", cudaGetErrorString(e));
     return FHE_OK;
   }
   const long long before = fhe::kernel_launches();
-  int rc = enqueue_items(c, p->items, s);
+  int rc = enqueue_plan(p, s);
   p->kernels = (int)(fhe::kernel_launches() - before);
   return rc;
 }
@@ -115,10 +218,14 @@ extern "C" int fhe_batch_launch(fhe_plan *p, fhe_stream stream) {
 extern "C" int fhe_plan_destroy(fhe_plan *p) {
   if (!p) return fhe_fail(FHE_EINVAL, "fhe_plan_destroy: null");
   cudaSetDevice(p->ctx->device);
-  if (p->exec) cudaGraphExecDestroy(p->exec);
-  if (p->graph) cudaGraphDestroy(p->graph);
-  delete p;
+  destroy(p);
   return FHE_OK;
 }
 
 extern "C" int fhe_plan_kernel_count(const fhe_plan *p) { return p ? p->kernels : -1; }
+
+extern "C" int fhe_plan_groups(const fhe_plan *p, int *sizes, int max) {
+  if (!p) return fhe_fail(FHE_EINVAL, "fhe_plan_groups: null");
+  for (int i = 0; i < max && i < (int)p->group_sizes.size(); i++) sizes[i] = p->group_sizes[i];
+  return (int)p->group_sizes.size();
+}

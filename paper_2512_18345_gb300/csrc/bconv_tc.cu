@@ -3,6 +3,6 @@
 #include "internal.h"
 
 namespace fhe {
-cudaError_t launch_bconv_tc(const DevTables &, const BconvArgs &, int, cudaStream_t) { return cudaErrorNotSupported; }
+cudaError_t launch_bconv_tc(const DevTables &, const BconvArgs &, int, int, cudaStream_t) { return cudaErrorNotSupported; }
 }  // namespace fhe
 bool fhe_tc_available() { return false; }

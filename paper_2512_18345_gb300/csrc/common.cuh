@@ -72,20 +72,15 @@ struct Seg {
   int src_stride;    // in limbs (0: every limb reads the same source limb)
   int src_prime;     // prime of the source limb if it differs (rescale), else -1
   const uint2 *scale;  // per-limb Shoup constant pairs (inverse-NTT output scale), or null
-  int t0;            // extended-basis index of the first limb (fused inner product)
+  int t0;            // extended-basis index of the first limb (inner product)
   int key_row0;      // key row of the first limb
-  int c;             // which half (0: b / c0, 1: a / c1) a fused inner product uses
-  int digit;         // digit index (base conversion) or -1
+  int c;             // which half (0: b / c0, 1: a / c1) a combine uses
+  int item;          // index of this segment's key-switching arguments
+  uint32_t galois;   // element-wise gather: Galois element applied to src (1: none)
 };
 
-struct SegList {
-  int nseg;
-  int total;                 // total limbs over all segments
-  const Seg *dev;            // if non-null: segments in device memory (batched plans)
-  Seg seg[kMaxSeg];
-};
-
-// Key-switching context for fused prologues / epilogues.
+// Key-switching arguments of one item (one key switch) for the inner product,
+// the automorphism gathers and the ModDown combine.
 struct KsArgs {
   const uint32_t *ext;   // [beta][n_ext][N] ModUp outputs (NTT form); own-digit limbs unused
   const uint32_t *own;   // [level][N] the key-switched polynomial in NTT form (own-digit limbs)
@@ -99,10 +94,32 @@ struct KsArgs {
   int add_c1;            // also add addp's second polynomial to c = 1 (HMult); rotation adds c0 only
 };
 
+constexpr int kMaxInlineItems = 4;
+
+// A launch's work list: segments and per-item arguments, either inline (by
+// value, single operations) or in device memory (batched plans).
+struct SegList {
+  int nseg;
+  int total;              // total limbs over all segments
+  const Seg *dev;         // if non-null: segments in device memory
+  const int2 *vmap;       // optional [total] (segment, limb within) for device lists
+  const KsArgs *ksdev;    // if non-null: per-item arguments in device memory
+  Seg seg[kMaxSeg];
+  KsArgs ks[kMaxInlineItems];
+};
+
 __device__ __forceinline__ const Seg &seg_at(const SegList &L, int i) { return L.dev ? L.dev[i] : L.seg[i]; }
+__device__ __forceinline__ const KsArgs &item_ks(const SegList &L, const Seg &s) {
+  return L.ksdev ? L.ksdev[s.item] : L.ks[s.item];
+}
 
 // Locate limb v (0 <= v < total) of a segment list: returns segment index and limb within it.
 __device__ __forceinline__ int seg_find(const SegList &L, int v, int &within) {
+  if (L.vmap) {
+    const int2 m = L.vmap[v];
+    within = m.y;
+    return m.x;
+  }
   int s = 0;
   for (; s < L.nseg; s++) {
     const int n = seg_at(L, s).n;

@@ -244,27 +244,31 @@ static int build_tables(fhe_ctx *c) {
   return FHE_OK;
 }
 
-static int alloc_workspace(fhe_ctx *c) {
+int ensure_slots(fhe_ctx *c, int n) {
   const size_t N = c->N;
   const int L = c->L, K = c->K, B = c->beta(L);
-  size_t off = 0;
-  auto take = [&](size_t limbs) {
-    size_t o = off;
-    off += limbs * N;
-    return o;
-  };
-  const size_t oY = take(L), oEXT = take((size_t)B * (L + K)), oUC = take(2 * K), oR = take(2 * L),
-               oD = take(3 * L), oU = take(2 * (L + K)), oTMP = take(2 * L), oV = take(2);
-  CUDA_OR_FAIL(cudaMalloc(&c->ws, off * sizeof(uint32_t)));
-  c->ws_bytes = off * sizeof(uint32_t);
-  c->wY = c->ws + oY;
-  c->wEXT = c->ws + oEXT;
-  c->wUC = c->ws + oUC;
-  c->wR = c->ws + oR;
-  c->wD = c->ws + oD;
-  c->wU = c->ws + oU;
-  c->wTMP = c->ws + oTMP;
-  c->wV = c->ws + oV;
+  const size_t limbs = (size_t)L + (size_t)B * (L + K) + 2 * (L + K) + 2 * K + 2 * L + 3 * L + 2 * L + 2;
+  c->slot_bytes = limbs * N * sizeof(uint32_t);
+  while ((int)c->slots.size() < n) {
+    fhe_ctx::Slot s;
+    CUDA_OR_FAIL(cudaMalloc(&s.base, c->slot_bytes));
+    uint32_t *p = s.base;
+    auto take = [&](size_t l) {
+      uint32_t *r = p;
+      p += l * N;
+      return r;
+    };
+    s.Y = take(L);
+    s.EXT = take((size_t)B * (L + K));
+    s.U = take(2 * (L + K));
+    s.UC = take(2 * K);
+    s.R = take(2 * L);
+    s.D = take(3 * L);
+    s.TMP = take(2 * L);
+    s.V = take(2);
+    c->slots.push_back(s);
+    c->ws_bytes += c->slot_bytes;
+  }
   return FHE_OK;
 }
 
@@ -286,7 +290,7 @@ fhe_ctx::~fhe_ctx() {
   cudaFree(d_mdT);
   cudaFree(d_mdmap);
   cudaFree(d_rs_qinv);
-  cudaFree(ws);
+  for (auto &s : slots) cudaFree(s.base);
   cudaFree(relin_key);
   for (auto &kv : rot_keys) cudaFree(kv.second);
   for (auto p : scratch_tabs) cudaFree(p);
@@ -338,7 +342,7 @@ extern "C" int fhe_ctx_create(fhe_ctx **out, uint32_t N, const uint32_t *q, int 
   c->alpha = alpha;
   c->primes = pr;
   int rc = build_tables(c);
-  if (rc == FHE_OK) rc = alloc_workspace(c);
+  if (rc == FHE_OK) rc = ensure_slots(c, 1);
   if (rc == FHE_OK && (cudaEventCreateWithFlags(&c->order_ev, cudaEventDisableTiming) != cudaSuccess ||
                        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
                        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||

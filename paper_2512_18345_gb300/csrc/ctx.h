@@ -16,6 +16,8 @@ struct fhe_ctx {
   uint32_t psi[64] = {};
   int bconv_mode = 0;  // FHE_BCONV_SCALAR / FHE_BCONV_TC
   int fused = 1;
+  size_t batch_budget = 0;  // L2 bytes per batched group (0: 3/4 of the L2 size)
+  int batch_max_group = 0;  // items per batched group (0: 8)
 
   // device tables
   fhe::PrimeC *d_pc = nullptr;
@@ -38,11 +40,21 @@ struct fhe_ctx {
   uint32_t *relin_key = nullptr;
   std::map<uint32_t, uint32_t *> rot_keys;  // by Galois element
 
-  // workspace
-  uint32_t *ws = nullptr;
+  // workspace: slots, each holding every scratch array of one key switch at level L
+  struct Slot {
+    uint32_t *base = nullptr;
+    uint32_t *Y = nullptr;    // [L][N]        scaled INTT of the key-switched polynomial
+    uint32_t *EXT = nullptr;  // [beta][L+K][N] ModUp outputs
+    uint32_t *U = nullptr;    // [2][L+K][N]   inner product
+    uint32_t *UC = nullptr;   // [2][K][N]     special limbs in coefficient form
+    uint32_t *R = nullptr;    // [2][L][N]     ModDown base conversion
+    uint32_t *D = nullptr;    // [3][L][N]     HMult tensor
+    uint32_t *TMP = nullptr;  // [2][L][N]     plain-pipeline gather
+    uint32_t *V = nullptr;    // [2][N]        rescale
+  };
+  std::vector<Slot> slots;
+  size_t slot_bytes = 0;
   size_t ws_bytes = 0;
-  uint32_t *wY = nullptr, *wEXT = nullptr, *wUC = nullptr, *wR = nullptr, *wD = nullptr, *wU = nullptr,
-           *wTMP = nullptr, *wV = nullptr;
 
   // cross-stream ordering of calls on this context
   cudaStream_t last_stream = nullptr;
@@ -62,8 +74,6 @@ struct fhe_ctx {
 int fhe_fail(int code, const char *fmt, ...);
 uint32_t h_mulmod_pub(uint32_t a, uint32_t b, uint32_t q);
 uint32_t h_invmod_pub(uint32_t a, uint32_t q);
-// pipelines shared with the batched plans
-int run_modup(fhe_ctx *c, const uint32_t *d, int level, uint32_t galois_d, uint32_t *ext, cudaStream_t s);
-int run_moddown(fhe_ctx *c, fhe::KsArgs ks, int level, uint32_t *out, cudaStream_t s);
+int ensure_slots(fhe_ctx *c, int n);
 uint32_t fhe_galois_elt(int32_t rot, uint32_t N);
 bool fhe_tc_available();

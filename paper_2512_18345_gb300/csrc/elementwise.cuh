@@ -12,24 +12,25 @@ namespace fhe {
 constexpr int kEwThreads = 256;
 
 enum : int {
-  EW_GATHER = 0,   // dst = src[sigma(j)]               (galois = ks.galois_own)
+  EW_GATHER = 0,   // dst = src[sigma(j)]               (galois = seg.galois)
   EW_SCALE = 1,    // dst = src * scale[l]
   EW_IP = 2,       // (k_ip) both halves of the key inner product
   EW_COMBINE = 3,  // dst = (src - src2) P^-1 (+ add)  (src = u, src2 = NTT(r))
   EW_ADD = 4,      // dst = src + src2
   EW_MUL = 5,      // dst = src * src2
   EW_COPY = 6,     // dst = src
+  EW_TENSOR = 7,   // HMult tensor: src = a, src2 = b ([2][n][N] each), dst = (d0, d1, d2) [3][n][N]
 };
 
 template <int OP>
-__global__ void __launch_bounds__(kEwThreads) k_ew(const __grid_constant__ SegList sl, const PrimeC *pc,
-                                                   const __grid_constant__ KsArgs ks, int logn) {
+__global__ void __launch_bounds__(kEwThreads) k_ew(const __grid_constant__ SegList sl, const PrimeC *pc, int logn) {
   const size_t N = (size_t)1 << logn;
   const int blocks_per_limb = (int)(N / (4 * kEwThreads));
   const int v = blockIdx.x / blocks_per_limb;
   const uint32_t j0 = (uint32_t)((blockIdx.x % blocks_per_limb) * 4 * kEwThreads + threadIdx.x * 4);
   int within;
   const Seg &sg = seg_at(sl, seg_find(sl, v, within));
+  const KsArgs &ks = item_ks(sl, sg);
   const int prime = sg.prime + within;
   const PrimeC P = pc[prime];
   const uint32_t q = P.q;
@@ -37,9 +38,30 @@ __global__ void __launch_bounds__(kEwThreads) k_ew(const __grid_constant__ SegLi
   const uint32_t *src2 = sg.src2 ? sg.src2 + (size_t)within * N : nullptr;
   uint32_t *dst = sg.dst + (size_t)within * N;
   uint32_t o[4];
+  if (OP == EW_TENSOR) {  // the segment covers one ciphertext's limbs; n = level is the poly stride
+    const size_t poly = (size_t)sg.n * N, off = (size_t)within * N + j0;
+    const uint4 A0 = __ldg(reinterpret_cast<const uint4 *>(sg.src + off));
+    const uint4 A1 = __ldg(reinterpret_cast<const uint4 *>(sg.src + poly + off));
+    const uint4 B0 = __ldg(reinterpret_cast<const uint4 *>(sg.src2 + off));
+    const uint4 B1 = __ldg(reinterpret_cast<const uint4 *>(sg.src2 + poly + off));
+    const uint32_t a0[4] = {A0.x, A0.y, A0.z, A0.w}, a1[4] = {A1.x, A1.y, A1.z, A1.w};
+    const uint32_t b0[4] = {B0.x, B0.y, B0.z, B0.w}, b1[4] = {B1.x, B1.y, B1.z, B1.w};
+    uint32_t d0[4], d1[4], d2[4];
+#pragma unroll
+    for (int x = 0; x < 4; x++) {
+      d0[x] = mul_mod(a0[x], b0[x], P);
+      d1[x] = reduce_u64((uint64_t)a0[x] * b1[x] + (uint64_t)a1[x] * b0[x], P);  // < 2^63
+      d2[x] = mul_mod(a1[x], b1[x], P);
+    }
+    uint32_t *d = sg.dst + off;
+    *reinterpret_cast<uint4 *>(d) = make_uint4(d0[0], d0[1], d0[2], d0[3]);
+    *reinterpret_cast<uint4 *>(d + poly) = make_uint4(d1[0], d1[1], d1[2], d1[3]);
+    *reinterpret_cast<uint4 *>(d + 2 * poly) = make_uint4(d2[0], d2[1], d2[2], d2[3]);
+    return;
+  }
   if (OP == EW_GATHER) {
 #pragma unroll
-    for (int e = 0; e < 4; e++) o[e] = __ldg(src + galois_src(j0 + e, ks.galois_own, logn));
+    for (int e = 0; e < 4; e++) o[e] = __ldg(src + galois_src(j0 + e, sg.galois, logn));
   } else {
     const uint4 a = __ldg(reinterpret_cast<const uint4 *>(src + j0));
     const uint32_t av[4] = {a.x, a.y, a.z, a.w};
@@ -79,50 +101,48 @@ __global__ void __launch_bounds__(kEwThreads) k_ew(const __grid_constant__ SegLi
 // at u_0[t0]; u_1 sits n_ext limbs further.  beta <= 4, so the four 62-bit
 // products of a sum fit one 64-bit accumulator.
 template <bool GOWN, bool GEXT>
-__global__ void __launch_bounds__(kEwThreads) k_ip(const __grid_constant__ SegList sl, const PrimeC *pc,
-                                                   const __grid_constant__ KsArgs ks, int logn) {
+__global__ void __launch_bounds__(kEwThreads) k_ip(const __grid_constant__ SegList sl, const PrimeC *pc, int logn) {
   const size_t N = (size_t)1 << logn;
   const int blocks_per_limb = (int)(N / (4 * kEwThreads));
   const int v = blockIdx.x / blocks_per_limb;
   const uint32_t j0 = (uint32_t)((blockIdx.x % blocks_per_limb) * 4 * kEwThreads + threadIdx.x * 4);
   int within;
   const Seg &sg = seg_at(sl, seg_find(sl, v, within));
+  const KsArgs &ks = item_ks(sl, sg);
   const int t = sg.t0 + within, row = sg.key_row0 + within;
   const PrimeC P = pc[sg.prime + within];
   const size_t kstride = (size_t)2 * (ks.L + ks.K) * N;
+  // issue every digit's loads before any arithmetic (memory-level parallelism)
+  uint4 ev[4], kv0[4], kv1[4];
+#pragma unroll
+  for (int jd = 0; jd < 4; jd++) {
+    if (jd < ks.beta) {
+      const bool own = t < ks.level && t >= jd * ks.alpha && t < (jd + 1) * ks.alpha;
+      const uint32_t *p = own ? ks.own + (size_t)t * N : ks.ext + ((size_t)jd * ks.n_ext + t) * N;
+      if ((own && GOWN) || (!own && GEXT)) {
+        const uint32_t g = own ? ks.galois_own : ks.galois_ext;
+        ev[jd] = make_uint4(__ldg(p + galois_src(j0, g, logn)), __ldg(p + galois_src(j0 + 1, g, logn)),
+                            __ldg(p + galois_src(j0 + 2, g, logn)), __ldg(p + galois_src(j0 + 3, g, logn)));
+      } else {
+        ev[jd] = __ldg(reinterpret_cast<const uint4 *>(p + j0));
+      }
+      const uint32_t *kp = ks.key + jd * kstride + (size_t)row * N + j0;
+      kv0[jd] = __ldg(reinterpret_cast<const uint4 *>(kp));
+      kv1[jd] = __ldg(reinterpret_cast<const uint4 *>(kp + (size_t)(ks.L + ks.K) * N));
+    } else {
+      ev[jd] = kv0[jd] = kv1[jd] = make_uint4(0, 0, 0, 0);
+    }
+  }
   uint64_t a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0};
 #pragma unroll
   for (int jd = 0; jd < 4; jd++) {
-    if (jd >= ks.beta) break;
-    const bool own = t < ks.level && t >= jd * ks.alpha && t < (jd + 1) * ks.alpha;
-    uint32_t e[4];
-    if (own) {
-      const uint32_t *p = ks.own + (size_t)t * N;
-      if (GOWN) {
-#pragma unroll
-        for (int i = 0; i < 4; i++) e[i] = __ldg(p + galois_src(j0 + i, ks.galois_own, logn));
-      } else {
-        const uint4 x = __ldg(reinterpret_cast<const uint4 *>(p + j0));
-        e[0] = x.x; e[1] = x.y; e[2] = x.z; e[3] = x.w;
-      }
-    } else {
-      const uint32_t *p = ks.ext + ((size_t)jd * ks.n_ext + t) * N;
-      if (GEXT) {
-#pragma unroll
-        for (int i = 0; i < 4; i++) e[i] = __ldg(p + galois_src(j0 + i, ks.galois_ext, logn));
-      } else {
-        const uint4 x = __ldg(reinterpret_cast<const uint4 *>(p + j0));
-        e[0] = x.x; e[1] = x.y; e[2] = x.z; e[3] = x.w;
-      }
-    }
-    const uint32_t *kp = ks.key + jd * kstride + (size_t)row * N + j0;
-    const uint4 k0 = __ldg(reinterpret_cast<const uint4 *>(kp));
-    const uint4 k1 = __ldg(reinterpret_cast<const uint4 *>(kp + (size_t)(ks.L + ks.K) * N));
-    const uint32_t kk0[4] = {k0.x, k0.y, k0.z, k0.w}, kk1[4] = {k1.x, k1.y, k1.z, k1.w};
+    const uint32_t e4[4] = {ev[jd].x, ev[jd].y, ev[jd].z, ev[jd].w};
+    const uint32_t k0[4] = {kv0[jd].x, kv0[jd].y, kv0[jd].z, kv0[jd].w};
+    const uint32_t k1[4] = {kv1[jd].x, kv1[jd].y, kv1[jd].z, kv1[jd].w};
 #pragma unroll
     for (int i = 0; i < 4; i++) {
-      a0[i] += (uint64_t)e[i] * kk0[i];
-      a1[i] += (uint64_t)e[i] * kk1[i];
+      a0[i] += (uint64_t)e4[i] * k0[i];
+      a1[i] += (uint64_t)e4[i] * k1[i];
     }
   }
   uint32_t *d0 = sg.dst + (size_t)within * N + j0, *d1 = d0 + (size_t)ks.n_ext * N;

@@ -37,18 +37,16 @@ struct DevTables {
 
 // One NTT pass over every limb of `sl` (column or block pass, forward or inverse).
 cudaError_t launch_ntt_pass(const DevTables &t, bool column, bool fwd, int pro, int epi, const SegList &sl,
-                            const KsArgs &ks, cudaStream_t s);
+                            cudaStream_t s);
 // Both passes: forward = column (pro, lazy) then block (plain, epi);
 // inverse = block (pro, lazy) then column (plain, epi).  In place after the first pass (dst of sl).
 cudaError_t launch_ntt(const DevTables &t, bool fwd, int pro, int epi, const SegList &first, const SegList &second,
-                       const KsArgs &ks, cudaStream_t s);
-cudaError_t launch_bconv(const DevTables &t, const BconvArgs &a, int max_in, cudaStream_t s);
-cudaError_t launch_bconv_tc(const DevTables &t, const BconvArgs &a, int max_in, cudaStream_t s);
-cudaError_t launch_ew(const DevTables &t, int op, const SegList &sl, const KsArgs &ks, cudaStream_t s);
+                       cudaStream_t s);
+cudaError_t launch_bconv(const DevTables &t, const BconvArgs &a, int max_in, int max_out, cudaStream_t s);
+cudaError_t launch_bconv_tc(const DevTables &t, const BconvArgs &a, int max_in, int max_out, cudaStream_t s);
+cudaError_t launch_ew(const DevTables &t, int op, const SegList &sl, cudaStream_t s);
 // key inner product (both halves) for the ext limbs of sl; seg.dst = u_0[t0]
-cudaError_t launch_ip(const DevTables &t, const SegList &sl, const KsArgs &ks, cudaStream_t s);
-cudaError_t launch_tensor(const DevTables &t, const uint32_t *a, const uint32_t *b, uint32_t *d, int level,
-                          cudaStream_t s);
+cudaError_t launch_ip(const DevTables &t, const SegList &sl, bool gather_own, bool gather_ext, cudaStream_t s);
 
 // number of kernels launched since the counter was last read (for the benchmark's launch count)
 long long kernel_launches();

@@ -66,18 +66,34 @@ struct NttGeom {
   }
 };
 
+// Element k (0..S) of a thread's sub-transform for register slot e in a round:
+// the "hi" round puts e on k's bits 7..4 (tau on 3..0), the "lo" round on bits
+// 3..0; with R == 4 there is one round and k = e.
+template <int R>
+__device__ __forceinline__ int kmap(bool hi, int e, int tau) {
+  return R == 4 ? e : (hi ? ((e << 4) | tau) : ((tau << 4) | e));
+}
+
+// dynamic shared memory of a pass: its staged twiddles (the column pass: the S - 1
+// twiddles of its R stages, shared by every column; the block pass: the 240
+// twiddles of its first four stages for its 16 blocks, 16 2^sigma at 16 (2^sigma - 1))
+__host__ __device__ constexpr int ntt_twiddle_smem(bool column, int S) { return (column ? S : 240) * 8; }
+
 template <int LOGN, bool COLUMN, bool FWD, int PRO, int EPI>
-__global__ void __launch_bounds__(kNttThreads) k_ntt(const __grid_constant__ SegList sl, const NttTables tb,
-                                                     const __grid_constant__ KsArgs ks) {
+__global__ void __launch_bounds__(kNttThreads) k_ntt(const __grid_constant__ SegList sl, const NttTables tb) {
   using G = NttGeom<LOGN, COLUMN>;
-  constexpr int R = G::R, C = G::C, N = G::N, LOGD = G::LOGD;
-  __shared__ uint32_t sm[G::SMEM];
-  __shared__ uint2 tws[COLUMN ? G::S : 1];
+  constexpr int R = G::R, N = G::N, S0 = COLUMN ? 0 : LOGN - 8;
+  // staged twiddles: the column pass needs the S - 1 twiddles of stages 0..R-1 (shared
+  // by all columns); the block pass needs, per stage sigma of its 8, the 16 2^sigma
+  // twiddles of its 16 blocks, stored at 16 (2^sigma - 1).
+  __shared__ uint32_t sm[R == 8 ? G::SMEM : 1];
+  extern __shared__ uint2 tws[];  // dynamic: ntt_twiddle_smem(COLUMN, S) bytes
 
   const int v = blockIdx.x / G::TILES, tile = blockIdx.x % G::TILES;
   int within;
   const int si = seg_find(sl, v, within);
   const Seg &sg = seg_at(sl, si);
+  const KsArgs &ks = item_ks(sl, sg);
   const int prime = sg.prime + within;
   const PrimeC P = tb.pc[prime];
   const uint32_t q = P.q;
@@ -88,34 +104,16 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt(const __grid_constant__ Seg
 
   if (COLUMN) {
     for (int i = tid; i < G::S; i += kNttThreads) tws[i] = __ldg(tw + i);
+  } else {
+    const int blk0 = tile * 16;
+#pragma unroll
+    for (int sig = 0; sig < 4; sig++) {
+      const int cnt = 16 << sig;
+      const uint2 *from = tw + (1 << (S0 + sig)) + (blk0 << sig);
+      if (tid < cnt) tws[16 * ((1 << sig) - 1) + tid] = __ldg(from + tid);
+    }
   }
 
-  // ---- load the tile (coalesced along the contiguous direction)
-#pragma unroll 4
-  for (int it = 0; it < 16; it++) {
-    const int idx = it * kNttThreads + tid;
-    int c, k;
-    if (COLUMN) {
-      c = idx % C;
-      k = idx / C;
-    } else {
-      k = idx & 255;
-      c = idx >> 8;
-    }
-    const uint32_t j = G::gidx(tile, c, k);
-    uint32_t x;
-    if (PRO == PRO_PLAIN) {
-      x = __ldg(src + j);
-    } else if (PRO == PRO_GATHER) {
-      x = __ldg(src + galois_src(j, ks.galois_own, LOGN));
-    } else {  // PRO_REDUCE: value of another prime's limb, reduced exactly mod q
-      x = reduce_u64(__ldg(src + j), P);
-    }
-    sm[G::addr(c, k)] = x;
-  }
-  __syncthreads();
-
-  // ---- butterfly rounds, 4 stages per round in registers
   int c, tau;
   if (COLUMN && R == 4) {
     c = tid;
@@ -128,30 +126,88 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt(const __grid_constant__ Seg
     tau = tid & 15;
   }
   constexpr int ROUNDS = R / 4;
+  // round 0 is the hi round going forward (large distances first), lo going backward
+  const bool hi0 = (R == 8) && FWD;
+
+  // block pass, lo round (stages sigma = 4 + m, m = 0..3): thread (c, tau) uses the 2^m
+  // consecutive twiddles 2^(S0+sigma) + ((blk0 + c) << sigma) + (tau << m) + [0, 2^m), each
+  // exactly once; prefetch them into registers (tl[2^m - 1 + k]) with vector loads.
+  uint2 tl[COLUMN ? 1 : 15];
+  if (!COLUMN) {
+    const int blk = tile * 16 + c;
 #pragma unroll
-  for (int rho = 0; rho < ROUNDS; rho++) {
-    // hi round: e occupies k bits 7..4; lo round: k bits 3..0 (R == 4: k = e)
-    const bool hi = (R == 8) && (FWD ? rho == 0 : rho == 1);
-    uint32_t x[16];
+    for (int m = 0; m < 4; m++) {
+      const int sig = 4 + m;
+      const uint2 *from = tw + (1 << (S0 + sig)) + (blk << sig) + (tau << m);
+      if (m == 0) {
+        tl[0] = __ldg(from);
+      } else {
+#pragma unroll
+        for (int k2 = 0; k2 < (1 << m) / 2; k2++) {
+          const uint4 w = __ldg(reinterpret_cast<const uint4 *>(from) + k2);
+          tl[(1 << m) - 1 + 2 * k2] = make_uint2(w.x, w.y);
+          tl[(1 << m) - 1 + 2 * k2 + 1] = make_uint2(w.z, w.w);
+        }
+      }
+    }
+  }
+
+  // ---- round-0 elements straight from global memory (prologue applied)
+  uint32_t x[16];
+  if (!COLUMN && !hi0 && PRO == PRO_PLAIN) {
+    // inverse block pass: a thread's 16 elements are contiguous
+    const uint4 *p = reinterpret_cast<const uint4 *>(src + G::gidx(tile, c, kmap<R>(false, 0, tau)));
+#pragma unroll
+    for (int e4 = 0; e4 < 4; e4++) {
+      const uint4 w = __ldg(p + e4);
+      x[4 * e4] = w.x;
+      x[4 * e4 + 1] = w.y;
+      x[4 * e4 + 2] = w.z;
+      x[4 * e4 + 3] = w.w;
+    }
+  } else {
 #pragma unroll
     for (int e = 0; e < 16; e++) {
-      const int k = (R == 4) ? e : (hi ? ((e << 4) | tau) : ((tau << 4) | e));
-      x[e] = sm[G::addr(c, k)];
+      const uint32_t j = G::gidx(tile, c, kmap<R>(hi0, e, tau));
+      if (PRO == PRO_GATHER)
+        x[e] = __ldg(src + galois_src(j, ks.galois_own, LOGN));
+      else if (PRO == PRO_REDUCE)  // value of another prime's limb, reduced exactly mod q
+        x[e] = reduce_u64(__ldg(src + j), P);
+      else
+        x[e] = __ldg(src + j);
+    }
+  }
+  __syncthreads();  // staged twiddles
+
+#pragma unroll
+  for (int rho = 0; rho < ROUNDS; rho++) {
+    const bool hi = (R == 8) && (FWD ? rho == 0 : rho == 1);
+    if (rho > 0) {  // exchange through shared memory between the rounds
+#pragma unroll
+      for (int e = 0; e < 16; e++) sm[G::addr(c, kmap<R>(!hi, e, tau))] = x[e];
+      __syncthreads();
+#pragma unroll
+      for (int e = 0; e < 16; e++) x[e] = sm[G::addr(c, kmap<R>(hi, e, tau))];
     }
 #pragma unroll
     for (int i = 0; i < 4; i++) {
-      const int bit = FWD ? 3 - i : i;
-      const int kbit = hi ? bit + 4 : bit;
-      const int gbit = LOGD + kbit;                 // pair distance 2^gbit in the limb
-      const int s = LOGN - 1 - gbit;                // Cooley-Tukey stage index
+      const int bit = FWD ? 3 - i : i;          // register-slot bit of this butterfly stage
+      const int kbit = hi ? bit + 4 : bit;      // bit of k (pair distance 2^kbit inside the sub-transform)
+      // twiddle index = base (runtime, per round and stage) + (e >> (bit + 1))
+      int base;
+      if (COLUMN) {
+        const int s = R - 1 - kbit;  // Cooley-Tukey stage: psi^brv(2^s + (k_lo >> (kbit + 1)))
+        base = (1 << s) + ((R == 8 && !hi) ? (tau << (3 - bit)) : 0);
+      } else {
+        const int sig = 7 - kbit;    // stage within the pass; local index (c << sig) + (k_lo >> (kbit + 1))
+        base = 16 * ((1 << sig) - 1) + (c << sig);  // hi round only (sig < 4)
+      }
 #pragma unroll
       for (int e = 0; e < 16; e++) {
         if (e & (1 << bit)) continue;
         const int e2 = e | (1 << bit);
-        const int klo = (R == 4) ? e : (hi ? ((e << 4) | tau) : ((tau << 4) | e));
-        const uint32_t jlo = G::gidx(tile, c, klo);
-        const uint32_t widx = (1u << s) + (jlo >> (gbit + 1));
-        const uint2 W = COLUMN ? tws[widx] : __ldg(tw + widx);
+        // block pass lo round: register twiddle tl[2^m - 1 + (e >> (bit + 1))], m = 3 - bit
+        const uint2 W = (!COLUMN && !hi) ? tl[(1 << (3 - bit)) - 1 + (e >> (bit + 1))] : tws[base + (e >> (bit + 1))];
         if (FWD) {
           const uint32_t t = red2(shoup_lazy(x[e2], W.x, W.y, q), q);
           const uint32_t u = red2(x[e], q);
@@ -164,32 +220,37 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt(const __grid_constant__ Seg
         }
       }
     }
-#pragma unroll
-    for (int e = 0; e < 16; e++) {
-      const int k = (R == 4) ? e : (hi ? ((e << 4) | tau) : ((tau << 4) | e));
-      sm[G::addr(c, k)] = x[e];
-    }
-    __syncthreads();
   }
 
-  // ---- store the tile
+  // ---- epilogue straight from registers
+  const bool hiL = (R == 8) && !FWD;  // the last round
   uint2 scale = make_uint2(0, 0);
   if (EPI == EPI_SCALE || EPI == EPI_RESCALE) scale = sg.scale ? sg.scale[within] : tb.ninv[prime];
   uint2 pinv = make_uint2(0, 0);
   if (EPI == EPI_COMBINE) pinv = ks.pinv[prime];
-#pragma unroll 4
-  for (int it = 0; it < 16; it++) {
-    const int idx = it * kNttThreads + tid;
-    int cc, k;
-    if (COLUMN) {
-      cc = idx % C;
-      k = idx / C;
+  const bool contiguous = !COLUMN && !hiL;  // forward block pass: 16 consecutive elements per thread
+  const uint32_t j0 = G::gidx(tile, c, kmap<R>(hiL, 0, tau));
+  uint32_t a[16];  // second operand of the combine / rescale epilogues
+  if (EPI == EPI_RESCALE || EPI == EPI_COMBINE) {
+    const uint32_t *s2 = sg.src2 + (size_t)within * N;
+    if (contiguous) {
+#pragma unroll
+      for (int e4 = 0; e4 < 4; e4++) {
+        const uint4 w = __ldg(reinterpret_cast<const uint4 *>(s2 + j0) + e4);
+        a[4 * e4] = w.x;
+        a[4 * e4 + 1] = w.y;
+        a[4 * e4 + 2] = w.z;
+        a[4 * e4 + 3] = w.w;
+      }
     } else {
-      k = idx & 255;
-      cc = idx >> 8;
+#pragma unroll
+      for (int e = 0; e < 16; e++) a[e] = __ldg(s2 + G::gidx(tile, c, kmap<R>(hiL, e, tau)));
     }
-    const uint32_t j = G::gidx(tile, cc, k);
-    const uint32_t val = sm[G::addr(cc, k)];
+  }
+#pragma unroll
+  for (int e = 0; e < 16; e++) {
+    const uint32_t j = contiguous ? j0 + e : G::gidx(tile, c, kmap<R>(hiL, e, tau));
+    const uint32_t val = x[e];
     uint32_t o;
     if (EPI == EPI_LAZY) {
       o = val;
@@ -198,18 +259,24 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt(const __grid_constant__ Seg
     } else if (EPI == EPI_SCALE) {
       o = shoup(val, scale.x, scale.y, q);
     } else if (EPI == EPI_RESCALE) {
-      const uint32_t a = __ldg(sg.src2 + (size_t)within * N + j);
-      o = shoup(a + q - red2(val, q), scale.x, scale.y, q);
-    } else {  // EPI_COMBINE: limb t = t0 + within is a q-limb (< level)
+      o = shoup(a[e] + q - red2(val, q), scale.x, scale.y, q);
+    } else {  // EPI_COMBINE: limb t = t0 + within is a q-limb (< level); a = inner product u
       const int t = sg.t0 + within;
-      const uint32_t u = __ldg(sg.src2 + (size_t)within * N + j);
-      o = shoup(u + q - red2(val, q), pinv.x, pinv.y, q);
+      o = shoup(a[e] + q - red2(val, q), pinv.x, pinv.y, q);
       if (ks.addp && (sg.c == 0 || ks.add_c1)) {
         const uint32_t ja = ks.galois_add == 1u ? j : galois_src(j, ks.galois_add, LOGN);
         o = add_mod(o, __ldg(ks.addp + ((size_t)sg.c * ks.level + t) * N + ja), q);
       }
     }
-    dst[j] = o;
+    x[e] = o;
+  }
+  if (contiguous) {
+    uint4 *p = reinterpret_cast<uint4 *>(dst + j0);
+#pragma unroll
+    for (int e4 = 0; e4 < 4; e4++) p[e4] = make_uint4(x[4 * e4], x[4 * e4 + 1], x[4 * e4 + 2], x[4 * e4 + 3]);
+  } else {
+#pragma unroll
+    for (int e = 0; e < 16; e++) dst[G::gidx(tile, c, kmap<R>(hiL, e, tau))] = x[e];
   }
 }
 

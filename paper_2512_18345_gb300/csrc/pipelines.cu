@@ -21,6 +21,7 @@
 #include "ctx.h"
 #include "elementwise.cuh"
 #include "internal.h"
+#include "program.h"
 
 using namespace fhe;
 
@@ -39,7 +40,7 @@ static Seg mkseg(const uint32_t *src, uint32_t *dst, int n, int prime) {
   s.prime = prime;
   s.src_stride = 1;
   s.src_prime = -1;
-  s.digit = -1;
+
   return s;
 }
 
@@ -47,6 +48,7 @@ struct SegBuilder {
   SegList l;
   SegBuilder() {
     memset(&l, 0, sizeof l);
+    l.ks[0].galois_own = l.ks[0].galois_ext = l.ks[0].galois_add = 1;
   }
   void add(const Seg &s) {
     if (s.n <= 0) return;
@@ -60,180 +62,19 @@ static bool overlaps(const void *a, size_t abytes, const void *b, size_t bbytes)
   return x < y + bbytes && y < x + abytes;
 }
 
-// ------------------------------------------------------------------ stage 1: ModUp
-// d: [level][N] NTT form, read through sigma_{galois_d}.  Writes ext [beta][level+K][N]
-// (NTT form) except each digit's own limbs.
-int run_modup(fhe_ctx *c, const uint32_t *d, int level, uint32_t galois_d, uint32_t *ext, cudaStream_t s) {
-  const size_t N = c->N;
-  const int L = c->L, K = c->K, A = c->alpha, beta = c->beta(level), n_ext = level + K;
+[[maybe_unused]] static KsArgs ks_none() {
   KsArgs ks;
   memset(&ks, 0, sizeof ks);
-  ks.galois_own = galois_d;
-  ks.galois_ext = ks.galois_add = 1;
-  if (c->fused) {
-    SegBuilder first, second;
-    first.add(mkseg(d, c->wY, level, 0));
-    Seg s2 = mkseg(c->wY, c->wY, level, 0);
-    s2.scale = c->d_mu_scale + (size_t)(level - 1) * L;
-    second.add(s2);
-    LAUNCH_OR_FAIL(launch_ntt(c->tabs, false, galois_d != 1u ? PRO_GATHER : PRO_PLAIN, EPI_SCALE, first.l, second.l,
-                              ks, s));
-  } else {
-    const uint32_t *src = d;
-    if (galois_d != 1u) {
-      SegBuilder g;
-      g.add(mkseg(d, c->wTMP, level, 0));
-      LAUNCH_OR_FAIL(launch_ew(c->tabs, EW_GATHER, g.l, ks, s));
-      src = c->wTMP;
-    }
-    SegBuilder first, second, sc;
-    first.add(mkseg(src, c->wY, level, 0));
-    second.add(mkseg(c->wY, c->wY, level, 0));
-    LAUNCH_OR_FAIL(launch_ntt(c->tabs, false, PRO_PLAIN, EPI_SCALE, first.l, second.l, ks, s));
-    Seg s3 = mkseg(c->wY, c->wY, level, 0);
-    s3.scale = c->d_mu_qhinv + (size_t)(level - 1) * L;
-    sc.add(s3);
-    LAUNCH_OR_FAIL(launch_ew(c->tabs, EW_SCALE, sc.l, ks, s));
-  }
-  // base conversion of every digit
-  BconvArgs ba;
-  memset(&ba, 0, sizeof ba);
-  int max_in = 0;
-  for (int j = 0; j < beta; j++) {
-    const int lo = j * A, hi = std::min((j + 1) * A, level);
-    BconvGroup &g = ba.g[ba.ngroups++];
-    g.in = c->wY + (size_t)lo * N;
-    g.out = ext + (size_t)j * n_ext * N;
-    g.T = c->modup_T[(size_t)(level - 1) * c->dnum + j];
-    g.omap = c->modup_map[(size_t)(level - 1) * c->dnum + j];
-    g.n_in = hi - lo;
-    g.n_out = n_ext - (hi - lo);
-    max_in = std::max(max_in, hi - lo);
-  }
-  if (c->bconv_mode == FHE_BCONV_TC)
-    LAUNCH_OR_FAIL(launch_bconv_tc(c->tabs, ba, max_in, s));
-  else
-    LAUNCH_OR_FAIL(launch_bconv(c->tabs, ba, max_in, s));
-  // NTT of the converted limbs of every digit (runs of consecutive primes)
-  SegBuilder nt;
-  for (int j = 0; j < beta; j++) {
-    const int lo = j * A, hi = std::min((j + 1) * A, level);
-    uint32_t *e = ext + (size_t)j * n_ext * N;
-    nt.add(mkseg(e, e, lo, 0));
-    nt.add(mkseg(e + (size_t)hi * N, e + (size_t)hi * N, level - hi, hi));
-    nt.add(mkseg(e + (size_t)level * N, e + (size_t)level * N, K, L));
-  }
-  LAUNCH_OR_FAIL(launch_ntt(c->tabs, true, PRO_PLAIN, EPI_PLAIN, nt.l, nt.l, ks, s));
-  return FHE_OK;
-}
-
-// ------------------------------------------------------------------ stages 2 + 3: inner product, ModDown
-// ks carries ext, own (+ galois), key, addp (+ galois, add_c1).  Writes out [2][level][N].
-//
-// Fused pipeline (complementary pipelining, Section IV-B): the inner product
-// of the K special limbs is computed first and feeds ModDown's INTT / BConv /
-// NTT chain; the inner product of the l ciphertext limbs (the DRAM-bound part:
-// it streams 2 beta l key limbs) runs concurrently on the context's auxiliary
-// stream and is joined only before the last NTT pass, whose epilogue does the
-// combine (u - NTT(r)) P^-1 + add.
-int run_moddown(fhe_ctx *c, KsArgs ks, int level, uint32_t *out, cudaStream_t s) {
-  const size_t N = c->N;
-  const int L = c->L, K = c->K, n_ext = level + K;
-  ks.level = level;
-  ks.n_ext = n_ext;
-  ks.beta = c->beta(level);
-  ks.alpha = c->alpha;
-  ks.L = L;
-  ks.K = K;
-  ks.pinv = c->d_pinv;
-  BconvArgs ba;
-  memset(&ba, 0, sizeof ba);
-  for (int cc = 0; cc < 2; cc++) {
-    BconvGroup &g = ba.g[ba.ngroups++];
-    g.in = c->wUC + (size_t)cc * K * N;
-    g.out = c->wR + (size_t)cc * level * N;
-    g.T = c->d_mdT;
-    g.omap = c->d_mdmap;
-    g.n_in = K;
-    g.n_out = level;
-  }
-  SegBuilder ipq, ipp;
-  {
-    Seg a = mkseg(nullptr, c->wU, level, 0);
-    a.t0 = 0;
-    a.key_row0 = 0;
-    ipq.add(a);
-    Seg b = mkseg(nullptr, c->wU + (size_t)level * N, K, L);
-    b.t0 = level;
-    b.key_row0 = L;
-    ipp.add(b);
-  }
-  SegBuilder first, second, sc, na, nb;
-  for (int cc = 0; cc < 2; cc++) {
-    uint32_t *uc = c->wUC + (size_t)cc * K * N;
-    first.add(mkseg(c->wU + ((size_t)cc * n_ext + level) * N, uc, K, L));
-    Seg b = mkseg(uc, uc, K, L);
-    if (c->fused) b.scale = c->d_md_scale;
-    second.add(b);
-    Seg x = mkseg(uc, uc, K, L);
-    x.scale = c->d_md_phinv;
-    sc.add(x);
-    uint32_t *r = c->wR + (size_t)cc * level * N;
-    na.add(mkseg(r, r, level, 0));
-    Seg y = mkseg(r, out + (size_t)cc * level * N, level, 0);
-    y.src2 = c->wU + (size_t)cc * n_ext * N;
-    y.t0 = 0;
-    y.c = cc;
-    nb.add(y);
-  }
-  if (c->fused) {
-    LAUNCH_OR_FAIL(cudaEventRecord(c->ev_fork, s));
-    LAUNCH_OR_FAIL(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
-    LAUNCH_OR_FAIL(launch_ip(c->tabs, ipq.l, ks, c->aux));
-    LAUNCH_OR_FAIL(cudaEventRecord(c->ev_join, c->aux));
-    LAUNCH_OR_FAIL(launch_ip(c->tabs, ipp.l, ks, s));
-    LAUNCH_OR_FAIL(launch_ntt(c->tabs, false, PRO_PLAIN, EPI_SCALE, first.l, second.l, ks, s));
-    if (c->bconv_mode == FHE_BCONV_TC)
-      LAUNCH_OR_FAIL(launch_bconv_tc(c->tabs, ba, K, s));
-    else
-      LAUNCH_OR_FAIL(launch_bconv(c->tabs, ba, K, s));
-    LAUNCH_OR_FAIL(launch_ntt_pass(c->tabs, true, true, PRO_PLAIN, EPI_LAZY, na.l, ks, s));
-    LAUNCH_OR_FAIL(cudaStreamWaitEvent(s, c->ev_join, 0));
-    LAUNCH_OR_FAIL(launch_ntt_pass(c->tabs, false, true, PRO_PLAIN, EPI_COMBINE, nb.l, ks, s));
-    return FHE_OK;
-  }
-  // plain: every step its own kernel, in order
-  SegBuilder ip;
-  ip.add(ipq.l.seg[0]);
-  ip.add(ipp.l.seg[0]);
-  LAUNCH_OR_FAIL(launch_ip(c->tabs, ip.l, ks, s));
-  LAUNCH_OR_FAIL(launch_ntt(c->tabs, false, PRO_PLAIN, EPI_SCALE, first.l, second.l, ks, s));
-  LAUNCH_OR_FAIL(launch_ew(c->tabs, EW_SCALE, sc.l, ks, s));
-  if (c->bconv_mode == FHE_BCONV_TC)
-    LAUNCH_OR_FAIL(launch_bconv_tc(c->tabs, ba, K, s));
-  else
-    LAUNCH_OR_FAIL(launch_bconv(c->tabs, ba, K, s));
-  LAUNCH_OR_FAIL(launch_ntt(c->tabs, true, PRO_PLAIN, EPI_PLAIN, na.l, na.l, ks, s));
-  SegBuilder cb;
-  for (int cc = 0; cc < 2; cc++) {
-    Seg x = mkseg(c->wU + (size_t)cc * n_ext * N, out + (size_t)cc * level * N, level, 0);
-    x.src2 = c->wR + (size_t)cc * level * N;
-    x.t0 = 0;
-    x.c = cc;
-    cb.add(x);
-  }
-  LAUNCH_OR_FAIL(launch_ew(c->tabs, EW_COMBINE, cb.l, ks, s));
-  return FHE_OK;
-}
-
-static KsArgs ks_base(const uint32_t *own, const uint32_t *ext, const uint32_t *key) {
-  KsArgs ks;
-  memset(&ks, 0, sizeof ks);
-  ks.own = own;
-  ks.ext = ext;
-  ks.key = key;
   ks.galois_own = ks.galois_ext = ks.galois_add = 1;
   return ks;
+}
+
+// run a program of at most kMaxInlineItems items with by-value launch arguments
+static int run_items(fhe_ctx *c, const std::vector<Item> &items, cudaStream_t s) {
+  Program P;
+  int rc = build_program(c, items, c->fused != 0, P);
+  if (rc != FHE_OK) return rc;
+  return run_program_inline(c, P, s);
 }
 
 static int check_level(const fhe_ctx *c, int level, const char *fn) {
@@ -266,8 +107,13 @@ extern "C" int fhe_keyswitch(fhe_ctx *c, const uint32_t *d, int level, int32_t k
   cudaSetDevice(c->device);
   cudaStream_t s = (cudaStream_t)stream;
   c->order_stream(s);
-  CHECK(run_modup(c, d, level, 1u, c->wEXT, s));
-  return run_moddown(c, ks_base(d, c->wEXT, key), level, out, s);
+  Item it;
+  it.kind = IT_KS;
+  it.level = level;
+  it.in = d;
+  it.out = out;
+  it.key = key;
+  return run_items(c, {it}, s);
 }
 
 extern "C" int fhe_rotate(fhe_ctx *c, const uint32_t *ct, int level, int32_t rot, uint32_t *out, fhe_stream stream) {
@@ -289,12 +135,14 @@ extern "C" int fhe_rotate(fhe_ctx *c, const uint32_t *ct, int level, int32_t rot
   const uint32_t *key = c->find_key(rot);
   if (!key) return fhe_fail(FHE_ENOKEY, "fhe_rotate: no rotation key for %d", rot);
   c->order_stream(s);
-  CHECK(run_modup(c, ct + poly, level, k, c->wEXT, s));
-  KsArgs ks = ks_base(ct + poly, c->wEXT, key);
-  ks.galois_own = k;
-  ks.addp = ct;
-  ks.galois_add = k;
-  return run_moddown(c, ks, level, out, s);
+  Item it;
+  it.kind = IT_ROTATE;
+  it.level = level;
+  it.galois = k;
+  it.in = ct;
+  it.out = out;
+  it.key = key;
+  return run_items(c, {it}, s);
 }
 
 extern "C" int fhe_hmult(fhe_ctx *c, const uint32_t *a, const uint32_t *b, int level, uint32_t *out,
@@ -308,13 +156,14 @@ extern "C" int fhe_hmult(fhe_ctx *c, const uint32_t *a, const uint32_t *b, int l
   cudaSetDevice(c->device);
   cudaStream_t s = (cudaStream_t)stream;
   c->order_stream(s);
-  const size_t poly = (size_t)level * c->N;
-  LAUNCH_OR_FAIL(launch_tensor(c->tabs, a, b, c->wD, level, s));
-  CHECK(run_modup(c, c->wD + 2 * poly, level, 1u, c->wEXT, s));
-  KsArgs ks = ks_base(c->wD + 2 * poly, c->wEXT, c->relin_key);
-  ks.addp = c->wD;
-  ks.add_c1 = 1;
-  return run_moddown(c, ks, level, out, s);
+  Item it;
+  it.kind = IT_RELIN;
+  it.level = level;
+  it.in = a;
+  it.in2 = b;
+  it.out = out;
+  it.key = c->relin_key;
+  return run_items(c, {it}, s);
 }
 
 extern "C" int fhe_rescale(fhe_ctx *c, const uint32_t *ct, int level, uint32_t *out, fhe_stream stream) {
@@ -327,16 +176,16 @@ extern "C" int fhe_rescale(fhe_ctx *c, const uint32_t *ct, int level, uint32_t *
   cudaSetDevice(c->device);
   cudaStream_t s = (cudaStream_t)stream;
   c->order_stream(s);
-  KsArgs ks = ks_base(nullptr, nullptr, nullptr);
+  uint32_t *V = c->slots[0].V;
   SegBuilder f1, f2, g1, g2;
   for (int cc = 0; cc < 2; cc++) {
-    f1.add(mkseg(ct + cc * poly + (size_t)(level - 1) * N, c->wV + cc * N, 1, level - 1));
-    f2.add(mkseg(c->wV + cc * N, c->wV + cc * N, 1, level - 1));
+    f1.add(mkseg(ct + cc * poly + (size_t)(level - 1) * N, V + cc * N, 1, level - 1));
+    f2.add(mkseg(V + cc * N, V + cc * N, 1, level - 1));
   }
-  LAUNCH_OR_FAIL(launch_ntt(c->tabs, false, PRO_PLAIN, EPI_SCALE, f1.l, f2.l, ks, s));
+  LAUNCH_OR_FAIL(launch_ntt(c->tabs, false, PRO_PLAIN, EPI_SCALE, f1.l, f2.l, s));
   for (int cc = 0; cc < 2; cc++) {
     uint32_t *o = out + (size_t)cc * (level - 1) * N;
-    Seg a = mkseg(c->wV + cc * N, o, level - 1, 0);
+    Seg a = mkseg(V + cc * N, o, level - 1, 0);
     a.src_stride = 0;
     a.src_prime = level - 1;
     g1.add(a);
@@ -345,7 +194,7 @@ extern "C" int fhe_rescale(fhe_ctx *c, const uint32_t *ct, int level, uint32_t *
     b.scale = c->d_rs_qinv + (size_t)(level - 1) * c->L;
     g2.add(b);
   }
-  LAUNCH_OR_FAIL(launch_ntt(c->tabs, true, PRO_REDUCE, EPI_RESCALE, g1.l, g2.l, ks, s));
+  LAUNCH_OR_FAIL(launch_ntt(c->tabs, true, PRO_REDUCE, EPI_RESCALE, g1.l, g2.l, s));
   return FHE_OK;
 }
 
@@ -368,9 +217,9 @@ extern "C" int fhe_rotate_hoisted(fhe_ctx *c, const uint32_t *ct, int level, con
   cudaSetDevice(c->device);
   cudaStream_t s = (cudaStream_t)stream;
   c->order_stream(s);
-  bool need_modup = false;
-  for (int r = 0; r < n; r++) need_modup |= fhe_galois_elt(rots[r], c->N) != 1u;
-  if (need_modup) CHECK(run_modup(c, ct + poly, level, 1u, c->wEXT, s));
+  // one shared ModUp of c1 (slot 0), then the rotations' ModDowns batched
+  // kMaxInlineItems - 1 at a time, each with its own slot
+  std::vector<Item> todo;
   for (int r = 0; r < n; r++) {
     const uint32_t k = fhe_galois_elt(rots[r], c->N);
     if (k == 1u) {
@@ -378,10 +227,32 @@ extern "C" int fhe_rotate_hoisted(fhe_ctx *c, const uint32_t *ct, int level, con
         return fhe_fail(FHE_ECUDA, "fhe_rotate_hoisted: copy");
       continue;
     }
-    KsArgs ks = ks_base(ct + poly, c->wEXT, keys[r]);
-    ks.galois_own = ks.galois_ext = ks.galois_add = k;
-    ks.addp = ct;
-    CHECK(run_moddown(c, ks, level, outs[r], s));
+    Item it;
+    it.kind = IT_MODDOWN;
+    it.level = level;
+    it.galois = k;
+    it.in = ct;
+    it.out = outs[r];
+    it.key = keys[r];
+    it.ext_slot = 0;
+    todo.push_back(it);
+  }
+  if (todo.empty()) return FHE_OK;
+  Item up;
+  up.kind = IT_MODUP;
+  up.level = level;
+  up.in = ct + poly;
+  up.slot = 0;
+  const int per = kMaxInlineItems - 1;
+  for (size_t b = 0; b < todo.size(); b += per) {
+    std::vector<Item> batch;
+    if (b == 0) batch.push_back(up);
+    for (size_t r = b; r < std::min(todo.size(), b + per); r++) {
+      Item it = todo[r];
+      it.slot = 1 + (int)(r - b);
+      batch.push_back(it);
+    }
+    CHECK(run_items(c, batch, s));
   }
   return FHE_OK;
 }
@@ -396,7 +267,7 @@ static int elementwise2(fhe_ctx *c, int op, const uint32_t *a, const uint32_t *b
     sb.add(x);
   }
   c->order_stream(s);
-  LAUNCH_OR_FAIL(launch_ew(c->tabs, op, sb.l, ks_base(nullptr, nullptr, nullptr), s));
+  LAUNCH_OR_FAIL(launch_ew(c->tabs, op, sb.l, s));
   return FHE_OK;
 }
 
@@ -444,8 +315,7 @@ static int transform(fhe_ctx *c, uint32_t *a, const int *idx, int n, bool fwd, f
       sb.add(mkseg(a + (size_t)i * N, a + (size_t)i * N, j - i, idx[i]));
       i = j;
     }
-    LAUNCH_OR_FAIL(launch_ntt(c->tabs, fwd, PRO_PLAIN, fwd ? EPI_PLAIN : EPI_SCALE, sb.l, sb.l,
-                              ks_base(nullptr, nullptr, nullptr), s));
+    LAUNCH_OR_FAIL(launch_ntt(c->tabs, fwd, PRO_PLAIN, fwd ? EPI_PLAIN : EPI_SCALE, sb.l, sb.l, s));
   }
   return FHE_OK;
 }
@@ -468,7 +338,14 @@ extern "C" int fhe_modup(fhe_ctx *c, const uint32_t *d, int level, uint32_t *ext
   cudaSetDevice(c->device);
   cudaStream_t s = (cudaStream_t)stream;
   c->order_stream(s);
-  CHECK(run_modup(c, d, level, 1u, ext, s));
+  Item it;
+  it.kind = IT_MODUP;
+  it.level = level;
+  it.in = d;
+  it.slot = 0;
+  CHECK(run_items(c, {it}, s));
+  if (cudaMemcpyAsync(ext, c->slots[0].EXT, 4 * N * (size_t)beta * n_ext, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return fhe_fail(FHE_ECUDA, "fhe_modup: copy");
   for (int j = 0; j < beta; j++) {
     const int lo = j * c->alpha, hi = std::min((j + 1) * c->alpha, level);
     if (cudaMemcpyAsync(ext + ((size_t)j * n_ext + lo) * N, d + (size_t)lo * N, 4 * N * (hi - lo),
@@ -489,34 +366,34 @@ extern "C" int fhe_moddown(fhe_ctx *c, const uint32_t *u, int level, uint32_t *o
   cudaSetDevice(c->device);
   cudaStream_t s = (cudaStream_t)stream;
   c->order_stream(s);
-  KsArgs ks = ks_base(nullptr, nullptr, nullptr);
-  ks.pinv = c->d_pinv;
-  ks.level = level;
+  uint32_t *UC = c->slots[0].UC, *R = c->slots[0].R;
   SegBuilder first, second, nr, cb;
-  first.add(mkseg(u + (size_t)level * N, c->wUC, K, L));
-  Seg b = mkseg(c->wUC, c->wUC, K, L);
+  first.add(mkseg(u + (size_t)level * N, UC, K, L));
+  Seg b = mkseg(UC, UC, K, L);
   b.scale = c->d_md_scale;
   second.add(b);
-  LAUNCH_OR_FAIL(launch_ntt(c->tabs, false, PRO_PLAIN, EPI_SCALE, first.l, second.l, ks, s));
+  LAUNCH_OR_FAIL(launch_ntt(c->tabs, false, PRO_PLAIN, EPI_SCALE, first.l, second.l, s));
   BconvArgs ba;
   memset(&ba, 0, sizeof ba);
   BconvGroup &g = ba.g[ba.ngroups++];
-  g.in = c->wUC;
-  g.out = c->wR;
+  g.in = UC;
+  g.out = R;
   g.T = c->d_mdT;
   g.omap = c->d_mdmap;
   g.n_in = K;
   g.n_out = level;
   if (c->bconv_mode == FHE_BCONV_TC)
-    LAUNCH_OR_FAIL(launch_bconv_tc(c->tabs, ba, K, s));
+    LAUNCH_OR_FAIL(launch_bconv_tc(c->tabs, ba, K, level, s));
   else
-    LAUNCH_OR_FAIL(launch_bconv(c->tabs, ba, K, s));
-  nr.add(mkseg(c->wR, c->wR, level, 0));
-  LAUNCH_OR_FAIL(launch_ntt(c->tabs, true, PRO_PLAIN, EPI_PLAIN, nr.l, nr.l, ks, s));
+    LAUNCH_OR_FAIL(launch_bconv(c->tabs, ba, K, level, s));
+  nr.add(mkseg(R, R, level, 0));
+  LAUNCH_OR_FAIL(launch_ntt(c->tabs, true, PRO_PLAIN, EPI_PLAIN, nr.l, nr.l, s));
   Seg x = mkseg(u, out, level, 0);
-  x.src2 = c->wR;
+  x.src2 = R;
   cb.add(x);
-  LAUNCH_OR_FAIL(launch_ew(c->tabs, EW_COMBINE, cb.l, ks, s));
+  cb.l.ks[0].pinv = c->d_pinv;
+  cb.l.ks[0].level = level;
+  LAUNCH_OR_FAIL(launch_ew(c->tabs, EW_COMBINE, cb.l, s));
   return FHE_OK;
 }
 
@@ -585,7 +462,7 @@ extern "C" int fhe_bconv(fhe_ctx *c, const uint32_t *in, const int *in_idx, int 
       x.scale = dPre + j;
       sb.add(x);
     }
-    if (launch_ew(c->tabs, EW_SCALE, sb.l, ks_base(nullptr, nullptr, nullptr), s) != cudaSuccess)
+    if (launch_ew(c->tabs, EW_SCALE, sb.l, s) != cudaSuccess)
       rc = fhe_fail(FHE_ECUDA, "fhe_bconv: scale");
   }
   BconvArgs ba;
@@ -598,7 +475,8 @@ extern "C" int fhe_bconv(fhe_ctx *c, const uint32_t *in, const int *in_idx, int 
   g.n_in = n_in;
   g.n_out = n_out;
   if (rc == FHE_OK) {
-    cudaError_t e = c->bconv_mode == FHE_BCONV_TC ? launch_bconv_tc(c->tabs, ba, n_in, s) : launch_bconv(c->tabs, ba, n_in, s);
+    cudaError_t e = c->bconv_mode == FHE_BCONV_TC ? launch_bconv_tc(c->tabs, ba, n_in, n_out, s)
+                                                  : launch_bconv(c->tabs, ba, n_in, n_out, s);
     if (e != cudaSuccess) rc = fhe_fail(FHE_ECUDA, "fhe_bconv: %s", cudaGetErrorString(e));
   }
   // the temporary tables are released once the stream has consumed them

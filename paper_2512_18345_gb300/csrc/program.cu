@@ -1,0 +1,379 @@
+// Stage-program builder and executors (see program.h).
+#include <algorithm>
+#include <cstring>
+
+#include "../../include/fhe.h"
+#include "elementwise.cuh"
+#include "program.h"
+
+using namespace fhe;
+
+static Seg seg(const uint32_t *src, uint32_t *dst, int n, int prime, int item) {
+  Seg s;
+  memset(&s, 0, sizeof s);
+  s.src = src;
+  s.dst = dst;
+  s.n = n;
+  s.prime = prime;
+  s.src_stride = 1;
+  s.src_prime = -1;
+  s.item = item;
+  s.galois = 1;
+  return s;
+}
+
+static void add(Stage &st, const Seg &s) {
+  if (s.n > 0) st.segs.push_back(s);
+}
+
+static Stage ntt_stage(bool column, bool fwd, int pro, int epi) {
+  Stage s;
+  s.kind = Stage::NTT;
+  s.column = column;
+  s.fwd = fwd;
+  s.pro = pro;
+  s.epi = epi;
+  return s;
+}
+
+static Stage ew_stage(int op) {
+  Stage s;
+  s.kind = Stage::EW;
+  s.ewop = op;
+  return s;
+}
+
+static Stage marker(Stage::Kind k) {
+  Stage s;
+  s.kind = k;
+  return s;
+}
+
+int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Program &P) {
+  const size_t N = c->N;
+  const int L = c->L, K = c->K, A = c->alpha;
+  P.ks.clear();
+  P.stages.clear();
+  int max_slot = 0;
+  for (const Item &it : items) max_slot = std::max(max_slot, std::max(it.slot, it.ext_slot));
+  int rc = ensure_slots(c, max_slot + 1);
+  if (rc != FHE_OK) return rc;
+
+  // per-item arguments and the polynomial each item key-switches
+  std::vector<const uint32_t *> dpoly(items.size(), nullptr);
+  for (size_t i = 0; i < items.size(); i++) {
+    const Item &it = items[i];
+    const fhe_ctx::Slot &S = c->slots[it.slot];
+    const size_t poly = (size_t)it.level * N;
+    KsArgs k;
+    memset(&k, 0, sizeof k);
+    k.ext = S.EXT;
+    k.key = it.key;
+    k.pinv = c->d_pinv;
+    k.level = it.level;
+    k.n_ext = it.level + K;
+    k.beta = c->beta(it.level);
+    k.alpha = A;
+    k.L = L;
+    k.K = K;
+    k.galois_own = k.galois_ext = k.galois_add = 1;
+    switch (it.kind) {
+      case IT_KS:
+        dpoly[i] = it.in;
+        break;
+      case IT_ROTATE:
+        dpoly[i] = it.in + poly;
+        k.galois_own = k.galois_add = it.galois;
+        k.addp = it.in;
+        break;
+      case IT_RELIN:
+        dpoly[i] = S.D + 2 * poly;
+        k.addp = S.D;
+        k.add_c1 = 1;
+        break;
+      case IT_MODUP:  // `in` is the polynomial itself
+        dpoly[i] = it.in;
+        break;
+      case IT_MODDOWN:
+        k.ext = c->slots[it.ext_slot].EXT;
+        k.galois_own = k.galois_ext = k.galois_add = it.galois;
+        k.addp = it.in;
+        break;
+    }
+    k.own = it.kind == IT_MODDOWN ? it.in + poly : dpoly[i];
+    // the plain pipeline gathers the rotated polynomial into TMP first
+    if (!fused && it.kind == IT_ROTATE && it.galois != 1u) {
+      k.own = S.TMP;
+      k.galois_own = 1;
+    }
+    P.ks.push_back(k);
+  }
+  auto has_modup = [](const Item &it) { return it.kind != IT_MODDOWN; };
+  auto has_moddown = [](const Item &it) { return it.kind != IT_MODUP; };
+
+  // ---- HMult tensor
+  Stage tensor = ew_stage(EW_TENSOR);
+  for (size_t i = 0; i < items.size(); i++)
+    if (items[i].kind == IT_RELIN) {
+      Seg s = seg(items[i].in, c->slots[items[i].slot].D, items[i].level, 0, (int)i);
+      s.src2 = items[i].in2;
+      add(tensor, s);
+    }
+  if (!tensor.segs.empty()) P.stages.push_back(tensor);
+
+  // ---- stage 1: ModUp
+  bool any_rot = false;
+  for (const Item &it : items) any_rot |= has_modup(it) && it.kind == IT_ROTATE && it.galois != 1u;
+  Stage gather = ew_stage(EW_GATHER);
+  Stage i1 = ntt_stage(false, false, (fused && any_rot) ? PRO_GATHER : PRO_PLAIN, EPI_LAZY);
+  Stage i2 = ntt_stage(true, false, PRO_PLAIN, EPI_SCALE);
+  Stage sc = ew_stage(EW_SCALE);
+  Stage bc;
+  bc.kind = Stage::BCONV;
+  Stage n1 = ntt_stage(true, true, PRO_PLAIN, EPI_LAZY);
+  for (size_t i = 0; i < items.size(); i++) {
+    const Item &it = items[i];
+    if (!has_modup(it)) continue;
+    const fhe_ctx::Slot &S = c->slots[it.slot];
+    const int level = it.level, n_ext = level + K, beta = c->beta(level);
+    const uint32_t *src = dpoly[i];
+    if (!fused && it.kind == IT_ROTATE && it.galois != 1u) {
+      Seg gs = seg(src, S.TMP, level, 0, (int)i);
+      gs.galois = it.galois;
+      add(gather, gs);
+      src = S.TMP;
+    }
+    add(i1, seg(src, S.Y, level, 0, (int)i));
+    Seg y = seg(S.Y, S.Y, level, 0, (int)i);
+    if (fused) y.scale = c->d_mu_scale + (size_t)(level - 1) * L;
+    add(i2, y);
+    Seg z = seg(S.Y, S.Y, level, 0, (int)i);
+    z.scale = c->d_mu_qhinv + (size_t)(level - 1) * L;
+    add(sc, z);
+    for (int j = 0; j < beta; j++) {
+      const int lo = j * A, hi = std::min((j + 1) * A, level);
+      BconvGroup g;
+      g.in = S.Y + (size_t)lo * N;
+      g.out = S.EXT + (size_t)j * n_ext * N;
+      g.T = c->modup_T[(size_t)(level - 1) * c->dnum + j];
+      g.omap = c->modup_map[(size_t)(level - 1) * c->dnum + j];
+      g.n_in = hi - lo;
+      g.n_out = n_ext - (hi - lo);
+      bc.groups.push_back(g);
+      bc.max_in = std::max(bc.max_in, g.n_in);
+      bc.max_out = std::max(bc.max_out, g.n_out);
+      uint32_t *e = S.EXT + (size_t)j * n_ext * N;
+      add(n1, seg(e, e, lo, 0, (int)i));
+      add(n1, seg(e + (size_t)hi * N, e + (size_t)hi * N, level - hi, hi, (int)i));
+      add(n1, seg(e + (size_t)level * N, e + (size_t)level * N, K, L, (int)i));
+    }
+  }
+  if (!i1.segs.empty()) {
+    if (!fused && !gather.segs.empty()) P.stages.push_back(gather);
+    P.stages.push_back(i1);
+    P.stages.push_back(i2);
+    if (!fused) P.stages.push_back(sc);
+    P.stages.push_back(bc);
+    P.stages.push_back(n1);
+    Stage n2 = n1;
+    n2.column = false;
+    n2.epi = EPI_PLAIN;
+    P.stages.push_back(n2);
+  }
+
+  // ---- stages 2 and 3: inner product, ModDown
+  Stage ipq;
+  ipq.kind = Stage::IP;
+  Stage ipp = ipq;
+  Stage m1 = ntt_stage(false, false, PRO_PLAIN, EPI_LAZY);
+  Stage m2 = ntt_stage(true, false, PRO_PLAIN, EPI_SCALE);
+  Stage msc = ew_stage(EW_SCALE);
+  Stage mbc;
+  mbc.kind = Stage::BCONV;
+  Stage r1 = ntt_stage(true, true, PRO_PLAIN, EPI_LAZY);
+  Stage r2 = ntt_stage(false, true, PRO_PLAIN, fused ? EPI_COMBINE : EPI_PLAIN);
+  Stage cb = ew_stage(EW_COMBINE);
+  for (size_t i = 0; i < items.size(); i++) {
+    const Item &it = items[i];
+    if (!has_moddown(it)) continue;
+    const fhe_ctx::Slot &S = c->slots[it.slot];
+    const int level = it.level, n_ext = level + K;
+    const KsArgs &k = P.ks[i];
+    ipq.gather_own |= k.galois_own != 1u;
+    ipq.gather_ext |= k.galois_ext != 1u;
+    Seg a = seg(nullptr, S.U, level, 0, (int)i);
+    a.t0 = 0;
+    a.key_row0 = 0;
+    add(ipq, a);
+    Seg b = seg(nullptr, S.U + (size_t)level * N, K, L, (int)i);
+    b.t0 = level;
+    b.key_row0 = L;
+    add(ipp, b);
+    for (int cc = 0; cc < 2; cc++) {
+      uint32_t *uc = S.UC + (size_t)cc * K * N, *r = S.R + (size_t)cc * level * N;
+      add(m1, seg(S.U + ((size_t)cc * n_ext + level) * N, uc, K, L, (int)i));
+      Seg x = seg(uc, uc, K, L, (int)i);
+      if (fused) x.scale = c->d_md_scale;
+      add(m2, x);
+      Seg y = seg(uc, uc, K, L, (int)i);
+      y.scale = c->d_md_phinv;
+      add(msc, y);
+      BconvGroup g;
+      g.in = uc;
+      g.out = r;
+      g.T = c->d_mdT;
+      g.omap = c->d_mdmap;
+      g.n_in = K;
+      g.n_out = level;
+      mbc.groups.push_back(g);
+      mbc.max_in = std::max(mbc.max_in, K);
+      mbc.max_out = std::max(mbc.max_out, level);
+      add(r1, seg(r, r, level, 0, (int)i));
+      Seg z = fused ? seg(r, it.out + (size_t)cc * level * N, level, 0, (int)i) : seg(r, r, level, 0, (int)i);
+      z.src2 = S.U + (size_t)cc * n_ext * N;
+      z.c = cc;
+      add(r2, z);
+      Seg w = seg(S.U + (size_t)cc * n_ext * N, it.out + (size_t)cc * level * N, level, 0, (int)i);
+      w.src2 = r;
+      w.c = cc;
+      add(cb, w);
+    }
+  }
+  ipp.gather_own = ipq.gather_own;
+  ipp.gather_ext = ipq.gather_ext;
+  if (!ipq.segs.empty()) {
+    if (fused) {
+      P.stages.push_back(marker(Stage::FORK));
+      ipq.aux = true;
+      P.stages.push_back(ipq);
+      P.stages.push_back(marker(Stage::JOIN_RECORD));
+      P.stages.push_back(ipp);
+    } else {
+      Stage all = ipq;
+      all.segs.insert(all.segs.end(), ipp.segs.begin(), ipp.segs.end());
+      P.stages.push_back(all);
+    }
+    P.stages.push_back(m1);
+    P.stages.push_back(m2);
+    if (!fused) P.stages.push_back(msc);
+    P.stages.push_back(mbc);
+    P.stages.push_back(r1);
+    if (fused) P.stages.push_back(marker(Stage::JOIN_WAIT));
+    P.stages.push_back(r2);
+    if (!fused) P.stages.push_back(cb);
+  }
+  return FHE_OK;
+}
+
+// ------------------------------------------------------------------ execution
+
+static cudaError_t launch_stage(fhe_ctx *c, const Stage &st, const SegList &sl, const BconvArgs &ba,
+                                cudaStream_t s) {
+  cudaStream_t q = st.aux ? c->aux : s;
+  switch (st.kind) {
+    case Stage::NTT: return launch_ntt_pass(c->tabs, st.column, st.fwd, st.pro, st.epi, sl, q);
+    case Stage::EW: return launch_ew(c->tabs, st.ewop, sl, q);
+    case Stage::IP: return launch_ip(c->tabs, sl, st.gather_own, st.gather_ext, q);
+    case Stage::BCONV:
+      return c->bconv_mode == FHE_BCONV_TC ? launch_bconv_tc(c->tabs, ba, st.max_in, st.max_out, q)
+                                           : launch_bconv(c->tabs, ba, st.max_in, st.max_out, q);
+    case Stage::FORK: {
+      cudaError_t e = cudaEventRecord(c->ev_fork, s);
+      return e != cudaSuccess ? e : cudaStreamWaitEvent(c->aux, c->ev_fork, 0);
+    }
+    case Stage::JOIN_RECORD: return cudaEventRecord(c->ev_join, c->aux);
+    case Stage::JOIN_WAIT: return cudaStreamWaitEvent(s, c->ev_join, 0);
+  }
+  return cudaErrorInvalidValue;
+}
+
+bool program_fits_inline(const Program &P) {
+  if ((int)P.ks.size() > kMaxInlineItems) return false;
+  for (const Stage &st : P.stages)
+    if ((int)st.segs.size() > kMaxSeg || (int)st.groups.size() > kMaxBconvGroups) return false;
+  return true;
+}
+
+int run_program_inline(fhe_ctx *c, const Program &P, cudaStream_t s) {
+  if (!program_fits_inline(P)) return fhe_fail(FHE_EINVAL, "internal: program does not fit inline launch arguments");
+  SegList sl;
+  BconvArgs ba;
+  for (const Stage &st : P.stages) {
+    memset(&sl, 0, sizeof sl);
+    memset(&ba, 0, sizeof ba);
+    for (const Seg &x : st.segs) {
+      sl.seg[sl.nseg++] = x;
+      sl.total += x.n;
+    }
+    for (size_t i = 0; i < P.ks.size(); i++) sl.ks[i] = P.ks[i];
+    for (const BconvGroup &g : st.groups) ba.g[ba.ngroups++] = g;
+    cudaError_t e = launch_stage(c, st, sl, ba, s);
+    if (e != cudaSuccess) return fhe_fail(FHE_ECUDA, "stage launch: %s", cudaGetErrorString(e));
+  }
+  return FHE_OK;
+}
+
+int upload_program(fhe_ctx *c, const Program &P, DevProgram &D) {
+  // one device buffer: per-item arguments, then per stage its segments, limb map and groups
+  size_t bytes = sizeof(KsArgs) * P.ks.size();
+  auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  bytes = align(bytes);
+  std::vector<size_t> seg_off(P.stages.size()), map_off(P.stages.size()), grp_off(P.stages.size());
+  for (size_t i = 0; i < P.stages.size(); i++) {
+    const Stage &st = P.stages[i];
+    int total = 0;
+    for (const Seg &x : st.segs) total += x.n;
+    seg_off[i] = bytes;
+    bytes = align(bytes + sizeof(Seg) * st.segs.size());
+    map_off[i] = bytes;
+    bytes = align(bytes + sizeof(int2) * total);
+    grp_off[i] = bytes;
+    bytes = align(bytes + sizeof(BconvGroup) * st.groups.size());
+  }
+  std::vector<char> host(bytes, 0);
+  memcpy(host.data(), P.ks.data(), sizeof(KsArgs) * P.ks.size());
+  for (size_t i = 0; i < P.stages.size(); i++) {
+    const Stage &st = P.stages[i];
+    memcpy(host.data() + seg_off[i], st.segs.data(), sizeof(Seg) * st.segs.size());
+    int2 *m = reinterpret_cast<int2 *>(host.data() + map_off[i]);
+    int v = 0;
+    for (size_t sidx = 0; sidx < st.segs.size(); sidx++)
+      for (int w = 0; w < st.segs[sidx].n; w++) m[v++] = make_int2((int)sidx, w);
+    memcpy(host.data() + grp_off[i], st.groups.data(), sizeof(BconvGroup) * st.groups.size());
+  }
+  if (cudaMalloc(&D.buf, bytes) != cudaSuccess) return fhe_fail(FHE_ENOMEM, "program upload: %zu bytes", bytes);
+  if (cudaMemcpy(D.buf, host.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+    return fhe_fail(FHE_ECUDA, "program upload copy");
+  char *base = static_cast<char *>(D.buf);
+  D.lists.assign(P.stages.size(), SegList{});
+  D.bargs.assign(P.stages.size(), BconvArgs{});
+  for (size_t i = 0; i < P.stages.size(); i++) {
+    const Stage &st = P.stages[i];
+    SegList &sl = D.lists[i];
+    memset(&sl, 0, sizeof sl);
+    sl.nseg = (int)st.segs.size();
+    for (const Seg &x : st.segs) sl.total += x.n;
+    sl.dev = reinterpret_cast<const Seg *>(base + seg_off[i]);
+    sl.vmap = reinterpret_cast<const int2 *>(base + map_off[i]);
+    sl.ksdev = reinterpret_cast<const KsArgs *>(base);
+    BconvArgs &ba = D.bargs[i];
+    memset(&ba, 0, sizeof ba);
+    ba.ngroups = (int)st.groups.size();
+    ba.dev = reinterpret_cast<const BconvGroup *>(base + grp_off[i]);
+  }
+  (void)c;
+  return FHE_OK;
+}
+
+int run_program_dev(fhe_ctx *c, const Program &P, const DevProgram &D, cudaStream_t s) {
+  for (size_t i = 0; i < P.stages.size(); i++) {
+    cudaError_t e = launch_stage(c, P.stages[i], D.lists[i], D.bargs[i], s);
+    if (e != cudaSuccess) return fhe_fail(FHE_ECUDA, "stage launch: %s", cudaGetErrorString(e));
+  }
+  return FHE_OK;
+}
+
+void free_program(DevProgram &D) {
+  if (D.buf) cudaFree(D.buf);
+  D.buf = nullptr;
+}

@@ -1,0 +1,54 @@
+// Stage programs: the key-switching pipeline of a list of items (key
+// switches, rotations, relinearisations, hoisted ModUp / ModDown halves),
+// emitted stage by stage so that one launch processes the same stage of every
+// item (Section IV-A multi-polynomial caching and batching: B sequences per
+// stage instead of one).
+#pragma once
+#include <vector>
+
+#include "ctx.h"
+
+enum ItemKind { IT_KS = 0, IT_ROTATE = 1, IT_RELIN = 2, IT_MODUP = 3, IT_MODDOWN = 4 };
+
+struct Item {
+  int kind = IT_KS;
+  int level = 0;
+  uint32_t galois = 1;             // rotation Galois element (1: none)
+  const uint32_t *in = nullptr;    // KS / MODUP: d [level][N]; ROTATE / MODDOWN: ct [2][level][N]; RELIN: a
+  const uint32_t *in2 = nullptr;   // RELIN: b
+  uint32_t *out = nullptr;         // [2][level][N] (not for MODUP)
+  const uint32_t *key = nullptr;   // switching key (not for MODUP)
+  int slot = 0;                    // workspace slot of this item
+  int ext_slot = 0;                // MODDOWN: slot whose EXT holds the shared ModUp output
+};
+
+struct Stage {
+  enum Kind { NTT, BCONV, IP, EW, FORK, JOIN_RECORD, JOIN_WAIT } kind = NTT;
+  bool column = false, fwd = false;
+  int pro = 0, epi = 0, ewop = 0;
+  bool aux = false;
+  bool gather_own = false, gather_ext = false;
+  int max_in = 0, max_out = 0;
+  std::vector<fhe::Seg> segs;
+  std::vector<fhe::BconvGroup> groups;
+};
+
+struct Program {
+  std::vector<fhe::KsArgs> ks;  // per item
+  std::vector<Stage> stages;
+};
+
+// Device copies of a program's launch descriptors (for captured plans).
+struct DevProgram {
+  void *buf = nullptr;
+  std::vector<fhe::SegList> lists;   // per stage (segment stages)
+  std::vector<fhe::BconvArgs> bargs; // per stage (BConv stages)
+};
+
+int ensure_slots(fhe_ctx *c, int n);
+int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Program &P);
+bool program_fits_inline(const Program &P);
+int run_program_inline(fhe_ctx *c, const Program &P, cudaStream_t s);
+int upload_program(fhe_ctx *c, const Program &P, DevProgram &D);
+int run_program_dev(fhe_ctx *c, const Program &P, const DevProgram &D, cudaStream_t s);
+void free_program(DevProgram &D);

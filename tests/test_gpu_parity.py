@@ -251,6 +251,44 @@ def test_batch_plan_equals_single_ops(c1):
     plan.close()
 
 
+@pytest.mark.parametrize("budget,max_group", [(0, 0), (1, 2), (0, 3)])
+def test_batch_plan_full_size_groups(c2, budget, max_group):
+    """Mixed rotations / relinearisations / key switches at uneven levels,
+    N = 2^16, split into groups of various sizes: every item bit-exact."""
+    from paper_2512_18345_gb300 import binding
+    P, OP, ctx = c2
+    ctx.set_batch(budget, max_group)
+    g = inputs.rng(95 + max_group)
+    rk = rand_key(P, g)
+    ctx.set_relin_key(dev(rk))
+    specs = [("rotate", 24, 777), ("relin", 17, 0), ("rotate", 5, 12345), ("ks", 9, 0), ("rotate", 24, 3),
+             ("relin", 1, 0)]
+    items, want = [], []
+    for op, lv, rot in specs:
+        a = np.stack([inputs.uniform_residues(g, P.q[:lv], P.N) for _ in range(2)])
+        out = binding.empty((2, lv, P.N))
+        if op == "rotate":
+            k = rand_key(P, g)
+            ctx.set_rot_key(rot, dev(k))
+            items.append(dict(op=binding.FHE_OP_ROTATE, level=lv, rot=rot, **{"in": dev(a)}, out=out))
+            want.append(oracle.rotate(OP, a, lv, rot, k))
+        elif op == "relin":
+            b = np.stack([inputs.uniform_residues(g, P.q[:lv], P.N) for _ in range(2)])
+            items.append(dict(op=binding.FHE_OP_RELIN, level=lv, **{"in": dev(a)}, in2=dev(b), out=out))
+            want.append(oracle.hmult(OP, a, b, lv, rk))
+        else:
+            items.append(dict(op=binding.FHE_OP_KS, level=lv, rot=binding.FHE_RELIN_KEY, **{"in": dev(a[0])}, out=out))
+            want.append(oracle.keyswitch(OP, a[0], lv, rk))
+    plan = ctx.batch_plan(items, binding.FHE_PLAN_GRAPH)
+    if max_group:
+        assert max(plan.groups) <= max_group
+    plan.launch()
+    for i, (it, w) in enumerate(zip(items, want)):
+        assert np.array_equal(host(it["out"]), w), f"item {i} {specs[i]}"
+    plan.close()
+    ctx.set_batch(0, 0)
+
+
 # ------------------------------------------------------------------ CKKS semantics through the GPU path
 
 def test_gpu_rotate_decodes(c1):
