@@ -236,6 +236,35 @@ typedef struct {
 FHE_API int fhe_trace_enable(fhe_ctx *ctx, int on);
 FHE_API int fhe_trace_read(fhe_ctx *ctx, fhe_kernel_stat *out, int max, int *n);
 
+/*
+ * Allocation-free base conversion.  The paper has no counterpart: this is an
+ * interface addition for callers that cannot allocate device memory -- code
+ * recording a CUDA stream capture (cudaMalloc and stream synchronization are
+ * not allowed while a capture is open), latency-critical loops that must avoid
+ * cudaMalloc's implicit device synchronization, and processes whose framework
+ * has already reserved all device memory for its own pool.
+ *
+ * Computes exactly what fhe_bconv computes (same bits) but allocates nothing:
+ * its scratch -- the pre-multiplied input, at most
+ * FHE_BCONV_NOALLOC_MAX_IN x FHE_BCONV_NOALLOC_MAX_N words, and the conversion
+ * tables -- is one fixed device array of about 2 MB that every GPU loading
+ * this library holds until the process exits.  Larger n_in, n_out or N are
+ * rejected with FHE_EINVAL (use fhe_bconv).  The context must already exist.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents; every word
+ * a call reads it writes first, so nothing has to be cleared.  Calls on one
+ * context are ordered by the library, but calls whose GPU work overlaps --
+ * unordered streams of different contexts on the same device -- race on the
+ * shared array.
+ */
+#define FHE_BCONV_NOALLOC_MAX_IN 8
+#define FHE_BCONV_NOALLOC_MAX_OUT 64
+#define FHE_BCONV_NOALLOC_MAX_N 65536
+FHE_API int fhe_bconv_noalloc(fhe_ctx *ctx, const uint32_t *in, const int *in_idx, int n_in, uint32_t *out,
+                              const int *out_idx, int n_out, fhe_stream stream);
+
 FHE_API const char *fhe_last_error(void);
 
 #ifdef __cplusplus

@@ -31,7 +31,7 @@ EXPORTS = (
     "fhe_rotate_hoisted", "fhe_pmult", "fhe_add", "fhe_ntt", "fhe_intt", "fhe_modup", "fhe_moddown",
     "fhe_bconv", "fhe_batch_plan", "fhe_batch_launch", "fhe_plan_destroy", "fhe_plan_kernel_count",
     "fhe_plan_groups", "fhe_ctx_set_batch",
-    "fhe_trace_enable", "fhe_trace_read", "fhe_last_error",
+    "fhe_trace_enable", "fhe_trace_read", "fhe_bconv_noalloc", "fhe_last_error",
 )
 
 
@@ -108,6 +108,7 @@ def lib() -> ctypes.CDLL:
         "fhe_ctx_set_batch": [vp, ctypes.c_size_t, ctypes.c_int],
         "fhe_trace_enable": [vp, ctypes.c_int],
         "fhe_trace_read": [vp, ctypes.POINTER(KernelStat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+        "fhe_bconv_noalloc": [vp, vp, ip, ctypes.c_int, vp, ip, ctypes.c_int, vp],
         "fhe_last_error": [],
     }
     for name, args in sig.items():
@@ -321,6 +322,12 @@ class Context:
         out = self._out(out, (len(out_idx), self.N))
         check(lib().fhe_bconv(self.h, _ptr(x), _idx(in_idx), len(in_idx), _ptr(out), _idx(out_idx), len(out_idx),
                               _stream(stream)))
+        return out
+
+    def bconv_noalloc(self, x, in_idx: Sequence[int], out_idx: Sequence[int], out, stream=None):
+        """fhe_bconv without any device allocation (fixed shared scratch; out must be given)."""
+        check(lib().fhe_bconv_noalloc(self.h, _ptr(x), _idx(in_idx), len(in_idx), _ptr(out), _idx(out_idx),
+                                      len(out_idx), _stream(stream)))
         return out
 
     def batch_plan(self, items: Iterable[dict], flags: int = FHE_PLAN_GRAPH) -> Plan:
