@@ -29,7 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "hrotate_N65536_L24_plain"
-METRIC = "key-switches/s at N=2^16,L=24 (HRotate, batched+graph)"
+METRIC = "key-switches/s at N=2^16,L=24 (HRotate, batched+TC-BConv)"
 UNIT = "key-switches/s"
 
 
@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the 64-item batch and linear-transform lines")
     return ap.parse_args()
 
 
@@ -166,6 +167,78 @@ def cpu_baseline(P, ct_np, key_np, rot, budget_s=12.0):
             "sample": f"{done} HRotates at N=2^16, L=24 (one workload item each), {dt:.1f} s"}
 
 
+def rand_key_np(inputs, P, g):
+    import numpy as np
+    return np.stack([np.stack([inputs.uniform_residues(g, P.primes, P.N) for _ in range(2)]) for _ in range(P.dnum)])
+
+
+def bench_batch64(binding, inputs, roofline, dev, timed, steps, bconv_mode):
+    """Fourth workload: 64 ciphertexts, levels uniform in 4..24, relin / rotate mix, one graph."""
+    import numpy as np
+    name = "batch64_N65536_L4to24"
+    w = inputs.WORKLOADS[name]
+    P = inputs.workload_params(name)
+    g = inputs.rng(w["seed"])
+    spec = inputs.batch_items(g, w["items"], w["level_lo"], w["level_hi"])
+    ctx = binding.Context.from_params(P, device=dev)
+    ctx.set_bconv(bconv_mode)
+    ctx.set_relin_key(binding.to_device(rand_key_np(inputs, P, g), dev))
+    seen, items, nbytes = set(), [], 0
+    for it in spec:
+        lv = it["level"]
+        a = binding.to_device(np.stack([inputs.uniform_residues(g, P.q[:lv], P.N) for _ in range(2)]), dev)
+        out = binding.empty((2, lv, P.N), dev)
+        if it["op"] == "rotate":
+            if it["rot"] not in seen:
+                seen.add(it["rot"])
+                ctx.set_rot_key(it["rot"], binding.to_device(rand_key_np(inputs, P, g), dev))
+            items.append(dict(op=binding.FHE_OP_ROTATE, level=lv, rot=it["rot"], **{"in": a}, out=out))
+        else:
+            b = binding.to_device(np.stack([inputs.uniform_residues(g, P.q[:lv], P.N) for _ in range(2)]), dev)
+            items.append(dict(op=binding.FHE_OP_RELIN, level=lv, **{"in": a}, in2=b, out=out))
+        nbytes += roofline.ks_bytes(P.N, lv, P.K, P.alpha)
+    plan = ctx.batch_plan(items, binding.FHE_PLAN_GRAPH)
+    for _ in range(3):
+        plan.launch()
+    k = max(3, min(steps, 30))
+    ms = timed(plan.launch, k)
+    ctx.sync()
+    res = {"value": 64 * k / (ms / 1e3), "unit": "key-switches/s", "ms_per_batch": ms / k, "items": 64,
+           "groups": plan.groups, "graph_kernels": plan.kernel_count, "bytes_per_batch_model": nbytes,
+           "distinct_rotation_keys": len(seen)}
+    plan.close()
+    ctx.close()
+    return res
+
+
+def bench_lt(binding, inputs, dev, timed, bconv_mode):
+    """Fifth workload: BSGS linear transform at N = 2^16, level 24, 16 baby x 8 giant steps."""
+    import numpy as np
+    name = "bsgs_lt_N65536_L24"
+    w = inputs.WORKLOADS[name]
+    P = inputs.workload_params(name)
+    g = inputs.rng(w["seed"])
+    baby, giant, level = w["baby"], w["giant"], P.L
+    ctx = binding.Context.from_params(P, device=dev)
+    ctx.set_bconv(bconv_mode)
+    for r in list(range(1, baby)) + [baby * gg for gg in range(1, giant)]:
+        ctx.set_rot_key(r, binding.to_device(rand_key_np(inputs, P, g), dev))
+    ct = binding.to_device(np.stack([inputs.uniform_residues(g, P.q, P.N) for _ in range(2)]), dev)
+    diags = binding.empty((baby * giant, level, P.N), dev)
+    for d in range(baby * giant):
+        diags[d].copy_(binding.to_device(inputs.uniform_residues(g, P.q, P.N), dev))
+    out = binding.empty((2, level, P.N), dev)
+    for _ in range(2):
+        ctx.linear_transform(ct, level, diags, baby, giant, out=out)
+    k = 5
+    ms = timed(lambda: ctx.linear_transform(ct, level, diags, baby, giant, out=out), k)
+    ctx.sync()
+    diag_bytes = baby * giant * level * P.N * 4
+    ctx.close()
+    return {"ms": ms / k, "key_switches": (baby - 1) + (giant - 1), "nominal_steps": [baby, giant],
+            "diagonals": baby * giant, "diagonal_bytes": diag_bytes}
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
@@ -228,17 +301,27 @@ def main():
             ms = float(t.item())
         return ms
 
-    # --- headline: fused pipeline, batch captured in one CUDA graph
+    # --- batched fused pipeline in one CUDA graph, CUDA-core base conversion (comparison)
     ctx.set_fused(True)
+    ctx.set_bconv(binding.FHE_BCONV_SCALAR)
+    plan_sc = ctx.batch_plan(items, binding.FHE_PLAN_GRAPH)
+    for _ in range(max(3, args.warmup)):
+        plan_sc.launch()
+    ms_sc = timed(plan_sc.launch, max(3, min(args.steps, 100)))
+    graph_scalar_ks = B * max(3, min(args.steps, 100)) * ws / (ms_sc / 1e3)
+    plan_sc.close()
+    # --- headline: batched fused pipeline, tensor-core base conversion, one CUDA graph
+    ctx.set_bconv(binding.FHE_BCONV_TC)
     plan = ctx.batch_plan(items, binding.FHE_PLAN_GRAPH)
     for _ in range(max(3, args.warmup)):
         plan.launch()
-    torch.cuda.synchronize()
+    ctx.sync()
     clocks = ClockSampler(dev)
     clocks.start()
     time.sleep(0.15)
     ms = timed(plan.launch, args.steps)
     clk = clocks.stop()
+    ctx.sync()
     ks_total = B * args.steps * ws
     value = ks_total / (ms / 1e3)
     graph_kernels = plan.kernel_count
@@ -250,6 +333,7 @@ def main():
         for it in items:
             ctx.rotate(it["in"], level, it["rot"], out=it["out"])
 
+    ctx.set_bconv(binding.FHE_BCONV_SCALAR)
     for _ in range(3):
         direct()
     ms_fused = timed(direct, cmp_steps)
@@ -258,6 +342,7 @@ def main():
         direct()
     ms_plain = timed(direct, cmp_steps)
     ctx.set_fused(True)
+    ctx.set_bconv(binding.FHE_BCONV_TC)
     plain_ks = B * cmp_steps * ws / (ms_plain / 1e3)
     fused_ks = B * cmp_steps * ws / (ms_fused / 1e3)
 
@@ -345,6 +430,15 @@ def main():
     e2e_val = B * e2e_steps * ws / (ms_e2e / 1e3)
     bytes_io = B * 2 * level * P.N * 4
 
+    # --- the fourth and fifth workloads (reported beside the headline)
+    extra = {}
+    if not args.no_extra:
+        extra["batch64_mixed_levels"] = bench_batch64(binding, inputs, roofline, dev, timed, args.steps,
+                                                      binding.FHE_BCONV_TC)
+        lt = bench_lt(binding, inputs, dev, timed, binding.FHE_BCONV_TC)
+        lt["hbm_floor_ms"] = lt["diagonal_bytes"] / (hbm_peak * 1e9) * 1e3
+        extra["bsgs_linear_transform_L24"] = lt
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         try:
@@ -361,7 +455,7 @@ def main():
                        "K": P.K, "dnum": P.dnum, "batch_per_gpu": B,
                        "l2": f"inputs larger than L2: {B} distinct ciphertext+key pairs, "
                              f"{B * (2 * level + 2 * P.dnum * (P.L + P.K)) * P.N * 4 / 1e6:.0f} MB per step",
-                       "path": "fused pipeline, batch captured in one CUDA graph"},
+                       "path": "fused pipeline, tensor-core BConv, batch captured in one CUDA graph"},
             "gpu_launches": graph_kernels * args.steps,
             "clocks": clk,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io},
@@ -369,9 +463,11 @@ def main():
             "cpu_baseline": cpu,
             "l2_roofline": {"bytes_per_ks": bks, "l2_gbs_measured": l2_gbs, "frac": l2_frac,
                             "definition": "B_KS(l) / measured L2 read+write bandwidth / time per key switch"},
-            "paths": {"graph_fused_batched": value, "direct_fused_batched": batched_direct_ks,
-                      "direct_fused_single": fused_ks, "plain_per_kernel_single": plain_ks},
+            "paths": {"graph_batched_tc_bconv": value, "graph_batched_scalar_bconv": graph_scalar_ks,
+                      "direct_batched_tc_bconv": batched_direct_ks, "direct_fused_single_scalar": fused_ks,
+                      "plain_per_kernel_single_scalar": plain_ks},
             "batch_groups": groups,
+            "other_workloads": extra,
             "kernels": {k: {"launches": v[0], "ms": v[1], "share": v[1] / total_ms} for k, v in
                         sorted(stats.items(), key=lambda kv: -kv[1][1])},
         }

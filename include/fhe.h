@@ -106,6 +106,12 @@ FHE_API int fhe_ctx_destroy(fhe_ctx *ctx);
 FHE_API int fhe_ctx_info(const fhe_ctx *ctx, fhe_info *out);
 /* Select the BConv implementation for later calls (FHE_BCONV_SCALAR / FHE_BCONV_TC). */
 FHE_API int fhe_ctx_set_bconv(fhe_ctx *ctx, int mode);
+/*
+ * Synchronize the context's device and report device-side failures: returns
+ * FHE_ETIMEOUT (and clears the condition) when a kernel's bounded wait on the
+ * tensor cores expired since the last call; its outputs are then invalid.
+ */
+FHE_API int fhe_ctx_sync(fhe_ctx *ctx);
 /* Fuse stage epilogues (1, default) or run the plain per-kernel pipeline (0).  Same bits. */
 FHE_API int fhe_ctx_set_fused(fhe_ctx *ctx, int fused);
 
@@ -158,6 +164,19 @@ FHE_API int fhe_rescale(fhe_ctx *ctx, const uint32_t *ct, int level, uint32_t *o
  */
 FHE_API int fhe_rotate_hoisted(fhe_ctx *ctx, const uint32_t *ct, int level, const int32_t *rots, int n,
                        uint32_t *const *outs, fhe_stream stream);
+
+/*
+ * Baby-step / giant-step plaintext matrix-vector product, the linear-transform
+ * shape of bootstrapping (hoisted rotations, Section V-C):
+ *   out = sum_{g < giant} rot_{baby g}( sum_{b < baby} diags[g baby + b] (.) rot_b(ct) )
+ * ct [2][level][N]; diags [giant * baby][level][N] NTT-form plaintexts (device);
+ * out [2][level][N] (must not overlap ct).  The baby rotations share one ModUp
+ * (as fhe_rotate_hoisted); the giant rotations are ordinary rotations.  Needs the
+ * rotation keys of 1..baby-1 and baby g (g = 1..giant-1).  baby <= 32, giant <= 16.
+ * No rescale.  The context grows a scratch buffer of (baby + 2 giant) ciphertexts.
+ */
+FHE_API int fhe_linear_transform(fhe_ctx *ctx, const uint32_t *ct, int level, const uint32_t *diags, int baby,
+                                 int giant, uint32_t *out, fhe_stream stream);
 
 /* Plaintext multiply: out_c = ct_c * pt ([level][N] NTT form), c = 0, 1. out may equal ct. */
 FHE_API int fhe_pmult(fhe_ctx *ctx, const uint32_t *ct, const uint32_t *pt, int level, uint32_t *out, fhe_stream stream);

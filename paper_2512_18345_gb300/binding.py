@@ -26,9 +26,9 @@ FHE_PLAN_GRAPH = 1
 
 # every entry point declared in include/fhe.h
 EXPORTS = (
-    "fhe_ctx_create", "fhe_ctx_destroy", "fhe_ctx_info", "fhe_ctx_set_bconv", "fhe_ctx_set_fused",
+    "fhe_ctx_create", "fhe_ctx_destroy", "fhe_ctx_info", "fhe_ctx_set_bconv", "fhe_ctx_set_fused", "fhe_ctx_sync",
     "fhe_set_relin_key", "fhe_set_rot_key", "fhe_keyswitch", "fhe_rotate", "fhe_hmult", "fhe_rescale",
-    "fhe_rotate_hoisted", "fhe_pmult", "fhe_add", "fhe_ntt", "fhe_intt", "fhe_modup", "fhe_moddown",
+    "fhe_rotate_hoisted", "fhe_linear_transform", "fhe_pmult", "fhe_add", "fhe_ntt", "fhe_intt", "fhe_modup", "fhe_moddown",
     "fhe_bconv", "fhe_batch_plan", "fhe_batch_launch", "fhe_plan_destroy", "fhe_plan_kernel_count",
     "fhe_plan_groups", "fhe_ctx_set_batch",
     "fhe_trace_enable", "fhe_trace_read", "fhe_bconv_noalloc", "fhe_last_error",
@@ -85,6 +85,7 @@ def lib() -> ctypes.CDLL:
         "fhe_ctx_info": [vp, ctypes.POINTER(FheInfo)],
         "fhe_ctx_set_bconv": [vp, ctypes.c_int],
         "fhe_ctx_set_fused": [vp, ctypes.c_int],
+        "fhe_ctx_sync": [vp],
         "fhe_set_relin_key": [vp, vp, vp],
         "fhe_set_rot_key": [vp, ctypes.c_int32, vp, vp],
         "fhe_keyswitch": [vp, vp, ctypes.c_int, ctypes.c_int32, vp, vp],
@@ -93,6 +94,7 @@ def lib() -> ctypes.CDLL:
         "fhe_rescale": [vp, vp, ctypes.c_int, vp, vp],
         "fhe_rotate_hoisted": [vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_int,
                                ctypes.POINTER(vp), vp],
+        "fhe_linear_transform": [vp, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp, vp],
         "fhe_pmult": [vp, vp, vp, ctypes.c_int, vp, vp],
         "fhe_add": [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp, vp],
         "fhe_ntt": [vp, vp, ip, ctypes.c_int, vp],
@@ -230,6 +232,10 @@ class Context:
         d["psi"] = list(i.psi)[: i.L + i.K]
         return d
 
+    def sync(self) -> None:
+        """Synchronize the device; raises FheError(FHE_ETIMEOUT) if a device-side wait expired."""
+        check(lib().fhe_ctx_sync(self.h))
+
     def set_bconv(self, mode: int) -> None:
         check(lib().fhe_ctx_set_bconv(self.h, mode))
 
@@ -285,6 +291,11 @@ class Context:
         o = (vp * n)(*[o.data_ptr() for o in outs])
         check(lib().fhe_rotate_hoisted(self.h, _ptr(ct), level, r, n, o, _stream(stream)))
         return outs
+
+    def linear_transform(self, ct, level: int, diags, baby: int, giant: int, out=None, stream=None):
+        out = self._out(out, (2, level, self.N))
+        check(lib().fhe_linear_transform(self.h, _ptr(ct), level, _ptr(diags), baby, giant, _ptr(out), _stream(stream)))
+        return out
 
     def pmult(self, ct, pt, level: int, out=None, stream=None):
         out = self._out(out, (2, level, self.N))

@@ -25,6 +25,8 @@ struct BconvGroup {
   const uint32_t *T;    // [n_out][n_in] device table
   const int2 *omap;     // [n_out] (limb offset from out, prime index)
   int n_in, n_out;
+  const uint16_t *Btc;  // tensor-core path: byte-digit table, canonical layout, npad x kpad bf16
+  int kpad, npad;       // round16(4 n_in), round16(4 n_out)
 };
 
 constexpr int kMaxBconvGroups = 8;

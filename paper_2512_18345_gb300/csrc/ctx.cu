@@ -158,6 +158,7 @@ static int build_tables(fhe_ctx *c) {
   std::vector<uint2> mu_scale((size_t)L * L), mu_qhinv((size_t)L * L);
   c->modup_T.assign((size_t)L * c->dnum, nullptr);
   c->modup_map.assign((size_t)L * c->dnum, nullptr);
+  c->modup_Btc.assign((size_t)L * c->dnum, nullptr);
   for (int level = 1; level <= L; level++) {
     const int beta = c->beta(level);
     for (int j = 0; j < beta; j++) {
@@ -188,6 +189,9 @@ static int build_tables(fhe_ctx *c) {
       (void)a;
       CUDA_OR_FAIL(upload(&c->modup_T[(size_t)(level - 1) * c->dnum + j], T));
       CUDA_OR_FAIL(upload(&c->modup_map[(size_t)(level - 1) * c->dnum + j], om));
+      std::vector<uint32_t> pout;
+      for (const int2 &m : om) pout.push_back(pr[m.y]);
+      CUDA_OR_FAIL(upload(&c->modup_Btc[(size_t)(level - 1) * c->dnum + j], fhe::bconv_tc_table(T, hi - lo, pout)));
     }
   }
   CUDA_OR_FAIL(upload(&c->d_mu_scale, mu_scale));
@@ -225,6 +229,9 @@ static int build_tables(fhe_ctx *c) {
   CUDA_OR_FAIL(upload(&c->d_pinv, pinv));
   CUDA_OR_FAIL(upload(&c->d_mdT, mdT));
   CUDA_OR_FAIL(upload(&c->d_mdmap, mdmap));
+  CUDA_OR_FAIL(upload(&c->d_md_Btc, fhe::bconv_tc_table(mdT, K, std::vector<uint32_t>(pr.begin(), pr.begin() + L))));
+  CUDA_OR_FAIL(upload(&c->d_status, std::vector<unsigned int>(1, 0u)));
+  c->tabs.status = c->d_status;
 
   // rescale: q_{l-1}^-1 mod q_i for every level l and i < l-1
   std::vector<uint2> rs((size_t)L * L, make_uint2(0, 0));
@@ -241,6 +248,7 @@ static int build_tables(fhe_ctx *c) {
   c->tabs.pc = c->d_pc;
   c->tabs.logn = c->logn;
   c->tabs.tracer = nullptr;
+  c->tabs.status = c->d_status;
   return FHE_OK;
 }
 
@@ -284,6 +292,9 @@ fhe_ctx::~fhe_ctx() {
   cudaFree(d_mu_qhinv);
   for (auto p : modup_T) cudaFree(p);
   for (auto p : modup_map) cudaFree(p);
+  for (auto p : modup_Btc) cudaFree(p);
+  cudaFree(d_md_Btc);
+  cudaFree(d_status);
   cudaFree(d_md_scale);
   cudaFree(d_md_phinv);
   cudaFree(d_pinv);
@@ -291,6 +302,7 @@ fhe_ctx::~fhe_ctx() {
   cudaFree(d_mdmap);
   cudaFree(d_rs_qinv);
   for (auto &s : slots) cudaFree(s.base);
+  cudaFree(lt_scratch);
   cudaFree(relin_key);
   for (auto &kv : rot_keys) cudaFree(kv.second);
   for (auto p : scratch_tabs) cudaFree(p);
@@ -427,6 +439,20 @@ extern "C" int fhe_trace_read(fhe_ctx *c, fhe_kernel_stat *out, int max, int *n)
   c->tracer.reset();
   *n = (int)agg.size();
   for (int i = 0; i < max && i < (int)agg.size(); i++) out[i] = agg[i];
+  return FHE_OK;
+}
+
+extern "C" int fhe_ctx_sync(fhe_ctx *c) {
+  if (!c) return fhe_fail(FHE_EINVAL, "fhe_ctx_sync: null");
+  cudaSetDevice(c->device);
+  CUDA_OR_FAIL(cudaDeviceSynchronize());
+  unsigned int st = 0;
+  CUDA_OR_FAIL(cudaMemcpy(&st, c->d_status, sizeof st, cudaMemcpyDeviceToHost));
+  if (st) {
+    const unsigned int zero = 0;
+    CUDA_OR_FAIL(cudaMemcpy(c->d_status, &zero, sizeof zero, cudaMemcpyHostToDevice));
+    return fhe_fail(FHE_ETIMEOUT, "fhe_ctx_sync: a bounded device-side wait expired (status 0x%x)", st);
+  }
   return FHE_OK;
 }
 

@@ -26,10 +26,13 @@ struct fhe_ctx {
   uint2 *d_mu_qhinv = nullptr;  // [L][L]: (D/q_t)^-1 mod q_t
   std::vector<uint32_t *> modup_T;  // [(level-1)*dnum + j]: BConv table, rows in ext-limb order
   std::vector<int2 *> modup_map;    // same index: (ext limb, prime) per row
+  std::vector<uint16_t *> modup_Btc; // same index: byte-digit table of the tensor-core conversion
   uint2 *d_md_scale = nullptr, *d_md_phinv = nullptr;  // [K]
   uint2 *d_pinv = nullptr;                             // [L] P^-1 mod q_i
   uint32_t *d_mdT = nullptr;                           // [L][K] (P/p_k) mod q_i
   int2 *d_mdmap = nullptr;                             // [L] (i, i)
+  uint16_t *d_md_Btc = nullptr;                        // tensor-core table of the ModDown conversion
+  unsigned int *d_status = nullptr;                    // device status word (expired waits)
   uint2 *d_rs_qinv = nullptr;                          // [L][L]
   std::vector<void *> scratch_tabs;                    // tables built for fhe_bconv calls
   size_t table_bytes = 0;
@@ -54,6 +57,8 @@ struct fhe_ctx {
   };
   std::vector<Slot> slots;
   size_t slot_bytes = 0;
+  uint32_t *lt_scratch = nullptr;  // linear transform: baby / giant rotations and inner sums
+  size_t lt_words = 0;
   size_t ws_bytes = 0;
 
   // cross-stream ordering of calls on this context

@@ -32,8 +32,24 @@ struct DevTables {
   NttTables ntt;
   const PrimeC *pc;
   int logn;
-  Tracer *tracer;  // null: no tracing
+  Tracer *tracer;          // null: no tracing
+  unsigned int *status;    // device word: bit 0 set when a bounded device-side wait expired
 };
+
+// bracket one launch with trace events when tracing is on
+struct TraceScope {
+  Tracer *t;
+  cudaStream_t s;
+  TraceScope(const DevTables &tb, const char *name, cudaStream_t st) : t(tb.tracer), s(st) {
+    if (t) t->begin(name, s);
+  }
+  ~TraceScope() {
+    if (t) t->end(s);
+  }
+};
+void note_launch();
+// the byte-digit table of the tensor-core base conversion (host side)
+std::vector<uint16_t> bconv_tc_table(const std::vector<uint32_t> &T, int n_in, const std::vector<uint32_t> &p_out);
 
 // One NTT pass over every limb of `sl` (column or block pass, forward or inverse).
 cudaError_t launch_ntt_pass(const DevTables &t, bool column, bool fwd, int pro, int epi, const SegList &sl,

@@ -77,6 +77,39 @@ static int run_items(fhe_ctx *c, const std::vector<Item> &items, cudaStream_t s)
   return run_program_inline(c, P, s);
 }
 
+// Run items in consecutive chunks, each as large as by-value launch arguments allow.
+// Items other than IT_MODUP get workspace slots first_slot, first_slot + 1, ... within
+// their chunk; an IT_MODUP item keeps its own slot.
+int run_items_chunked(fhe_ctx *c, const std::vector<Item> &items, int first_slot, cudaStream_t s) {
+  size_t i = 0;
+  while (i < items.size()) {
+    std::vector<Item> chunk;
+    Program best;
+    int nslot = 0;
+    size_t j = i;
+    while (j < items.size()) {
+      Item it = items[j];
+      if (it.kind != IT_MODUP) it.slot = first_slot + nslot;
+      chunk.push_back(it);
+      Program Q;
+      const int rc = build_program(c, chunk, c->fused != 0, Q);
+      if (rc != FHE_OK) return rc;
+      if (!program_fits_inline(Q)) {
+        chunk.pop_back();
+        break;
+      }
+      best = std::move(Q);
+      if (it.kind != IT_MODUP) nslot++;
+      j++;
+    }
+    if (chunk.empty()) return fhe_fail(FHE_EINVAL, "internal: one item does not fit the launch arguments");
+    const int rc = run_program_inline(c, best, s);
+    if (rc != FHE_OK) return rc;
+    i = j;
+  }
+  return FHE_OK;
+}
+
 static int check_level(const fhe_ctx *c, int level, const char *fn) {
   if (level < 1 || level > c->L) return fhe_fail(FHE_ELEVEL, "%s: level %d outside [1, %d]", fn, level, c->L);
   return FHE_OK;
@@ -243,17 +276,8 @@ extern "C" int fhe_rotate_hoisted(fhe_ctx *c, const uint32_t *ct, int level, con
   up.level = level;
   up.in = ct + poly;
   up.slot = 0;
-  const int per = kMaxInlineItems - 1;
-  for (size_t b = 0; b < todo.size(); b += per) {
-    std::vector<Item> batch;
-    if (b == 0) batch.push_back(up);
-    for (size_t r = b; r < std::min(todo.size(), b + per); r++) {
-      Item it = todo[r];
-      it.slot = 1 + (int)(r - b);
-      batch.push_back(it);
-    }
-    CHECK(run_items(c, batch, s));
-  }
+  todo.insert(todo.begin(), up);
+  CHECK(run_items_chunked(c, todo, 1, s));
   return FHE_OK;
 }
 
@@ -382,6 +406,9 @@ extern "C" int fhe_moddown(fhe_ctx *c, const uint32_t *u, int level, uint32_t *o
   g.omap = c->d_mdmap;
   g.n_in = K;
   g.n_out = level;
+  g.Btc = c->d_md_Btc;
+  g.kpad = (4 * K + 15) / 16 * 16;
+  g.npad = (4 * level + 15) / 16 * 16;
   if (c->bconv_mode == FHE_BCONV_TC)
     LAUNCH_OR_FAIL(launch_bconv_tc(c->tabs, ba, K, level, s));
   else
@@ -439,17 +466,24 @@ extern "C" int fhe_bconv(fhe_ctx *c, const uint32_t *in, const int *in_idx, int 
   uint32_t *dT = nullptr, *y = nullptr;
   int2 *dM = nullptr;
   uint2 *dPre = nullptr;
+  uint16_t *dB = nullptr;
+  std::vector<uint32_t> pout;
+  for (int o = 0; o < n_out; o++) pout.push_back(pr[out_idx[o]]);
+  const std::vector<uint16_t> Btc = bconv_tc_table(T, n_in, pout);
   auto cleanup = [&]() {
     cudaFree(dT);
     cudaFree(dM);
     cudaFree(dPre);
     cudaFree(y);
+    cudaFree(dB);
   };
   if (cudaMalloc(&dT, 4 * T.size()) != cudaSuccess || cudaMalloc(&dM, 8 * om.size()) != cudaSuccess ||
-      cudaMalloc(&dPre, 8 * pre.size()) != cudaSuccess || cudaMalloc(&y, 4 * N * n_in) != cudaSuccess) {
+      cudaMalloc(&dPre, 8 * pre.size()) != cudaSuccess || cudaMalloc(&y, 4 * N * n_in) != cudaSuccess ||
+      cudaMalloc(&dB, 2 * Btc.size()) != cudaSuccess) {
     cleanup();
     return fhe_fail(FHE_ENOMEM, "fhe_bconv: temporary tables");
   }
+  cudaMemcpy(dB, Btc.data(), 2 * Btc.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(dT, T.data(), 4 * T.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(dM, om.data(), 8 * om.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(dPre, pre.data(), 8 * pre.size(), cudaMemcpyHostToDevice);
@@ -474,6 +508,9 @@ extern "C" int fhe_bconv(fhe_ctx *c, const uint32_t *in, const int *in_idx, int 
   g.omap = dM;
   g.n_in = n_in;
   g.n_out = n_out;
+  g.Btc = dB;
+  g.kpad = (4 * n_in + 15) / 16 * 16;
+  g.npad = (4 * n_out + 15) / 16 * 16;
   if (rc == FHE_OK) {
     cudaError_t e = c->bconv_mode == FHE_BCONV_TC ? launch_bconv_tc(c->tabs, ba, n_in, n_out, s)
                                                   : launch_bconv(c->tabs, ba, n_in, n_out, s);

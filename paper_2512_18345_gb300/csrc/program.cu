@@ -153,12 +153,17 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
     for (int j = 0; j < beta; j++) {
       const int lo = j * A, hi = std::min((j + 1) * A, level);
       BconvGroup g;
+      memset(&g, 0, sizeof g);
+    memset(&g, 0, sizeof g);
       g.in = S.Y + (size_t)lo * N;
       g.out = S.EXT + (size_t)j * n_ext * N;
       g.T = c->modup_T[(size_t)(level - 1) * c->dnum + j];
       g.omap = c->modup_map[(size_t)(level - 1) * c->dnum + j];
       g.n_in = hi - lo;
       g.n_out = n_ext - (hi - lo);
+      g.Btc = c->modup_Btc[(size_t)(level - 1) * c->dnum + j];
+      g.kpad = (4 * g.n_in + 15) / 16 * 16;
+      g.npad = (4 * g.n_out + 15) / 16 * 16;
       bc.groups.push_back(g);
       bc.max_in = std::max(bc.max_in, g.n_in);
       bc.max_out = std::max(bc.max_out, g.n_out);
@@ -219,12 +224,17 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
       y.scale = c->d_md_phinv;
       add(msc, y);
       BconvGroup g;
+      memset(&g, 0, sizeof g);
+    memset(&g, 0, sizeof g);
       g.in = uc;
       g.out = r;
       g.T = c->d_mdT;
       g.omap = c->d_mdmap;
       g.n_in = K;
       g.n_out = level;
+      g.Btc = c->d_md_Btc;
+      g.kpad = (4 * K + 15) / 16 * 16;
+      g.npad = (4 * level + 15) / 16 * 16;
       mbc.groups.push_back(g);
       mbc.max_in = std::max(mbc.max_in, K);
       mbc.max_out = std::max(mbc.max_out, level);

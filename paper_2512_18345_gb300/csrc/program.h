@@ -52,3 +52,4 @@ int run_program_inline(fhe_ctx *c, const Program &P, cudaStream_t s);
 int upload_program(fhe_ctx *c, const Program &P, DevProgram &D);
 int run_program_dev(fhe_ctx *c, const Program &P, const DevProgram &D, cudaStream_t s);
 void free_program(DevProgram &D);
+int run_items_chunked(fhe_ctx *c, const std::vector<Item> &items, int first_slot, cudaStream_t s);
