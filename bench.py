@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the 64-item batch and linear-transform lines")
+    ap.add_argument("--profile-run", choices=["scalar", "tc"], default=None,
+                    help="only launch the batched stage programs (one lane, no graph) warmup + steps times, "
+                         "in a fixed launch order for profilers; prints no JSON line")
     return ap.parse_args()
 
 
@@ -239,6 +242,59 @@ def bench_lt(binding, inputs, dev, timed, bconv_mode):
             "diagonals": baby * giant, "diagonal_bytes": diag_bytes}
 
 
+def kernel_model(name, P, level, G):
+    """Algorithmic bytes and operations of the stage kernel `name` summed over its
+    launches in one batched group of G HRotates at `level` (fused pipeline): each
+    NTT pass reads and writes its limbs once, the base conversions read their input
+    and write their output limbs once, the inner product reads the decomposed limbs
+    and both key halves and writes two extended polynomials."""
+    W = 4 * P.N
+    K, A, beta = P.K, P.alpha, P.beta(level)
+    widths = [min(A, level - j * A) for j in range(beta)]
+    conv = sum(level + K - w for w in widths)  # limbs ModUp produces by conversion
+    logn = P.N.bit_length() - 1
+    bf_col, bf_blk = P.N // 2 * (logn - 8), P.N // 2 * 8  # butterflies of one pass over one limb
+    macs = (sum(w * (level + K - w) for w in widths) + 2 * K * level) * P.N
+    m = {
+        "intt_blk+gather": (2 * level * W, level * bf_blk, "bfly"),
+        "intt_col+scale": (2 * (level + 2 * K) * W, (level + 2 * K) * bf_col, "bfly"),
+        "ntt_col": (2 * (conv + 2 * level) * W, (conv + 2 * level) * bf_col, "bfly"),
+        "ntt_blk": (2 * conv * W, conv * bf_blk, "bfly"),
+        "intt_blk": (2 * 2 * K * W, 2 * K * bf_blk, "bfly"),
+        "ntt_blk+combine": (7 * level * W, 2 * level * bf_blk, "bfly"),
+        "bconv": ((level + conv + 2 * K + 2 * level) * W, macs, "mac"),
+        "bconv_tc": ((level + conv + 2 * K + 2 * level) * W, macs, "mac"),
+        "inner_product": ((level + K) * (3 * beta + 2) * W, 2 * beta * (level + K) * P.N, "mac"),
+    }
+    b, o, unit = m.get(name, (0, 0, "bfly"))
+    return b * G, o * G, unit
+
+
+# ALU peaks from the probe's per-SM unit counts at the maximum SM clock (152 SMs, 2.07 GHz):
+# a Shoup radix-2 butterfly takes >= 4 IMAD-pipe issue cycles (IMAD.HI is half rate) ->
+# 16 per clock per SM; a 32x32->64-bit multiply-accumulate (IMAD.WIDE) ~23 per clock per SM.
+ALU_PEAK = {"bfly": 16 * 152 * 2.07e9, "mac": 23 * 152 * 2.07e9}
+
+
+def kernel_roofline(name, launches_per_group, launch_ms, P, level, G, hbm_peak):
+    """Roofline entry of one kernel: the bound (HBM bytes or ALU operations) with the
+    larger achieved fraction of its peak."""
+    nbytes, ops, unit = kernel_model(name, P, level, G)
+    lpg = max(launches_per_group, 1e-9)
+    per_launch_bytes, per_launch_ops = nbytes / lpg, ops / lpg
+    gbs = per_launch_bytes / (launch_ms / 1e3) / 1e9
+    ach_ops = per_launch_ops / (launch_ms / 1e3)
+    f_hbm, f_alu = gbs / hbm_peak, ach_ops / ALU_PEAK[unit]
+    common = {"traffic": None, "kernel": name, "launch_ms": launch_ms,
+              "algorithmic_bytes_per_launch": per_launch_bytes, "algorithmic_ops_per_launch": per_launch_ops,
+              "frac_hbm": f_hbm, "frac_alu": f_alu}
+    if f_alu >= f_hbm:
+        return {"bound": "alu", "achieved": ach_ops / 1e12, "peak": ALU_PEAK[unit] / 1e12, "unit": f"T{unit}/s",
+                "frac": f_alu, "peak_source": "derived from probe unit counts x 152 SMs x 2.07 GHz", **common}
+    return {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": f_hbm,
+            "peak_source": "measured (hbm_gbs)", **common}
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
@@ -279,6 +335,20 @@ def main():
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
 
+    if args.profile_run:
+        ctx.set_fused(True)
+        ctx.set_bconv(binding.FHE_BCONV_TC if args.profile_run == "tc" else binding.FHE_BCONV_SCALAR)
+        ctx.set_batch(0, 0, 1)
+        plan_p = ctx.batch_plan(items, 0)
+        for _ in range(args.warmup + args.steps):
+            plan_p.launch()
+        ctx.sync()
+        print(f"profile run: {B} HRotates at N={P.N}, L={level}, groups {plan_p.groups}, "
+              f"{args.warmup + args.steps} launches of {plan_p.kernel_count} kernels", file=sys.stderr)
+        plan_p.close()
+        ctx.close()
+        return
+
     def timed(fn, steps):
         if ws > 1:
             import torch.distributed as dist
@@ -313,6 +383,7 @@ def main():
     # --- headline: batched fused pipeline, tensor-core base conversion, one CUDA graph
     ctx.set_bconv(binding.FHE_BCONV_TC)
     plan = ctx.batch_plan(items, binding.FHE_PLAN_GRAPH)
+    head_groups = plan.groups
     for _ in range(max(3, args.warmup)):
         plan.launch()
     ctx.sync()
@@ -347,8 +418,11 @@ def main():
     fused_ks = B * cmp_steps * ws / (ms_fused / 1e3)
 
     # --- per-kernel times (CUDA events around each launch on its stream): the same batched
-    # stage programs as the headline, launched directly instead of through the graph
+    # stage programs as the headline, launched directly on one lane (no concurrent lane
+    # inflates a kernel's event interval)
+    ctx.set_batch(0, 0, 1)
     plan_direct = ctx.batch_plan(items, 0)
+    ctx.set_batch(0, 0, 0)
     for _ in range(3):
         plan_direct.launch()
     ctx.trace(True)
@@ -358,58 +432,31 @@ def main():
     ctx.trace(False)
     ms_batched_direct = timed(plan_direct.launch, cmp_steps)
     batched_direct_ks = B * cmp_steps * ws / (ms_batched_direct / 1e3)
-    groups = plan.groups
+    groups = plan_direct.groups
     plan_direct.close()
     total_ms = sum(v[1] for v in stats.values())
     top_name, (top_n, top_ms) = max(stats.items(), key=lambda kv: kv[1][1])
     per_launch_ms = top_ms / top_n
 
-    # --- L2 bandwidth (read + write of a 32 MB block, as in the paper's method) and peaks
+    # --- peaks: HBM from the measured file; L2 measured here with the library's probe
+    # (read + write of a 64 MB block, smaller than the L2, as in the paper's method)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    blk = torch.empty(8 << 20, dtype=torch.int32, device=f"cuda:{dev}")
-    blk2 = torch.empty_like(blk)
-    for _ in range(5):
-        blk2.copy_(blk)
-    l2_ms = timed(lambda: blk2.copy_(blk), 200)
-    l2_gbs = 2 * blk.numel() * 4 * 200 / (l2_ms / 1e3) / 1e9
+    l2 = binding.probe_bandwidth(dev, 64 << 20, 50)
+    l2_gbs = l2["copy"]
 
     # algorithmic bytes of the headline step and its L2-roofline fraction (paper's definition)
     bks = roofline.ks_bytes(P.N, level, P.K, P.alpha)
     l2_frac = (bks / (l2_gbs * 1e9)) / ((ms / 1e3) / (B * args.steps))
 
-    # dominant kernel: algorithmic bytes per launch and butterflies per launch
-    W = 4 * P.N
-    beta = P.beta(level)
-    conv = beta * (level + P.K) - level
-    # limbs one launch of each kernel transforms per item (ModUp and ModDown launches of one name
-    # averaged), times the items of an average group
-    limbs = {"intt_blk+gather": level, "intt_col+scale": (level + 2 * P.K) / 2.0, "ntt_col": (conv + 2 * level) / 2.0,
-             "ntt_blk": conv, "intt_blk": 2 * P.K, "ntt_blk+combine": 2 * level}
-    items_per_launch = B / max(1, len(groups))
-    n_l = limbs.get(top_name, level) * items_per_launch
-    half = 8 if top_name.endswith(("blk", "blk+gather", "blk+ip", "blk+combine")) else P.N.bit_length() - 1 - 8
-    bfly = n_l * (P.N // 2) * half
-    traffic_bytes = 2 * n_l * W
-    achieved_gbs = traffic_bytes / (per_launch_ms / 1e3) / 1e9
-    sm_clock_ghz = (clk["sm_mhz"] if clk else 1900.0) / 1e3
-    # ALU peak: a Shoup radix-2 butterfly needs >= 4 IMAD-pipe issue cycles (IMAD.HI is half rate),
-    # 64 IMAD lanes per SM per clock -> 16 butterflies / clock / SM
-    alu_peak = 16 * 152 * 2.07e9 / 1e12  # T butterflies/s at the maximum SM clock
-    alu_ach = bfly / (per_launch_ms / 1e3) / 1e12
-    if alu_ach / alu_peak >= achieved_gbs / hbm_peak:
-        roof = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "Tbutterfly/s",
-                "frac": alu_ach / alu_peak, "traffic": None, "kernel": top_name,
-                "peak_source": "derived: 16 Shoup butterflies/clk/SM x 152 SMs x 2.07 GHz",
-                "achieved_l2_gbs": achieved_gbs}
-    else:
-        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved_gbs / hbm_peak, "traffic": None, "kernel": top_name, "peak_source": "measured"}
-    roof["launch_ms"] = per_launch_ms
+    # dominant kernel of the batched step: algorithmic bytes and operations per launch
+    ngroups = max(1, len(groups))
+    roof = kernel_roofline(top_name, top_n / (cmp_steps * ngroups), per_launch_ms, P, level, B / ngroups,
+                           hbm_peak)
     roof["share"] = top_ms / total_ms if total_ms else None
 
     # --- e2e: host pinned buffers, copies inside the timed region, same public API
@@ -461,12 +508,12 @@ def main():
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io},
             "roofline": roof,
             "cpu_baseline": cpu,
-            "l2_roofline": {"bytes_per_ks": bks, "l2_gbs_measured": l2_gbs, "frac": l2_frac,
+            "l2_roofline": {"bytes_per_ks": bks, "l2_gbs_measured": l2_gbs, "frac": l2_frac, "l2_probe": l2,
                             "definition": "B_KS(l) / measured L2 read+write bandwidth / time per key switch"},
             "paths": {"graph_batched_tc_bconv": value, "graph_batched_scalar_bconv": graph_scalar_ks,
                       "direct_batched_tc_bconv": batched_direct_ks, "direct_fused_single_scalar": fused_ks,
                       "plain_per_kernel_single_scalar": plain_ks},
-            "batch_groups": groups,
+            "batch_groups": head_groups, "lanes": 2, "traced_groups_one_lane": groups,
             "other_workloads": extra,
             "kernels": {k: {"launches": v[0], "ms": v[1], "share": v[1] / total_ms} for k, v in
                         sorted(stats.items(), key=lambda kv: -kv[1][1])},

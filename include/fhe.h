@@ -234,11 +234,14 @@ FHE_API int fhe_plan_kernel_count(const fhe_plan *plan);
 /* sizes of the plan's item groups (at most max written); returns the number of groups */
 FHE_API int fhe_plan_groups(const fhe_plan *plan, int *sizes, int max);
 /*
- * Group sizing of later plans: a group's stage-1 working sets (beta(l)(l+K)
- * limbs per item) stay within l2_budget_bytes (0: 3/4 of the device's L2) and
- * a group holds at most max_group items (0: 8).  The autotuner sets these.
+ * Group sizing of later plans: the stage-1 working sets (beta(l)(l+K) limbs per
+ * item) of the groups resident at once stay within l2_budget_bytes (0: 3/4 of
+ * the device's L2), a group holds at most max_group items (0: 8), and groups
+ * run round-robin on `lanes` concurrent streams (0: 2), each lane with its own
+ * workspace, so that one group's DRAM-bound inner product overlaps another
+ * group's transforms.  The autotuner sets these.
  */
-FHE_API int fhe_ctx_set_batch(fhe_ctx *ctx, size_t l2_budget_bytes, int max_group);
+FHE_API int fhe_ctx_set_batch(fhe_ctx *ctx, size_t l2_budget_bytes, int max_group, int lanes);
 
 /*
  * Kernel tracing (measurement support): while enabled, every kernel the
@@ -253,6 +256,15 @@ typedef struct {
   double total_ms;
 } fhe_kernel_stat;
 FHE_API int fhe_trace_enable(fhe_ctx *ctx, int on);
+/*
+ * Bandwidth probe: read, write and read+write (copy) throughput in GB/s of a
+ * `bytes` block accessed `reps` times with 128-bit L2-cached loads and stores
+ * on `device` (allocates and frees two blocks).  A block smaller than the L2
+ * measures the L2 (the paper's method for its L2 bandwidth figure); the
+ * benchmark uses the copy figure as the denominator of its L2-roofline fraction.
+ */
+FHE_API int fhe_probe_bandwidth(int device, size_t bytes, int reps, double *read_gbs, double *write_gbs,
+                                double *copy_gbs);
 FHE_API int fhe_trace_read(fhe_ctx *ctx, fhe_kernel_stat *out, int max, int *n);
 
 /*

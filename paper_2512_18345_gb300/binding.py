@@ -31,7 +31,7 @@ EXPORTS = (
     "fhe_rotate_hoisted", "fhe_linear_transform", "fhe_pmult", "fhe_add", "fhe_ntt", "fhe_intt", "fhe_modup", "fhe_moddown",
     "fhe_bconv", "fhe_batch_plan", "fhe_batch_launch", "fhe_plan_destroy", "fhe_plan_kernel_count",
     "fhe_plan_groups", "fhe_ctx_set_batch",
-    "fhe_trace_enable", "fhe_trace_read", "fhe_bconv_noalloc", "fhe_last_error",
+    "fhe_trace_enable", "fhe_trace_read", "fhe_probe_bandwidth", "fhe_bconv_noalloc", "fhe_last_error",
 )
 
 
@@ -107,8 +107,10 @@ def lib() -> ctypes.CDLL:
         "fhe_plan_destroy": [vp],
         "fhe_plan_kernel_count": [vp],
         "fhe_plan_groups": [vp, ip, ctypes.c_int],
-        "fhe_ctx_set_batch": [vp, ctypes.c_size_t, ctypes.c_int],
+        "fhe_ctx_set_batch": [vp, ctypes.c_size_t, ctypes.c_int, ctypes.c_int],
         "fhe_trace_enable": [vp, ctypes.c_int],
+        "fhe_probe_bandwidth": [ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
         "fhe_trace_read": [vp, ctypes.POINTER(KernelStat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
         "fhe_bconv_noalloc": [vp, vp, ip, ctypes.c_int, vp, ip, ctypes.c_int, vp],
         "fhe_last_error": [],
@@ -158,6 +160,13 @@ def to_numpy(t) -> np.ndarray:
 def empty(shape, device: int = 0):
     import torch
     return torch.empty(tuple(shape), dtype=torch.int32, device=f"cuda:{device}")
+
+
+def probe_bandwidth(device: int = 0, nbytes: int = 64 << 20, reps: int = 50) -> dict:
+    """L2 (block smaller than L2) or DRAM bandwidth of 128-bit accesses, GB/s."""
+    r, w, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    check(lib().fhe_probe_bandwidth(device, nbytes, reps, ctypes.byref(r), ctypes.byref(w), ctypes.byref(c)))
+    return {"read": r.value, "write": w.value, "copy": c.value, "bytes": nbytes}
 
 
 class Plan:
@@ -239,8 +248,8 @@ class Context:
     def set_bconv(self, mode: int) -> None:
         check(lib().fhe_ctx_set_bconv(self.h, mode))
 
-    def set_batch(self, l2_budget_bytes: int = 0, max_group: int = 0) -> None:
-        check(lib().fhe_ctx_set_batch(self.h, l2_budget_bytes, max_group))
+    def set_batch(self, l2_budget_bytes: int = 0, max_group: int = 0, lanes: int = 0) -> None:
+        check(lib().fhe_ctx_set_batch(self.h, l2_budget_bytes, max_group, lanes))
 
     def set_fused(self, fused: bool) -> None:
         check(lib().fhe_ctx_set_fused(self.h, int(bool(fused))))

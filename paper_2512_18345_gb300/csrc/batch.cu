@@ -25,19 +25,41 @@ struct fhe_plan {
   std::vector<std::vector<std::pair<const uint32_t *, uint32_t *>>> copies;  // identity rotations per group
   size_t copy_bytes = 0;
   std::vector<int> group_sizes;
+  int nlanes = 1;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int kernels = 0;
 };
 
+// Groups run round-robin on the plan's lanes: lane 0 on the caller's stream,
+// lane l > 0 on the context's lane stream l, forked from and joined back into
+// the caller's stream.  Each lane has its own workspace slots, so groups on
+// different lanes overlap (one group's DRAM-bound inner product next to
+// another group's ALU-bound transforms).
 static int enqueue_plan(fhe_plan *p, cudaStream_t s) {
   fhe_ctx *c = p->ctx;
-  for (size_t g = 0; g < p->progs.size(); g++) {
-    for (auto &cp : p->copies[g])
-      if (cudaMemcpyAsync(cp.second, cp.first, p->copy_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-        return fhe_fail(FHE_ECUDA, "fhe_batch: copy");
-    int rc = run_program_dev(c, p->progs[g], p->dev[g], s);
+  const int nl = p->nlanes;
+  if (nl > 1) {
+    int rc = ensure_lanes(c, nl);
     if (rc != FHE_OK) return rc;
+    if (cudaEventRecord(c->lanes[0].done, s) != cudaSuccess) return fhe_fail(FHE_ECUDA, "fhe_batch: fork");
+    for (int l = 1; l < nl; l++)
+      if (cudaStreamWaitEvent(c->lanes[l].stream, c->lanes[0].done, 0) != cudaSuccess)
+        return fhe_fail(FHE_ECUDA, "fhe_batch: fork");
+  }
+  for (size_t g = 0; g < p->progs.size(); g++) {
+    const int lane = (int)(g % nl);
+    cudaStream_t q = lane == 0 ? s : c->lanes[lane].stream;
+    for (auto &cp : p->copies[g])
+      if (cudaMemcpyAsync(cp.second, cp.first, p->copy_bytes, cudaMemcpyDeviceToDevice, q) != cudaSuccess)
+        return fhe_fail(FHE_ECUDA, "fhe_batch: copy");
+    int rc = run_program_dev(c, p->progs[g], p->dev[g], q, lane);
+    if (rc != FHE_OK) return rc;
+  }
+  for (int l = 1; l < nl; l++) {
+    if (cudaEventRecord(c->lanes[l].done, c->lanes[l].stream) != cudaSuccess ||
+        cudaStreamWaitEvent(s, c->lanes[l].done, 0) != cudaSuccess)
+      return fhe_fail(FHE_ECUDA, "fhe_batch: join");
   }
   return FHE_OK;
 }
@@ -49,10 +71,11 @@ static void destroy(fhe_plan *p) {
   delete p;
 }
 
-extern "C" int fhe_ctx_set_batch(fhe_ctx *c, size_t l2_budget_bytes, int max_group) {
-  if (!c || max_group < 0) return fhe_fail(FHE_EINVAL, "fhe_ctx_set_batch: bad arguments");
+extern "C" int fhe_ctx_set_batch(fhe_ctx *c, size_t l2_budget_bytes, int max_group, int lanes) {
+  if (!c || max_group < 0 || lanes < 0 || lanes > 8) return fhe_fail(FHE_EINVAL, "fhe_ctx_set_batch: bad arguments");
   c->batch_budget = l2_budget_bytes;
   c->batch_max_group = max_group;
+  c->batch_lanes = lanes ? lanes : 2;
   return FHE_OK;
 }
 
@@ -83,6 +106,8 @@ extern "C" int fhe_batch_plan(fhe_ctx *c, const fhe_ks_item *items, int n, int f
     budget = (size_t)l2 * 3 / 4;
   }
   const int max_group = c->batch_max_group > 0 ? c->batch_max_group : 8;
+  const int nl = std::max(1, c->batch_lanes);
+  budget /= nl;  // groups on different lanes are resident in L2 at the same time
   std::vector<std::vector<int>> groups(1);
   size_t used = 0;
   for (int i = 0; i < n; i++) {
@@ -96,7 +121,13 @@ extern "C" int fhe_batch_plan(fhe_ctx *c, const fhe_ks_item *items, int n, int f
     used += fp;
   }
   int rc = FHE_OK;
-  for (auto &grp : groups) {
+  p->nlanes = std::min<int>(nl, (int)groups.size());
+  if (p->nlanes < 1) p->nlanes = 1;
+  size_t gmax = 1;
+  for (auto &grp : groups) gmax = std::max(gmax, grp.size());
+  for (size_t gi = 0; gi < groups.size(); gi++) {
+    auto &grp = groups[gi];
+    const int slot0 = (int)(gi % p->nlanes) * (int)gmax;
     std::vector<Item> its;
     std::vector<std::pair<const uint32_t *, uint32_t *>> cps;
     for (int i : grp) {
@@ -122,7 +153,7 @@ extern "C" int fhe_batch_plan(fhe_ctx *c, const fhe_ks_item *items, int n, int f
         it.galois = k;
         it.key = c->find_key(x.rot);
       }
-      it.slot = (int)its.size();
+      it.slot = slot0 + (int)its.size();
       its.push_back(it);
     }
     // copies of identity rotations have level-dependent sizes: handle them as one-item groups

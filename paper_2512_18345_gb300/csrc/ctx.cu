@@ -252,6 +252,25 @@ static int build_tables(fhe_ctx *c) {
   return FHE_OK;
 }
 
+int ensure_lanes(fhe_ctx *c, int n) {
+  while ((int)c->lanes.size() < n) {
+    fhe_ctx::Lane l;
+    if (c->lanes.empty()) {
+      l.aux = c->aux;
+      l.fork = c->ev_fork;
+      l.join = c->ev_join;
+    } else {
+      CUDA_OR_FAIL(cudaStreamCreateWithFlags(&l.aux, cudaStreamNonBlocking));
+      CUDA_OR_FAIL(cudaEventCreateWithFlags(&l.fork, cudaEventDisableTiming));
+      CUDA_OR_FAIL(cudaEventCreateWithFlags(&l.join, cudaEventDisableTiming));
+    }
+    CUDA_OR_FAIL(cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking));
+    CUDA_OR_FAIL(cudaEventCreateWithFlags(&l.done, cudaEventDisableTiming));
+    c->lanes.push_back(l);
+  }
+  return FHE_OK;
+}
+
 int ensure_slots(fhe_ctx *c, int n) {
   const size_t N = c->N;
   const int L = c->L, K = c->K, B = c->beta(L);
@@ -307,6 +326,15 @@ fhe_ctx::~fhe_ctx() {
   for (auto &kv : rot_keys) cudaFree(kv.second);
   for (auto p : scratch_tabs) cudaFree(p);
   if (order_ev) cudaEventDestroy(order_ev);
+  for (size_t i = 0; i < lanes.size(); i++) {
+    if (i > 0) {
+      cudaStreamDestroy(lanes[i].aux);
+      cudaEventDestroy(lanes[i].fork);
+      cudaEventDestroy(lanes[i].join);
+    }
+    cudaStreamDestroy(lanes[i].stream);
+    cudaEventDestroy(lanes[i].done);
+  }
   if (ev_fork) cudaEventDestroy(ev_fork);
   if (ev_join) cudaEventDestroy(ev_join);
   if (aux) cudaStreamDestroy(aux);

@@ -68,6 +68,14 @@ struct fhe_ctx {
   cudaEvent_t order_ev = nullptr;
   cudaStream_t aux = nullptr;  // concurrent branch of the fused pipeline
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // batched plans run their item groups on several lanes; each lane has its own
+  // stream, auxiliary stream and fork / join events (lane 0 reuses aux / ev_fork / ev_join)
+  struct Lane {
+    cudaStream_t stream = nullptr, aux = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, done = nullptr;
+  };
+  std::vector<Lane> lanes;
+  int batch_lanes = 2;
 
   int beta(int level) const;
   int ext_prime(int level, int t) const;
@@ -80,5 +88,6 @@ int fhe_fail(int code, const char *fmt, ...);
 uint32_t h_mulmod_pub(uint32_t a, uint32_t b, uint32_t q);
 uint32_t h_invmod_pub(uint32_t a, uint32_t q);
 int ensure_slots(fhe_ctx *c, int n);
+int ensure_lanes(fhe_ctx *c, int n);
 uint32_t fhe_galois_elt(int32_t rot, uint32_t N);
 bool fhe_tc_available();

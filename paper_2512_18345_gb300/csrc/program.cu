@@ -278,8 +278,11 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
 // ------------------------------------------------------------------ execution
 
 static cudaError_t launch_stage(fhe_ctx *c, const Stage &st, const SegList &sl, const BconvArgs &ba,
-                                cudaStream_t s) {
-  cudaStream_t q = st.aux ? c->aux : s;
+                                cudaStream_t s, int lane) {
+  cudaStream_t aux = lane > 0 ? c->lanes[lane].aux : c->aux;
+  cudaEvent_t ev_fork = lane > 0 ? c->lanes[lane].fork : c->ev_fork;
+  cudaEvent_t ev_join = lane > 0 ? c->lanes[lane].join : c->ev_join;
+  cudaStream_t q = st.aux ? aux : s;
   switch (st.kind) {
     case Stage::NTT: return launch_ntt_pass(c->tabs, st.column, st.fwd, st.pro, st.epi, sl, q);
     case Stage::EW: return launch_ew(c->tabs, st.ewop, sl, q);
@@ -288,11 +291,11 @@ static cudaError_t launch_stage(fhe_ctx *c, const Stage &st, const SegList &sl, 
       return c->bconv_mode == FHE_BCONV_TC ? launch_bconv_tc(c->tabs, ba, st.max_in, st.max_out, q)
                                            : launch_bconv(c->tabs, ba, st.max_in, st.max_out, q);
     case Stage::FORK: {
-      cudaError_t e = cudaEventRecord(c->ev_fork, s);
-      return e != cudaSuccess ? e : cudaStreamWaitEvent(c->aux, c->ev_fork, 0);
+      cudaError_t e = cudaEventRecord(ev_fork, s);
+      return e != cudaSuccess ? e : cudaStreamWaitEvent(aux, ev_fork, 0);
     }
-    case Stage::JOIN_RECORD: return cudaEventRecord(c->ev_join, c->aux);
-    case Stage::JOIN_WAIT: return cudaStreamWaitEvent(s, c->ev_join, 0);
+    case Stage::JOIN_RECORD: return cudaEventRecord(ev_join, aux);
+    case Stage::JOIN_WAIT: return cudaStreamWaitEvent(s, ev_join, 0);
   }
   return cudaErrorInvalidValue;
 }
@@ -317,7 +320,7 @@ int run_program_inline(fhe_ctx *c, const Program &P, cudaStream_t s) {
     }
     for (size_t i = 0; i < P.ks.size(); i++) sl.ks[i] = P.ks[i];
     for (const BconvGroup &g : st.groups) ba.g[ba.ngroups++] = g;
-    cudaError_t e = launch_stage(c, st, sl, ba, s);
+    cudaError_t e = launch_stage(c, st, sl, ba, s, 0);
     if (e != cudaSuccess) return fhe_fail(FHE_ECUDA, "stage launch: %s", cudaGetErrorString(e));
   }
   return FHE_OK;
@@ -375,9 +378,9 @@ int upload_program(fhe_ctx *c, const Program &P, DevProgram &D) {
   return FHE_OK;
 }
 
-int run_program_dev(fhe_ctx *c, const Program &P, const DevProgram &D, cudaStream_t s) {
+int run_program_dev(fhe_ctx *c, const Program &P, const DevProgram &D, cudaStream_t s, int lane) {
   for (size_t i = 0; i < P.stages.size(); i++) {
-    cudaError_t e = launch_stage(c, P.stages[i], D.lists[i], D.bargs[i], s);
+    cudaError_t e = launch_stage(c, P.stages[i], D.lists[i], D.bargs[i], s, lane);
     if (e != cudaSuccess) return fhe_fail(FHE_ECUDA, "stage launch: %s", cudaGetErrorString(e));
   }
   return FHE_OK;

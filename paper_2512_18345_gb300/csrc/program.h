@@ -50,6 +50,7 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
 bool program_fits_inline(const Program &P);
 int run_program_inline(fhe_ctx *c, const Program &P, cudaStream_t s);
 int upload_program(fhe_ctx *c, const Program &P, DevProgram &D);
-int run_program_dev(fhe_ctx *c, const Program &P, const DevProgram &D, cudaStream_t s);
+// lane: which lane's auxiliary stream and fork / join events the program uses
+int run_program_dev(fhe_ctx *c, const Program &P, const DevProgram &D, cudaStream_t s, int lane);
 void free_program(DevProgram &D);
 int run_items_chunked(fhe_ctx *c, const std::vector<Item> &items, int first_slot, cudaStream_t s);

@@ -251,13 +251,13 @@ def test_batch_plan_equals_single_ops(c1):
     plan.close()
 
 
-@pytest.mark.parametrize("budget,max_group", [(0, 0), (1, 2), (0, 3)])
-def test_batch_plan_full_size_groups(c2, budget, max_group):
+@pytest.mark.parametrize("budget,max_group,lanes", [(0, 0, 1), (1, 2, 2), (0, 3, 2), (0, 1, 3)])
+def test_batch_plan_full_size_groups(c2, budget, max_group, lanes):
     """Mixed rotations / relinearisations / key switches at uneven levels,
     N = 2^16, split into groups of various sizes: every item bit-exact."""
     from paper_2512_18345_gb300 import binding
     P, OP, ctx = c2
-    ctx.set_batch(budget, max_group)
+    ctx.set_batch(budget, max_group, lanes)
     g = inputs.rng(95 + max_group)
     rk = rand_key(P, g)
     ctx.set_relin_key(dev(rk))
@@ -286,7 +286,7 @@ def test_batch_plan_full_size_groups(c2, budget, max_group):
     for i, (it, w) in enumerate(zip(items, want)):
         assert np.array_equal(host(it["out"]), w), f"item {i} {specs[i]}"
     plan.close()
-    ctx.set_batch(0, 0)
+    ctx.set_batch(0, 0, 0)
 
 
 # ------------------------------------------------------------------ CKKS semantics through the GPU path
