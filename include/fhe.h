@@ -89,7 +89,8 @@ typedef struct {
 
 /* BConv implementation selector (fhe_ctx_set_bconv).  Both give identical bits. */
 #define FHE_BCONV_SCALAR 0 /* CUDA-core 64-bit multiply-accumulate, one final reduction */
-#define FHE_BCONV_TC 1     /* tensor cores: 8-bit digit split, exact fp32 accumulation */
+#define FHE_BCONV_TC 1     /* tensor cores: 8-bit digit split, f16 operands, exact fp32 accumulation;
+                              needs alpha <= 8 and K <= 8 (fhe_bconv: n_in <= 8) */
 
 /*
  * Create a context for ring degree N (a power of two, 2^12..2^16), ciphertext
@@ -104,7 +105,9 @@ FHE_API int fhe_ctx_create(fhe_ctx **out, uint32_t N, const uint32_t *q, int L, 
                    int device);
 FHE_API int fhe_ctx_destroy(fhe_ctx *ctx);
 FHE_API int fhe_ctx_info(const fhe_ctx *ctx, fhe_info *out);
-/* Select the BConv implementation for later calls (FHE_BCONV_SCALAR / FHE_BCONV_TC). */
+/* Select the BConv implementation for later calls (FHE_BCONV_SCALAR / FHE_BCONV_TC).
+ * FHE_EUNSUPPORTED for FHE_BCONV_TC when alpha > 8 or K > 8 (the exactness bound
+ * of the tensor-core digit split holds for at most 8 inputs per conversion). */
 FHE_API int fhe_ctx_set_bconv(fhe_ctx *ctx, int mode);
 /*
  * Synchronize the context's device and report device-side failures: returns
@@ -195,7 +198,8 @@ FHE_API int fhe_add(fhe_ctx *ctx, const uint32_t *a, const uint32_t *b, int npol
  *   fhe_bconv: coefficient-form fast base conversion of in [n_in][N] (primes
  *     in_idx) to out [n_out][N] (primes out_idx), Section II-B "BConv" with the
  *     table T[i][j] = (Qstar / q_j) mod p_i of Section III-C and the
- *     [(Qstar / q_j)^-1]_{q_j} pre-multiplication; n_in <= 16, n_out <= 64.
+ *     [(Qstar / q_j)^-1]_{q_j} pre-multiplication; n_in <= 16, n_out <= 64
+ *     (n_in <= 8 under FHE_BCONV_TC, else FHE_EUNSUPPORTED).
  */
 FHE_API int fhe_ntt(fhe_ctx *ctx, uint32_t *a, const int *prime_idx, int n, fhe_stream stream);
 FHE_API int fhe_intt(fhe_ctx *ctx, uint32_t *a, const int *prime_idx, int n, fhe_stream stream);

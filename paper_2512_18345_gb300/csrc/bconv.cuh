@@ -25,9 +25,14 @@ struct BconvGroup {
   const uint32_t *T;    // [n_out][n_in] device table
   const int2 *omap;     // [n_out] (limb offset from out, prime index)
   int n_in, n_out;
-  const uint16_t *Btc;  // tensor-core path: byte-digit table, canonical layout, npad x kpad bf16
-  int kpad, npad;       // round16(4 n_in), round16(4 n_out)
+  const uint16_t *Btc;  // tensor-core path: digit table, canonical layout, npad x kTcK f16
+  int npad;             // tc_npad(n_out)
 };
+
+// tensor-core base conversion: 128 coefficients per MMA, K = 32 data slots
+// (4 bytes of at most 8 inputs) + 4 offset slots + 12 zero slots
+constexpr int kTcM = 128, kTcK = 48, kTcMaxIn = 8;
+__host__ __device__ constexpr int tc_npad(int n_out) { return (4 * n_out + 15) / 16 * 16; }
 
 constexpr int kMaxBconvGroups = 8;
 struct BconvArgs {

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/fhe.h"
+#include "bconv.cuh"
 #include "elementwise.cuh"
 #include "internal.h"
 #include "ctx.h"
@@ -191,7 +192,8 @@ static int build_tables(fhe_ctx *c) {
       CUDA_OR_FAIL(upload(&c->modup_map[(size_t)(level - 1) * c->dnum + j], om));
       std::vector<uint32_t> pout;
       for (const int2 &m : om) pout.push_back(pr[m.y]);
-      CUDA_OR_FAIL(upload(&c->modup_Btc[(size_t)(level - 1) * c->dnum + j], fhe::bconv_tc_table(T, hi - lo, pout)));
+      if (hi - lo <= fhe::kTcMaxIn)  // tensor-core tables exist for digits of at most 8 limbs
+        CUDA_OR_FAIL(upload(&c->modup_Btc[(size_t)(level - 1) * c->dnum + j], fhe::bconv_tc_table(T, hi - lo, pout)));
     }
   }
   CUDA_OR_FAIL(upload(&c->d_mu_scale, mu_scale));
@@ -229,7 +231,8 @@ static int build_tables(fhe_ctx *c) {
   CUDA_OR_FAIL(upload(&c->d_pinv, pinv));
   CUDA_OR_FAIL(upload(&c->d_mdT, mdT));
   CUDA_OR_FAIL(upload(&c->d_mdmap, mdmap));
-  CUDA_OR_FAIL(upload(&c->d_md_Btc, fhe::bconv_tc_table(mdT, K, std::vector<uint32_t>(pr.begin(), pr.begin() + L))));
+  if (K <= fhe::kTcMaxIn)
+    CUDA_OR_FAIL(upload(&c->d_md_Btc, fhe::bconv_tc_table(mdT, K, std::vector<uint32_t>(pr.begin(), pr.begin() + L))));
   CUDA_OR_FAIL(upload(&c->d_status, std::vector<unsigned int>(1, 0u)));
   c->tabs.status = c->d_status;
 
@@ -433,6 +436,9 @@ extern "C" int fhe_ctx_set_bconv(fhe_ctx *c, int mode) {
   if (mode != FHE_BCONV_SCALAR && mode != FHE_BCONV_TC) return fhe_fail(FHE_EINVAL, "fhe_ctx_set_bconv: mode %d", mode);
   if (mode == FHE_BCONV_TC && !fhe_tc_available())
     return fhe_fail(FHE_EUNSUPPORTED, "fhe_ctx_set_bconv: tensor-core base conversion not built");
+  if (mode == FHE_BCONV_TC && (c->alpha > fhe::kTcMaxIn || c->K > fhe::kTcMaxIn))
+    return fhe_fail(FHE_EUNSUPPORTED, "fhe_ctx_set_bconv: tensor-core base conversion needs alpha <= %d and K <= %d",
+                    fhe::kTcMaxIn, fhe::kTcMaxIn);
   c->bconv_mode = mode;
   return FHE_OK;
 }

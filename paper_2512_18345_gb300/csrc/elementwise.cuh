@@ -4,6 +4,7 @@
 // parallel operations over L x N).  Four elements per thread; contiguous
 // reads and writes are 128-bit.
 #pragma once
+#include "async.cuh"
 #include "common.cuh"
 #include "ntt.cuh"
 
@@ -152,4 +153,144 @@ __global__ void __launch_bounds__(kEwThreads) k_ip(const __grid_constant__ SegLi
                                               reduce_u64(a1[3], P));
 }
 
+// Stage 2 as a persistent streaming kernel (the ext limbs are read in order).
+// A unit is kIpChunk coefficients of one extended limb.  Thread 0 streams each
+// unit's operands -- per digit the ModUp value (ext, or the own limb when it is
+// not read through an automorphism) and both key halves, 4 KB each -- into a
+// ring of shared-memory stages with cp.async.bulk, completing on one mbarrier
+// per stage, and writes the unit's descriptor (output, prime, digit count) next
+// to the stage; the copies of the next stages stay in flight while the CTA
+// reduces the current one.  Thread 0 alone polls the barrier (bounded); the
+// other threads sleep at the CTA barrier.  The own digit of a rotation
+// (sigma_{galois_own} applied on the fly) is gathered with plain loads issued
+// before the wait.
+constexpr int kIpChunk = 1024;  // coefficients per unit: 4 per thread
+constexpr int kIpThreads = 256;
+
+struct IpUnit {            // one unit, as the consumers need it
+  uint32_t *d0;            // u_0 at this unit's first coefficient; u_1 = d0 + d1_off
+  const uint32_t *gsrc;    // own limb read through the automorphism (nullptr: none)
+  PrimeC P;
+  uint32_t d1_off, galois, j0;
+  int beta, gjd;
+};
+
+template <bool GOWN>
+__global__ void __launch_bounds__(kIpThreads, 2) k_ip_bulk(const __grid_constant__ SegList sl, const PrimeC *pc,
+                                                           int logn, unsigned int *status, int beta_max, int stages) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int tid = threadIdx.x;
+  const size_t N = (size_t)1 << logn;
+  const int chunks = (int)(N / kIpChunk);
+  const int total = sl.total * chunks;
+  const size_t stage_words = (size_t)3 * beta_max * kIpChunk;
+  uint32_t *buf = reinterpret_cast<uint32_t *>(smem);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + (size_t)stages * stage_words * 4);
+  IpUnit *desc = reinterpret_cast<IpUnit *>(bar + stages);
+  __shared__ int s_ok;
+
+  // thread 0: describe unit u and stream its operands into stage st
+  auto issue = [&](int u, int st) {
+    int within;
+    const Seg &sg = seg_at(sl, seg_find(sl, u / chunks, within));
+    const KsArgs &ks = item_ks(sl, sg);
+    const int t = sg.t0 + within, row = sg.key_row0 + within;
+    const size_t c0 = (size_t)(u % chunks) * kIpChunk;
+    IpUnit d;
+    d.d0 = sg.dst + (size_t)within * N + c0;
+    d.d1_off = (uint32_t)((size_t)ks.n_ext * N);
+    d.P = pc[sg.prime + within];
+    d.beta = ks.beta;
+    d.gjd = (GOWN && t < ks.level) ? t / ks.alpha : -1;
+    d.gsrc = d.gjd >= 0 ? ks.own + (size_t)t * N : nullptr;
+    d.galois = ks.galois_own;
+    d.j0 = (uint32_t)c0;
+    desc[st] = d;
+    const size_t kstride = (size_t)2 * (ks.L + ks.K) * N, half = (size_t)(ks.L + ks.K) * N;
+    const uint32_t copies = 3u * (uint32_t)ks.beta - (d.gjd >= 0 ? 1u : 0u);
+    mbar_arrive_expect_tx(&bar[st], copies * kIpChunk * 4u);
+    uint32_t *dst = buf + (size_t)st * stage_words;
+    for (int jd = 0; jd < ks.beta; jd++) {
+      if (jd != d.gjd) {
+        const bool own = t < ks.level && t >= jd * ks.alpha && t < (jd + 1) * ks.alpha;
+        const uint32_t *e = own ? ks.own + (size_t)t * N : ks.ext + ((size_t)jd * ks.n_ext + t) * N;
+        bulk_g2s(dst + (size_t)(3 * jd) * kIpChunk, e + c0, kIpChunk * 4u, &bar[st]);
+      }
+      const uint32_t *kp = ks.key + jd * kstride + (size_t)row * N + c0;
+      bulk_g2s(dst + (size_t)(3 * jd + 1) * kIpChunk, kp, kIpChunk * 4u, &bar[st]);
+      bulk_g2s(dst + (size_t)(3 * jd + 2) * kIpChunk, kp + half, kIpChunk * 4u, &bar[st]);
+    }
+  };
+  if (tid == 0) {
+    for (int st = 0; st < stages; st++) mbar_init(&bar[st], 1);
+    for (int st = 0; st < stages; st++) {
+      const int u = blockIdx.x + st * gridDim.x;
+      if (u < total) issue(u, st);
+    }
+  }
+  __syncthreads();
+
+  // the gathered own values of a unit are loaded one unit ahead (after the wait
+  // that orders the unit's descriptor), so their latency overlaps a unit's work
+  auto gather = [&](const IpUnit &d) {
+    const uint32_t j = d.j0 + tid * 4;
+    return make_uint4(__ldg(d.gsrc + galois_src(j, d.galois, logn)), __ldg(d.gsrc + galois_src(j + 1, d.galois, logn)),
+                      __ldg(d.gsrc + galois_src(j + 2, d.galois, logn)), __ldg(d.gsrc + galois_src(j + 3, d.galois, logn)));
+  };
+  uint4 gnext = make_uint4(0, 0, 0, 0);
+  if (GOWN && (int)blockIdx.x < total && desc[0].gjd >= 0) gnext = gather(desc[0]);
+  bool ok = true;
+  int k = 0;
+  for (int u = blockIdx.x; u < total; u += gridDim.x, k++) {
+    const int st = k % stages;
+    const IpUnit d = desc[st];
+    const uint4 gv = gnext;
+    if (tid == 0) s_ok = mbar_wait_bounded(&bar[st], (uint32_t)(k / stages) & 1u) ? 1 : 0;
+    __syncthreads();
+    ok = s_ok != 0;
+    if (!ok) break;
+    if (GOWN && u + (int)gridDim.x < total) {  // descriptor of this CTA's next unit, written before this wait
+      const IpUnit dn = desc[(k + 1) % stages];
+      if (dn.gjd >= 0) gnext = gather(dn);
+    }
+    const uint32_t *src = buf + (size_t)st * stage_words + tid * 4;
+    uint64_t a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int jd = 0; jd < 4; jd++) {
+      if (jd < d.beta) {
+        const uint4 ev = jd == d.gjd ? gv : *reinterpret_cast<const uint4 *>(src + (size_t)(3 * jd) * kIpChunk);
+        const uint4 k0 = *reinterpret_cast<const uint4 *>(src + (size_t)(3 * jd + 1) * kIpChunk);
+        const uint4 k1 = *reinterpret_cast<const uint4 *>(src + (size_t)(3 * jd + 2) * kIpChunk);
+        const uint32_t e4[4] = {ev.x, ev.y, ev.z, ev.w}, k04[4] = {k0.x, k0.y, k0.z, k0.w},
+                       k14[4] = {k1.x, k1.y, k1.z, k1.w};
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+          a0[i] += (uint64_t)e4[i] * k04[i];
+          a1[i] += (uint64_t)e4[i] * k14[i];
+        }
+      }
+    }
+    uint32_t *d0 = d.d0 + tid * 4;
+    *reinterpret_cast<uint4 *>(d0) = make_uint4(reduce_u64(a0[0], d.P), reduce_u64(a0[1], d.P),
+                                                reduce_u64(a0[2], d.P), reduce_u64(a0[3], d.P));
+    *reinterpret_cast<uint4 *>(d0 + d.d1_off) = make_uint4(reduce_u64(a1[0], d.P), reduce_u64(a1[1], d.P),
+                                                           reduce_u64(a1[2], d.P), reduce_u64(a1[3], d.P));
+    __syncthreads();  // every thread is done with stage st and its descriptor
+    if (tid == 0) {
+      const int u2 = u + stages * gridDim.x;
+      if (u2 < total) {
+        fence_proxy_async_smem();
+        issue(u2, st);
+      }
+    }
+  }
+  if (!ok && tid == 0) {
+    // an expired wait: report it, then wait (bounded) for this CTA's copies still
+    // in flight so that none lands after the CTA has left the SM
+    atomicOr(status, 2u);
+    const int issued = (total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1;  // units of this CTA
+    for (int k2 = k; k2 < min(issued, k + stages); k2++)
+      mbar_wait_bounded(&bar[k2 % stages], (uint32_t)(k2 / stages) & 1u);
+  }
+}
 }  // namespace fhe

@@ -62,7 +62,9 @@ cudaError_t launch_bconv(const DevTables &t, const BconvArgs &a, int max_in, int
 cudaError_t launch_bconv_tc(const DevTables &t, const BconvArgs &a, int max_in, int max_out, cudaStream_t s);
 cudaError_t launch_ew(const DevTables &t, int op, const SegList &sl, cudaStream_t s);
 // key inner product (both halves) for the ext limbs of sl; seg.dst = u_0[t0]
-cudaError_t launch_ip(const DevTables &t, const SegList &sl, bool gather_own, bool gather_ext, cudaStream_t s);
+// beta_max: the largest digit count among the segments' items (sizes the stages)
+cudaError_t launch_ip(const DevTables &t, const SegList &sl, bool gather_own, bool gather_ext, int beta_max,
+                      cudaStream_t s);
 
 // number of kernels launched since the counter was last read (for the benchmark's launch count)
 long long kernel_launches();

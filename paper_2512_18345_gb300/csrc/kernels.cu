@@ -1,4 +1,5 @@
 // Kernel instantiations and launch wrappers.
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 
@@ -121,12 +122,36 @@ cudaError_t launch_bconv(const DevTables &t, const BconvArgs &a, int max_in, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_ip(const DevTables &t, const SegList &sl, bool gather_own, bool gather_ext, cudaStream_t s) {
-  const unsigned per_limb = (unsigned)((1u << t.logn) / (4 * kEwThreads));
-  const unsigned grid = (unsigned)sl.total * per_limb;
-  if (grid == 0) return cudaSuccess;
+cudaError_t launch_ip(const DevTables &t, const SegList &sl, bool gather_own, bool gather_ext, int beta_max,
+                      cudaStream_t s) {
+  if (sl.total == 0) return cudaSuccess;
   TraceScope ts(t, "inner_product", s);
   const bool go = gather_own, ge = gather_ext;
+  if (!ge && beta_max >= 1 && beta_max <= 4 && (1 << t.logn) % kIpChunk == 0) {
+    // streaming kernel: two CTAs per SM, as many stages as fit half an SM's shared memory
+    const int stage_bytes = 3 * beta_max * kIpChunk * 4;
+    const int per_stage = stage_bytes + 8 + (int)sizeof(IpUnit);
+    const int stages = std::min(8, (113 * 1024 - 256) / per_stage);
+    const int smem = stages * per_stage;
+    static bool configured[2] = {false, false};
+    if (!configured[go]) {
+      cudaError_t e = go ? cudaFuncSetAttribute(k_ip_bulk<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 113 * 1024)
+                         : cudaFuncSetAttribute(k_ip_bulk<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 113 * 1024);
+      if (e != cudaSuccess) return e;
+      configured[go] = true;
+    }
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int units = sl.total * ((1 << t.logn) / kIpChunk);
+    const unsigned grid = (unsigned)std::min(units, 2 * sms);
+    if (go) k_ip_bulk<true><<<grid, kIpThreads, smem, s>>>(sl, t.pc, t.logn, t.status, beta_max, stages);
+    else k_ip_bulk<false><<<grid, kIpThreads, smem, s>>>(sl, t.pc, t.logn, t.status, beta_max, stages);
+    g_launches++;
+    return cudaGetLastError();
+  }
+  const unsigned per_limb = (unsigned)((1u << t.logn) / (4 * kEwThreads));
+  const unsigned grid = (unsigned)sl.total * per_limb;
   if (go && ge) k_ip<true, true><<<grid, kEwThreads, 0, s>>>(sl, t.pc, t.logn);
   else if (go) k_ip<true, false><<<grid, kEwThreads, 0, s>>>(sl, t.pc, t.logn);
   else if (ge) k_ip<false, true><<<grid, kEwThreads, 0, s>>>(sl, t.pc, t.logn);

@@ -407,8 +407,7 @@ extern "C" int fhe_moddown(fhe_ctx *c, const uint32_t *u, int level, uint32_t *o
   g.n_in = K;
   g.n_out = level;
   g.Btc = c->d_md_Btc;
-  g.kpad = (4 * K + 15) / 16 * 16;
-  g.npad = (4 * level + 15) / 16 * 16;
+  g.npad = tc_npad(level);
   if (c->bconv_mode == FHE_BCONV_TC)
     LAUNCH_OR_FAIL(launch_bconv_tc(c->tabs, ba, K, level, s));
   else
@@ -438,6 +437,8 @@ extern "C" int fhe_bconv(fhe_ctx *c, const uint32_t *in, const int *in_idx, int 
     if (out_idx[i] < 0 || out_idx[i] >= NP) return fhe_fail(FHE_EINVAL, "fhe_bconv: out prime index");
   const size_t N = c->N;
   if (overlaps(in, 4 * N * n_in, out, 4 * N * n_out)) return fhe_fail(FHE_EALIAS, "fhe_bconv: out overlaps in");
+  if (c->bconv_mode == FHE_BCONV_TC && n_in > kTcMaxIn)
+    return fhe_fail(FHE_EUNSUPPORTED, "fhe_bconv: tensor-core base conversion takes at most %d inputs", kTcMaxIn);
   const std::vector<uint32_t> &pr = c->primes;
   // host tables: pre-factor (Qstar/q_j)^-1 mod q_j and T[o][j] = (Qstar/q_j) mod p_o
   std::vector<uint2> pre(n_in);
@@ -509,8 +510,7 @@ extern "C" int fhe_bconv(fhe_ctx *c, const uint32_t *in, const int *in_idx, int 
   g.n_in = n_in;
   g.n_out = n_out;
   g.Btc = dB;
-  g.kpad = (4 * n_in + 15) / 16 * 16;
-  g.npad = (4 * n_out + 15) / 16 * 16;
+  g.npad = tc_npad(n_out);
   if (rc == FHE_OK) {
     cudaError_t e = c->bconv_mode == FHE_BCONV_TC ? launch_bconv_tc(c->tabs, ba, n_in, n_out, s)
                                                   : launch_bconv(c->tabs, ba, n_in, n_out, s);

@@ -162,8 +162,7 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
       g.n_in = hi - lo;
       g.n_out = n_ext - (hi - lo);
       g.Btc = c->modup_Btc[(size_t)(level - 1) * c->dnum + j];
-      g.kpad = (4 * g.n_in + 15) / 16 * 16;
-      g.npad = (4 * g.n_out + 15) / 16 * 16;
+      g.npad = tc_npad(g.n_out);
       bc.groups.push_back(g);
       bc.max_in = std::max(bc.max_in, g.n_in);
       bc.max_out = std::max(bc.max_out, g.n_out);
@@ -233,8 +232,7 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
       g.n_in = K;
       g.n_out = level;
       g.Btc = c->d_md_Btc;
-      g.kpad = (4 * K + 15) / 16 * 16;
-      g.npad = (4 * level + 15) / 16 * 16;
+      g.npad = tc_npad(level);
       mbc.groups.push_back(g);
       mbc.max_in = std::max(mbc.max_in, K);
       mbc.max_out = std::max(mbc.max_out, level);
@@ -286,7 +284,7 @@ static cudaError_t launch_stage(fhe_ctx *c, const Stage &st, const SegList &sl, 
   switch (st.kind) {
     case Stage::NTT: return launch_ntt_pass(c->tabs, st.column, st.fwd, st.pro, st.epi, sl, q);
     case Stage::EW: return launch_ew(c->tabs, st.ewop, sl, q);
-    case Stage::IP: return launch_ip(c->tabs, sl, st.gather_own, st.gather_ext, q);
+    case Stage::IP: return launch_ip(c->tabs, sl, st.gather_own, st.gather_ext, c->dnum, q);
     case Stage::BCONV:
       return c->bconv_mode == FHE_BCONV_TC ? launch_bconv_tc(c->tabs, ba, st.max_in, st.max_out, q)
                                            : launch_bconv(c->tabs, ba, st.max_in, st.max_out, q);
