@@ -85,13 +85,15 @@ struct KsArgs {
   const uint32_t *ext;   // [beta][n_ext][N] ModUp outputs (NTT form); own-digit limbs unused
   const uint32_t *own;   // [level][N] the key-switched polynomial in NTT form (own-digit limbs)
   const uint32_t *key;   // [dnum][2][L+K][N]
-  const uint32_t *addp;  // [2][level][N] polynomial added after ModDown (c = 0, 1), or null
+  const uint32_t *addp;  // [2][level][N] pass-through polynomial (c = 0, 1) of the output, or null; the
+                         // inner product adds P * addp to u's q-limbs, so ModDown's (u - r) P^-1 carries it
   const uint2 *pinv;     // [L] Shoup pairs of P^-1 mod q_i
+  const uint2 *pmod;     // [L] Shoup pairs of P mod q_i
   int level, n_ext, beta, alpha, L, K;
   uint32_t galois_own;   // sigma applied when reading `own` (1 = none)
   uint32_t galois_ext;   // sigma applied when reading `ext` (hoisted rotations; 1 = none)
   uint32_t galois_add;   // sigma applied when reading `addp` (1 = none)
-  int add_c1;            // also add addp's second polynomial to c = 1 (HMult); rotation adds c0 only
+  int add_c1;            // addp's second polynomial also goes to c = 1 (HMult); a rotation adds c0 only
 };
 
 constexpr int kMaxInlineItems = 4;

@@ -201,7 +201,7 @@ static int build_tables(fhe_ctx *c) {
 
   // ModDown: pre-factor (P/p_k)^-1 mod p_k (with / without N^-1), table [P/p_k]_{q_i},
   // P^-1 mod q_i.
-  std::vector<uint2> md_scale(K), md_phinv(K), pinv(L);
+  std::vector<uint2> md_scale(K), md_phinv(K), pinv(L), pmod(L);
   std::vector<uint32_t> mdT((size_t)L * K);
   std::vector<int2> mdmap(L);
   for (int k = 0; k < K; k++) {
@@ -218,6 +218,7 @@ static int build_tables(fhe_ctx *c) {
     uint32_t P = 1;
     for (int m = 0; m < K; m++) P = h_mul(P, pr[L + m] % q, q);
     pinv[i] = h_pair(h_inv(P, q), q);
+    pmod[i] = h_pair(P, q);
     for (int k = 0; k < K; k++) {
       uint32_t prod = 1;
       for (int m = 0; m < K; m++)
@@ -229,6 +230,7 @@ static int build_tables(fhe_ctx *c) {
   CUDA_OR_FAIL(upload(&c->d_md_scale, md_scale));
   CUDA_OR_FAIL(upload(&c->d_md_phinv, md_phinv));
   CUDA_OR_FAIL(upload(&c->d_pinv, pinv));
+  CUDA_OR_FAIL(upload(&c->d_pmod, pmod));
   CUDA_OR_FAIL(upload(&c->d_mdT, mdT));
   CUDA_OR_FAIL(upload(&c->d_mdmap, mdmap));
   if (K <= fhe::kTcMaxIn)
@@ -320,6 +322,7 @@ fhe_ctx::~fhe_ctx() {
   cudaFree(d_md_scale);
   cudaFree(d_md_phinv);
   cudaFree(d_pinv);
+  cudaFree(d_pmod);
   cudaFree(d_mdT);
   cudaFree(d_mdmap);
   cudaFree(d_rs_qinv);

@@ -31,7 +31,8 @@ struct fhe_ctx {
   uint2 *d_pinv = nullptr;                             // [L] P^-1 mod q_i
   uint32_t *d_mdT = nullptr;                           // [L][K] (P/p_k) mod q_i
   int2 *d_mdmap = nullptr;                             // [L] (i, i)
-  uint16_t *d_md_Btc = nullptr;                        // tensor-core table of the ModDown conversion
+  uint16_t *d_md_Btc = nullptr;
+  uint2 *d_pmod = nullptr;                             // [L] Shoup pairs of P mod q_i                        // tensor-core table of the ModDown conversion
   unsigned int *d_status = nullptr;                    // device status word (expired waits)
   uint2 *d_rs_qinv = nullptr;                          // [L][L]
   std::vector<void *> scratch_tabs;                    // tables built for fhe_bconv calls

@@ -16,7 +16,7 @@ enum : int {
   EW_GATHER = 0,   // dst = src[sigma(j)]               (galois = seg.galois)
   EW_SCALE = 1,    // dst = src * scale[l]
   EW_IP = 2,       // (k_ip) both halves of the key inner product
-  EW_COMBINE = 3,  // dst = (src - src2) P^-1 (+ add)  (src = u, src2 = NTT(r))
+  EW_COMBINE = 3,  // dst = (src - src2) P^-1  (src = u, src2 = NTT(r))
   EW_ADD = 4,      // dst = src + src2
   EW_MUL = 5,      // dst = src * src2
   EW_COPY = 6,     // dst = src
@@ -80,15 +80,8 @@ __global__ void __launch_bounds__(kEwThreads) k_ew(const __grid_constant__ SegLi
       else if (OP == EW_ADD) o[e] = add_mod(av[e], bv[e], q);
       else if (OP == EW_MUL) o[e] = mul_mod(av[e], bv[e], P);
       else if (OP == EW_COPY) o[e] = av[e];
-      else {  // EW_COMBINE
-        uint32_t r = shoup(av[e] + q - bv[e], sc.x, sc.y, q);
-        const int t = sg.t0 + within;
-        if (ks.addp && (sg.c == 0 || ks.add_c1)) {
-          const uint32_t ja = ks.galois_add == 1u ? j0 + e : galois_src(j0 + e, ks.galois_add, logn);
-          r = add_mod(r, __ldg(ks.addp + ((size_t)sg.c * ks.level + t) * N + ja), q);
-        }
-        o[e] = r;
-      }
+      else  // EW_COMBINE (u carries P times the pass-through term)
+        o[e] = shoup(av[e] + q - bv[e], sc.x, sc.y, q);
     }
   }
   *reinterpret_cast<uint4 *>(dst + j0) = make_uint4(o[0], o[1], o[2], o[3]);
@@ -146,11 +139,25 @@ __global__ void __launch_bounds__(kEwThreads) k_ip(const __grid_constant__ SegLi
       a1[i] += (uint64_t)e4[i] * k1[i];
     }
   }
+  uint32_t r0[4], r1[4];
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    r0[i] = reduce_u64(a0[i], P);
+    r1[i] = reduce_u64(a1[i], P);
+  }
+  if (ks.addp && t < ks.level) {  // pass-through term: u_c += P * addp_c (c = 0; c = 1 for HMult)
+    const uint2 pm = ks.pmod[t];
+    const uint32_t *ap = ks.addp + (size_t)t * N;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      const uint32_t ja = ks.galois_add == 1u ? j0 + i : galois_src(j0 + i, ks.galois_add, logn);
+      r0[i] = add_mod(r0[i], shoup(__ldg(ap + ja), pm.x, pm.y, P.q), P.q);
+      if (ks.add_c1) r1[i] = add_mod(r1[i], shoup(__ldg(ap + (size_t)ks.level * N + ja), pm.x, pm.y, P.q), P.q);
+    }
+  }
   uint32_t *d0 = sg.dst + (size_t)within * N + j0, *d1 = d0 + (size_t)ks.n_ext * N;
-  *reinterpret_cast<uint4 *>(d0) = make_uint4(reduce_u64(a0[0], P), reduce_u64(a0[1], P), reduce_u64(a0[2], P),
-                                              reduce_u64(a0[3], P));
-  *reinterpret_cast<uint4 *>(d1) = make_uint4(reduce_u64(a1[0], P), reduce_u64(a1[1], P), reduce_u64(a1[2], P),
-                                              reduce_u64(a1[3], P));
+  *reinterpret_cast<uint4 *>(d0) = make_uint4(r0[0], r0[1], r0[2], r0[3]);
+  *reinterpret_cast<uint4 *>(d1) = make_uint4(r1[0], r1[1], r1[2], r1[3]);
 }
 
 // Stage 2 as a persistent streaming kernel (the ext limbs are read in order).
@@ -170,9 +177,11 @@ constexpr int kIpThreads = 256;
 struct IpUnit {            // one unit, as the consumers need it
   uint32_t *d0;            // u_0 at this unit's first coefficient; u_1 = d0 + d1_off
   const uint32_t *gsrc;    // own limb read through the automorphism (nullptr: none)
+  const uint32_t *add0;    // pass-through limb added (times P) to u_0, or nullptr; add1 = add0 + add1_off
   PrimeC P;
-  uint32_t d1_off, galois, j0;
-  int beta, gjd;
+  uint2 pm;                // P mod the unit's prime (Shoup pair)
+  uint32_t d1_off, galois, j0, galois_add, add1_off;
+  int beta, gjd, add1;
 };
 
 template <bool GOWN>
@@ -205,6 +214,12 @@ __global__ void __launch_bounds__(kIpThreads, 2) k_ip_bulk(const __grid_constant
     d.gsrc = d.gjd >= 0 ? ks.own + (size_t)t * N : nullptr;
     d.galois = ks.galois_own;
     d.j0 = (uint32_t)c0;
+    const bool add = ks.addp && t < ks.level;
+    d.add0 = add ? ks.addp + (size_t)t * N : nullptr;
+    d.add1 = add && ks.add_c1;
+    d.add1_off = (uint32_t)((size_t)ks.level * N);
+    d.galois_add = ks.galois_add;
+    d.pm = add ? ks.pmod[t] : make_uint2(0, 0);
     desc[st] = d;
     const size_t kstride = (size_t)2 * (ks.L + ks.K) * N, half = (size_t)(ks.L + ks.K) * N;
     const uint32_t copies = 3u * (uint32_t)ks.beta - (d.gjd >= 0 ? 1u : 0u);
@@ -237,21 +252,37 @@ __global__ void __launch_bounds__(kIpThreads, 2) k_ip_bulk(const __grid_constant
     return make_uint4(__ldg(d.gsrc + galois_src(j, d.galois, logn)), __ldg(d.gsrc + galois_src(j + 1, d.galois, logn)),
                       __ldg(d.gsrc + galois_src(j + 2, d.galois, logn)), __ldg(d.gsrc + galois_src(j + 3, d.galois, logn)));
   };
-  uint4 gnext = make_uint4(0, 0, 0, 0);
-  if (GOWN && (int)blockIdx.x < total && desc[0].gjd >= 0) gnext = gather(desc[0]);
+  // pass-through values of a unit (read through sigma_{galois_add}), also one unit ahead
+  auto pass = [&](const IpUnit &d, uint4 &p0, uint4 &p1) {
+    const uint32_t j = d.j0 + tid * 4;
+    if (d.galois_add == 1u) {
+      p0 = __ldg(reinterpret_cast<const uint4 *>(d.add0 + j));
+      if (d.add1) p1 = __ldg(reinterpret_cast<const uint4 *>(d.add0 + d.add1_off + j));
+    } else {
+      p0 = make_uint4(__ldg(d.add0 + galois_src(j, d.galois_add, logn)), __ldg(d.add0 + galois_src(j + 1, d.galois_add, logn)),
+                      __ldg(d.add0 + galois_src(j + 2, d.galois_add, logn)),
+                      __ldg(d.add0 + galois_src(j + 3, d.galois_add, logn)));
+    }
+  };
+  uint4 gnext = make_uint4(0, 0, 0, 0), pnext0 = make_uint4(0, 0, 0, 0), pnext1 = make_uint4(0, 0, 0, 0);
+  if ((int)blockIdx.x < total) {
+    if (GOWN && desc[0].gjd >= 0) gnext = gather(desc[0]);
+    if (desc[0].add0) pass(desc[0], pnext0, pnext1);
+  }
   bool ok = true;
   int k = 0;
   for (int u = blockIdx.x; u < total; u += gridDim.x, k++) {
     const int st = k % stages;
     const IpUnit d = desc[st];
-    const uint4 gv = gnext;
+    const uint4 gv = gnext, pv0 = pnext0, pv1 = pnext1;
     if (tid == 0) s_ok = mbar_wait_bounded(&bar[st], (uint32_t)(k / stages) & 1u) ? 1 : 0;
     __syncthreads();
     ok = s_ok != 0;
     if (!ok) break;
-    if (GOWN && u + (int)gridDim.x < total) {  // descriptor of this CTA's next unit, written before this wait
+    if (u + (int)gridDim.x < total) {  // descriptor of this CTA's next unit, written before this wait
       const IpUnit dn = desc[(k + 1) % stages];
-      if (dn.gjd >= 0) gnext = gather(dn);
+      if (GOWN && dn.gjd >= 0) gnext = gather(dn);
+      if (dn.add0) pass(dn, pnext0, pnext1);
     }
     const uint32_t *src = buf + (size_t)st * stage_words + tid * 4;
     uint64_t a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0};
@@ -270,11 +301,24 @@ __global__ void __launch_bounds__(kIpThreads, 2) k_ip_bulk(const __grid_constant
         }
       }
     }
+    uint32_t r0[4], r1[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      r0[i] = reduce_u64(a0[i], d.P);
+      r1[i] = reduce_u64(a1[i], d.P);
+    }
+    if (d.add0) {  // pass-through term: u_c += P * addp_c
+      const uint32_t p0[4] = {pv0.x, pv0.y, pv0.z, pv0.w}, p1[4] = {pv1.x, pv1.y, pv1.z, pv1.w};
+      const uint32_t q = d.P.q;
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        r0[i] = add_mod(r0[i], shoup(p0[i], d.pm.x, d.pm.y, q), q);
+        if (d.add1) r1[i] = add_mod(r1[i], shoup(p1[i], d.pm.x, d.pm.y, q), q);
+      }
+    }
     uint32_t *d0 = d.d0 + tid * 4;
-    *reinterpret_cast<uint4 *>(d0) = make_uint4(reduce_u64(a0[0], d.P), reduce_u64(a0[1], d.P),
-                                                reduce_u64(a0[2], d.P), reduce_u64(a0[3], d.P));
-    *reinterpret_cast<uint4 *>(d0 + d.d1_off) = make_uint4(reduce_u64(a1[0], d.P), reduce_u64(a1[1], d.P),
-                                                           reduce_u64(a1[2], d.P), reduce_u64(a1[3], d.P));
+    *reinterpret_cast<uint4 *>(d0) = make_uint4(r0[0], r0[1], r0[2], r0[3]);
+    *reinterpret_cast<uint4 *>(d0 + d.d1_off) = make_uint4(r1[0], r1[1], r1[2], r1[3]);
     __syncthreads();  // every thread is done with stage st and its descriptor
     if (tid == 0) {
       const int u2 = u + stages * gridDim.x;

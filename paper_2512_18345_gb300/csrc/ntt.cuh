@@ -260,13 +260,8 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt(const __grid_constant__ Seg
       o = shoup(val, scale.x, scale.y, q);
     } else if (EPI == EPI_RESCALE) {
       o = shoup(a[e] + q - red2(val, q), scale.x, scale.y, q);
-    } else {  // EPI_COMBINE: limb t = t0 + within is a q-limb (< level); a = inner product u
-      const int t = sg.t0 + within;
+    } else {  // EPI_COMBINE: a = inner product u (with P times the pass-through term folded in)
       o = shoup(a[e] + q - red2(val, q), pinv.x, pinv.y, q);
-      if (ks.addp && (sg.c == 0 || ks.add_c1)) {
-        const uint32_t ja = ks.galois_add == 1u ? j : galois_src(j, ks.galois_add, LOGN);
-        o = add_mod(o, __ldg(ks.addp + ((size_t)sg.c * ks.level + t) * N + ja), q);
-      }
     }
     x[e] = o;
   }

@@ -70,6 +70,7 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
     k.ext = S.EXT;
     k.key = it.key;
     k.pinv = c->d_pinv;
+    k.pmod = c->d_pmod;
     k.level = it.level;
     k.n_ext = it.level + K;
     k.beta = c->beta(it.level);
