@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the 64-item batch and linear-transform lines")
+    ap.add_argument("--lanes", type=int, default=0, help="concurrent lanes of the batched plans (0: library default)")
+    ap.add_argument("--l2-budget-mb", type=int, default=0,
+                    help="L2 budget that sizes a plan's item groups, in MB (0: library default)")
     ap.add_argument("--profile-run", choices=["scalar", "tc"], default=None,
                     help="only launch the batched stage programs (one lane, no graph) warmup + steps times, "
                          "in a fixed launch order for profilers; prints no JSON line")
@@ -200,6 +203,8 @@ def bench_batch64(binding, inputs, roofline, dev, timed, steps, bconv_mode):
             b = binding.to_device(np.stack([inputs.uniform_residues(g, P.q[:lv], P.N) for _ in range(2)]), dev)
             items.append(dict(op=binding.FHE_OP_RELIN, level=lv, **{"in": a}, in2=b, out=out))
         nbytes += roofline.ks_bytes(P.N, lv, P.K, P.alpha)
+    # schedule: measured by the library's autotuner at the mean level of the mix
+    tune = ctx.autotune(sum(it["level"] for it in items) // len(items), 16)
     plan = ctx.batch_plan(items, binding.FHE_PLAN_GRAPH)
     for _ in range(3):
         plan.launch()
@@ -207,7 +212,7 @@ def bench_batch64(binding, inputs, roofline, dev, timed, steps, bconv_mode):
     ms = timed(plan.launch, k)
     ctx.sync()
     res = {"value": 64 * k / (ms / 1e3), "unit": "key-switches/s", "ms_per_batch": ms / k, "items": 64,
-           "groups": plan.groups, "graph_kernels": plan.kernel_count, "bytes_per_batch_model": nbytes,
+           "autotune": tune, "groups": plan.groups, "graph_kernels": plan.kernel_count, "bytes_per_batch_model": nbytes,
            "distinct_rotation_keys": len(seen)}
     plan.close()
     ctx.close()
@@ -371,8 +376,17 @@ def main():
             ms = float(t.item())
         return ms
 
-    # --- batched fused pipeline in one CUDA graph, CUDA-core base conversion (comparison)
+    # --- schedule of the batched plans: the library's autotuner (measured on this GPU
+    # for this batch, tensor-core BConv kept), unless fixed on the command line
     ctx.set_fused(True)
+    tune = None
+    if args.lanes or args.l2_budget_mb:
+        ctx.set_batch(args.l2_budget_mb << 20, 0, args.lanes)
+    else:
+        ctx.set_bconv(binding.FHE_BCONV_TC)
+        tune = ctx.autotune(level, B)
+    budget = tune["l2_budget_bytes"] if tune else args.l2_budget_mb << 20
+    # --- batched fused pipeline in one CUDA graph, CUDA-core base conversion (comparison)
     ctx.set_bconv(binding.FHE_BCONV_SCALAR)
     plan_sc = ctx.batch_plan(items, binding.FHE_PLAN_GRAPH)
     for _ in range(max(3, args.warmup)):
@@ -420,9 +434,9 @@ def main():
     # --- per-kernel times (CUDA events around each launch on its stream): the same batched
     # stage programs as the headline, launched directly on one lane (no concurrent lane
     # inflates a kernel's event interval)
-    ctx.set_batch(0, 0, 1)
+    ctx.set_batch(budget, 0, 1)
     plan_direct = ctx.batch_plan(items, 0)
-    ctx.set_batch(0, 0, 0)
+    ctx.set_batch(budget, 0, tune["lanes"] if tune else args.lanes)
     for _ in range(3):
         plan_direct.launch()
     ctx.trace(True)
@@ -513,7 +527,8 @@ def main():
             "paths": {"graph_batched_tc_bconv": value, "graph_batched_scalar_bconv": graph_scalar_ks,
                       "direct_batched_tc_bconv": batched_direct_ks, "direct_fused_single_scalar": fused_ks,
                       "plain_per_kernel_single_scalar": plain_ks},
-            "batch_groups": head_groups, "lanes": 2, "traced_groups_one_lane": groups,
+            "batch_groups": head_groups, "lanes": tune["lanes"] if tune else (args.lanes or 2),
+            "autotune": tune, "traced_groups_one_lane": groups,
             "other_workloads": extra,
             "kernels": {k: {"launches": v[0], "ms": v[1], "share": v[1] / total_ms} for k, v in
                         sorted(stats.items(), key=lambda kv: -kv[1][1])},

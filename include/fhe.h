@@ -239,13 +239,38 @@ FHE_API int fhe_plan_kernel_count(const fhe_plan *plan);
 FHE_API int fhe_plan_groups(const fhe_plan *plan, int *sizes, int max);
 /*
  * Group sizing of later plans: the stage-1 working sets (beta(l)(l+K) limbs per
- * item) of the groups resident at once stay within l2_budget_bytes (0: 3/4 of
+ * item) of the groups resident at once stay within l2_budget_bytes (0: twice
  * the device's L2), a group holds at most max_group items (0: 8), and groups
  * run round-robin on `lanes` concurrent streams (0: 2), each lane with its own
  * workspace, so that one group's DRAM-bound inner product overlaps another
- * group's transforms.  The autotuner sets these.
+ * group's transforms.  fhe_autotune measures and sets these.
  */
 FHE_API int fhe_ctx_set_batch(fhe_ctx *ctx, size_t l2_budget_bytes, int max_group, int lanes);
+
+/*
+ * Schedule autotuner (Section IV-A batching, Section IV-C graphs): measures
+ * graph-captured plans of n_items (1..64) synthetic key switches at `level`
+ * on `stream` for every candidate schedule -- lanes 1..4 and group budgets of
+ * 3/4, 1, 2 and 4 times the device's L2 (and, with FHE_TUNE_BCONV, both BConv
+ * kernels) -- applies the fastest to the context (fhe_ctx_set_batch and, with
+ * FHE_TUNE_BCONV, fhe_ctx_set_bconv) and describes it in *out.  Allocates and
+ * frees its own buffers; without a relinearisation key it installs a filler
+ * key for the run and removes it.  Synchronizes the device.  FHE_EINVAL while
+ * `stream` is capturing; FHE_ETIMEOUT if a bounded device wait expired (the
+ * context's settings are then left as they were).
+ */
+#define FHE_TUNE_BCONV 1 /* also choose between the CUDA-core and tensor-core BConv */
+typedef struct {
+  int lanes;              /* chosen lane count */
+  size_t l2_budget_bytes; /* chosen group budget */
+  int max_group;          /* chosen group cap (0: default) */
+  int bconv_mode;         /* chosen BConv kernel */
+  int n_groups;           /* groups of the measured plan */
+  double us_per_ks;       /* measured time per key switch of the chosen schedule, microseconds */
+  double default_us_per_ks; /* the same for the default schedule (2 lanes, 2 x L2), 0 if not measured */
+  int candidates;         /* distinct schedules measured */
+} fhe_tune_result;
+FHE_API int fhe_autotune(fhe_ctx *ctx, int level, int n_items, int flags, fhe_tune_result *out, fhe_stream stream);
 
 /*
  * Kernel tracing (measurement support): while enabled, every kernel the

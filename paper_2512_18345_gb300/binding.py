@@ -23,6 +23,7 @@ FHE_RELIN_KEY = -(2 ** 31)
 FHE_BCONV_SCALAR, FHE_BCONV_TC = 0, 1
 FHE_OP_KS, FHE_OP_ROTATE, FHE_OP_RELIN = 0, 1, 2
 FHE_PLAN_GRAPH = 1
+FHE_TUNE_BCONV = 1
 
 # every entry point declared in include/fhe.h
 EXPORTS = (
@@ -31,7 +32,7 @@ EXPORTS = (
     "fhe_rotate_hoisted", "fhe_linear_transform", "fhe_pmult", "fhe_add", "fhe_ntt", "fhe_intt", "fhe_modup", "fhe_moddown",
     "fhe_bconv", "fhe_batch_plan", "fhe_batch_launch", "fhe_plan_destroy", "fhe_plan_kernel_count",
     "fhe_plan_groups", "fhe_ctx_set_batch",
-    "fhe_trace_enable", "fhe_trace_read", "fhe_probe_bandwidth", "fhe_bconv_noalloc", "fhe_last_error",
+    "fhe_trace_enable", "fhe_trace_read", "fhe_probe_bandwidth", "fhe_autotune", "fhe_bconv_noalloc", "fhe_last_error",
 )
 
 
@@ -51,6 +52,12 @@ class FheInfo(ctypes.Structure):
 
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int), ("total_ms", ctypes.c_double)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("lanes", ctypes.c_int), ("l2_budget_bytes", ctypes.c_size_t), ("max_group", ctypes.c_int),
+                ("bconv_mode", ctypes.c_int), ("n_groups", ctypes.c_int), ("us_per_ks", ctypes.c_double),
+                ("default_us_per_ks", ctypes.c_double), ("candidates", ctypes.c_int)]
 
 
 class KsItem(ctypes.Structure):
@@ -108,6 +115,7 @@ def lib() -> ctypes.CDLL:
         "fhe_plan_kernel_count": [vp],
         "fhe_plan_groups": [vp, ip, ctypes.c_int],
         "fhe_ctx_set_batch": [vp, ctypes.c_size_t, ctypes.c_int, ctypes.c_int],
+        "fhe_autotune": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(TuneResult), vp],
         "fhe_trace_enable": [vp, ctypes.c_int],
         "fhe_probe_bandwidth": [ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
@@ -250,6 +258,12 @@ class Context:
 
     def set_batch(self, l2_budget_bytes: int = 0, max_group: int = 0, lanes: int = 0) -> None:
         check(lib().fhe_ctx_set_batch(self.h, l2_budget_bytes, max_group, lanes))
+
+    def autotune(self, level: int, n_items: int, flags: int = 0, stream=None) -> dict:
+        """Measure the batched-plan schedules on the device and keep the fastest."""
+        r = TuneResult()
+        check(lib().fhe_autotune(self.h, level, n_items, flags, ctypes.byref(r), _stream(stream)))
+        return {f: getattr(r, f) for f, _ in TuneResult._fields_}
 
     def set_fused(self, fused: bool) -> None:
         check(lib().fhe_ctx_set_fused(self.h, int(bool(fused))))

@@ -1,0 +1,162 @@
+// Schedule autotuner for batched plans (the batching / CUDA-graph row of the
+// hot path; Section IV-A multi-polynomial caching, Section IV-C graphs).
+//
+// The paper sizes its batches by the L2 capacity; on GB300 the stage kernels
+// are bound by the integer pipes rather than by L2 traffic, so larger groups
+// that amortise each launch's ramp can win even when their working set spills
+// from L2, and concurrent lanes overlap one group's DRAM-bound inner product
+// with another group's transforms.  fhe_autotune measures the candidates on
+// the device -- real graph plans of synthetic key switches at the caller's
+// level and batch size -- and keeps the fastest.  Timing does not depend on
+// the residues or the key, so the inputs are filler residues below 2^20 (valid
+// for every prime of a context) and, when no relinearisation key is set, a
+// temporary filler key is installed for the run and removed afterwards.
+#include <algorithm>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "../../include/fhe.h"
+#include "ctx.h"
+#include "internal.h"
+
+namespace {
+__global__ void k_fill(uint32_t *p, size_t n, uint32_t seed) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    uint32_t x = (uint32_t)i * 2654435761u ^ seed;
+    x ^= x >> 15;
+    x *= 0x2C1B3C6Du;
+    x ^= x >> 12;
+    p[i] = x & 0xFFFFFu;
+  }
+}
+}  // namespace
+
+extern "C" int fhe_autotune(fhe_ctx *c, int level, int n_items, int flags, fhe_tune_result *out,
+                            fhe_stream stream) {
+  if (!c || !out) return fhe_fail(FHE_EINVAL, "fhe_autotune: null argument");
+  if (level < 1 || level > c->L) return fhe_fail(FHE_ELEVEL, "fhe_autotune: level %d", level);
+  if (n_items < 1 || n_items > 64) return fhe_fail(FHE_EINVAL, "fhe_autotune: n_items %d (1..64)", n_items);
+  if (flags & ~FHE_TUNE_BCONV) return fhe_fail(FHE_EINVAL, "fhe_autotune: flags %d", flags);
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+    return fhe_fail(FHE_EINVAL, "fhe_autotune: stream is capturing");
+  const size_t N = c->N, poly = (size_t)level * N;
+  uint32_t *ins = nullptr, *outs = nullptr, *tmp_key = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const size_t key_words = (size_t)c->dnum * 2 * (c->L + c->K) * N;
+  auto release = [&]() {
+    cudaFree(ins);
+    cudaFree(outs);
+    if (tmp_key) {
+      cudaFree(tmp_key);
+      c->relin_key = nullptr;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (cudaMalloc(&ins, 4 * poly * n_items) != cudaSuccess || cudaMalloc(&outs, 8 * poly * n_items) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    release();
+    return fhe_fail(FHE_ENOMEM, "fhe_autotune: buffers");
+  }
+  k_fill<<<1024, 256, 0, s>>>(ins, poly * n_items, 0x9E3779B9u);
+  if (!c->relin_key) {
+    if (cudaMalloc(&tmp_key, 4 * key_words) != cudaSuccess) {
+      release();
+      return fhe_fail(FHE_ENOMEM, "fhe_autotune: filler key");
+    }
+    k_fill<<<1024, 256, 0, s>>>(tmp_key, key_words, 0x85EBCA6Bu);
+    c->relin_key = tmp_key;
+  }
+  std::vector<fhe_ks_item> items(n_items);
+  for (int i = 0; i < n_items; i++) {
+    fhe_ks_item &it = items[i];
+    memset(&it, 0, sizeof it);
+    it.op = FHE_OP_KS;
+    it.level = level;
+    it.rot = FHE_RELIN_KEY;
+    it.in = ins + poly * i;
+    it.out = outs + 2 * poly * i;
+  }
+
+  int l2 = 0;
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device);
+  const size_t saved_budget = c->batch_budget;
+  const int saved_group = c->batch_max_group, saved_lanes = c->batch_lanes, saved_mode = c->bconv_mode;
+  std::vector<int> modes{c->bconv_mode};
+  if (flags & FHE_TUNE_BCONV) {
+    modes = {FHE_BCONV_SCALAR};
+    if (fhe_ctx_set_bconv(c, FHE_BCONV_TC) == FHE_OK) modes.push_back(FHE_BCONV_TC);
+    c->bconv_mode = saved_mode;
+  }
+  const size_t budgets[] = {(size_t)l2 * 3 / 4, (size_t)l2, (size_t)l2 * 2, (size_t)l2 * 4};
+  std::map<std::tuple<int, int, std::vector<int>>, double> seen;  // (mode, lanes, group sizes) -> us per KS
+  fhe_tune_result best;
+  memset(&best, 0, sizeof best);
+  best.us_per_ks = 1e30;
+  int rc = FHE_OK, tried = 0;
+  for (int mode : modes)
+    for (int lanes = 1; lanes <= 4 && rc == FHE_OK; lanes++)
+      for (size_t budget : budgets) {
+        c->bconv_mode = mode;
+        c->batch_budget = budget;
+        c->batch_lanes = lanes;
+        c->batch_max_group = 0;
+        fhe_plan *p = nullptr;
+        rc = fhe_batch_plan(c, items.data(), n_items, FHE_PLAN_GRAPH, &p);
+        if (rc != FHE_OK) break;
+        std::vector<int> gs(64);
+        const int ng = fhe_plan_groups(p, gs.data(), 64);
+        gs.resize(std::min(ng, 64));
+        const int eff_lanes = std::min(lanes, ng);
+        const bool is_default = mode == saved_mode && lanes == 2 && budget == budgets[2];
+        const auto key = std::make_tuple(mode, eff_lanes, gs);
+        auto found = seen.find(key);
+        if (found != seen.end()) {  // the same schedule as one already measured
+          if (is_default) best.default_us_per_ks = found->second;
+          fhe_plan_destroy(p);
+          continue;
+        }
+        const int reps = 5;
+        for (int w = 0; w < 2 && rc == FHE_OK; w++) rc = fhe_batch_launch(p, stream);
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && rc == FHE_OK; r++) rc = fhe_batch_launch(p, stream);
+        cudaEventRecord(e1, s);
+        float ms = 0.f;
+        if (rc == FHE_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+          rc = fhe_fail(FHE_ECUDA, "fhe_autotune: timing");
+        fhe_plan_destroy(p);
+        if (rc != FHE_OK) break;
+        tried++;
+        const double us = 1e3 * ms / (reps * n_items);
+        seen[key] = us;
+        if (is_default) best.default_us_per_ks = us;
+        if (us < best.us_per_ks) {
+          best.us_per_ks = us;
+          best.lanes = lanes;
+          best.l2_budget_bytes = budget;
+          best.max_group = 0;
+          best.bconv_mode = mode;
+          best.n_groups = ng;
+        }
+      }
+  if (rc == FHE_OK) rc = fhe_ctx_sync(c);  // an expired bounded device wait voids the timings
+  if (rc == FHE_OK && tried > 0) {
+    best.candidates = tried;
+    c->batch_budget = best.l2_budget_bytes;
+    c->batch_lanes = best.lanes;
+    c->batch_max_group = best.max_group;
+    c->bconv_mode = best.bconv_mode;
+    *out = best;
+  } else {
+    c->batch_budget = saved_budget;
+    c->batch_lanes = saved_lanes;
+    c->batch_max_group = saved_group;
+    c->bconv_mode = saved_mode;
+  }
+  release();
+  return rc;
+}

@@ -98,12 +98,14 @@ extern "C" int fhe_batch_plan(fhe_ctx *c, const fhe_ks_item *items, int n, int f
   p->ctx = c;
   p->items.assign(items, items + n);
   p->flags = flags;
-  // group items so that each group's stage-1 working set stays within the L2 budget
+  // group items so that the stage-1 working sets of the groups in flight stay within
+  // the budget (default: twice the L2 -- the stage kernels are bound by the integer
+  // pipes, and larger launches amortise their ramp more than L2 residency saves)
   size_t budget = c->batch_budget;
   if (!budget) {
     int l2 = 0;
     cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device);
-    budget = (size_t)l2 * 3 / 4;
+    budget = (size_t)l2 * 2;
   }
   const int max_group = c->batch_max_group > 0 ? c->batch_max_group : 8;
   const int nl = std::max(1, c->batch_lanes);
