@@ -115,6 +115,14 @@ FHE_API int fhe_ctx_set_bconv(fhe_ctx *ctx, int mode);
  * tensor cores expired since the last call; its outputs are then invalid.
  */
 FHE_API int fhe_ctx_sync(fhe_ctx *ctx);
+/*
+ * Failure-detection self-test (no counterpart in the paper): enqueues one CTA
+ * that waits, with the library's bounded wait and a short limit, on a barrier
+ * nothing arrives on; the expiry is recorded in the context's status word as a
+ * production kernel records it, so the next fhe_ctx_sync returns FHE_ETIMEOUT
+ * (and clears it).  No fault, trap or unbounded wait is involved.
+ */
+FHE_API int fhe_selftest_wait_timeout(fhe_ctx *ctx, fhe_stream stream);
 /* Fuse stage epilogues (1, default) or run the plain per-kernel pipeline (0).  Same bits. */
 FHE_API int fhe_ctx_set_fused(fhe_ctx *ctx, int fused);
 
@@ -275,7 +283,8 @@ FHE_API int fhe_autotune(fhe_ctx *ctx, int level, int n_items, int flags, fhe_tu
 /*
  * Kernel tracing (measurement support): while enabled, every kernel the
  * context launches outside a captured plan is bracketed by two CUDA events on
- * its stream.  fhe_trace_read synchronizes the device, returns per-kernel-name
+ * its stream, and the auxiliary branch of complementary pipelining runs on the
+ * main stream, so that each interval holds its kernel alone.  fhe_trace_read synchronizes the device, returns per-kernel-name
  * launch counts and summed event times (at most `max` entries, *n = number of
  * distinct names) and clears the record.
  */

@@ -32,7 +32,7 @@ EXPORTS = (
     "fhe_rotate_hoisted", "fhe_linear_transform", "fhe_pmult", "fhe_add", "fhe_ntt", "fhe_intt", "fhe_modup", "fhe_moddown",
     "fhe_bconv", "fhe_batch_plan", "fhe_batch_launch", "fhe_plan_destroy", "fhe_plan_kernel_count",
     "fhe_plan_groups", "fhe_ctx_set_batch",
-    "fhe_trace_enable", "fhe_trace_read", "fhe_probe_bandwidth", "fhe_autotune", "fhe_bconv_noalloc", "fhe_last_error",
+    "fhe_trace_enable", "fhe_trace_read", "fhe_probe_bandwidth", "fhe_autotune", "fhe_selftest_wait_timeout", "fhe_bconv_noalloc", "fhe_last_error",
 )
 
 
@@ -115,6 +115,7 @@ def lib() -> ctypes.CDLL:
         "fhe_plan_kernel_count": [vp],
         "fhe_plan_groups": [vp, ip, ctypes.c_int],
         "fhe_ctx_set_batch": [vp, ctypes.c_size_t, ctypes.c_int, ctypes.c_int],
+        "fhe_selftest_wait_timeout": [vp, vp],
         "fhe_autotune": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(TuneResult), vp],
         "fhe_trace_enable": [vp, ctypes.c_int],
         "fhe_probe_bandwidth": [ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -258,6 +259,10 @@ class Context:
 
     def set_batch(self, l2_budget_bytes: int = 0, max_group: int = 0, lanes: int = 0) -> None:
         check(lib().fhe_ctx_set_batch(self.h, l2_budget_bytes, max_group, lanes))
+
+    def selftest_wait_timeout(self, stream=None) -> None:
+        """Enqueue a bounded wait that expires; the next sync reports FHE_ETIMEOUT."""
+        check(lib().fhe_selftest_wait_timeout(self.h, _stream(stream)))
 
     def autotune(self, level: int, n_items: int, flags: int = 0, stream=None) -> dict:
         """Measure the batched-plan schedules on the device and keep the fastest."""

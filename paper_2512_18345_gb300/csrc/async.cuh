@@ -26,8 +26,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
 }
 
 // bounded wait for the completion of `phase`: false when the limit expired
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase) {
-  for (uint32_t it = 0; it < (1u << 20); it++) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase, uint32_t limit = 1u << 20) {
+  for (uint32_t it = 0; it < limit; it++) {
     if (mbar_try_wait(bar, phase)) return true;
     __nanosleep(32);
   }

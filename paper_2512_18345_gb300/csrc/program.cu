@@ -281,7 +281,12 @@ static cudaError_t launch_stage(fhe_ctx *c, const Stage &st, const SegList &sl, 
   cudaStream_t aux = lane > 0 ? c->lanes[lane].aux : c->aux;
   cudaEvent_t ev_fork = lane > 0 ? c->lanes[lane].fork : c->ev_fork;
   cudaEvent_t ev_join = lane > 0 ? c->lanes[lane].join : c->ev_join;
-  cudaStream_t q = st.aux ? aux : s;
+  // while tracing, the auxiliary branch runs on the main stream, so that every
+  // kernel's event interval holds that kernel alone
+  const bool serial = c->tabs.tracer != nullptr;
+  cudaStream_t q = st.aux && !serial ? aux : s;
+  if (serial && (st.kind == Stage::FORK || st.kind == Stage::JOIN_RECORD || st.kind == Stage::JOIN_WAIT))
+    return cudaSuccess;
   switch (st.kind) {
     case Stage::NTT: return launch_ntt_pass(c->tabs, st.column, st.fwd, st.pro, st.epi, sl, q);
     case Stage::EW: return launch_ew(c->tabs, st.ewop, sl, q);
