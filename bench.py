@@ -51,6 +51,28 @@ def parse():
     return ap.parse_args()
 
 
+def rank_seed(base_seed: int, rank: int) -> int:
+    """Seed of a rank's batch: every rank key-switches its own inputs (the key
+    switches are independent; weak scaling, no data-path collective)."""
+    return base_seed + 1000 * rank
+
+
+def max_over_ranks(ms: float, ws: int, device=None) -> float:
+    """The slowest rank's time: the job ends when its last rank does."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, ws: int, ms: float) -> float:
+    """Whole-job rate: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * ws / (ms / 1e3)
+
+
 def dist_setup(args):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -341,7 +363,7 @@ def main():
     torch.cuda.set_device(dev)
     P = inputs.workload_params(WORKLOAD)
     level, B = P.L, args.batch
-    g = inputs.rng(inputs.WORKLOADS[WORKLOAD]["seed"] + 1000 * rank)
+    g = inputs.rng(rank_seed(inputs.WORKLOADS[WORKLOAD]["seed"], rank))
     ctx = binding.Context.from_params(P, device=dev)
     cts_np, keys_np, rots = [], [], []
     used = set()
@@ -390,13 +412,7 @@ def main():
         if ws > 1:
             import torch.distributed as dist
             dist.barrier()
-        ms = e0.elapsed_time(e1)
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms], device=f"cuda:{dev}")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(e0.elapsed_time(e1), ws, f"cuda:{dev}")
 
     # --- schedule of the batched plans: the library's autotuner (measured on this GPU
     # for this batch, tensor-core BConv kept), unless fixed on the command line
@@ -429,8 +445,7 @@ def main():
     ms = timed(plan.launch, args.steps)
     clk = clocks.stop()
     ctx.sync()
-    ks_total = B * args.steps * ws
-    value = ks_total / (ms / 1e3)
+    value = job_throughput(B * args.steps, ws, ms)
     graph_kernels = plan.kernel_count
 
     # --- comparison paths on the same inputs (fewer steps)
