@@ -51,6 +51,16 @@ __host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
   return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// 32 lanes x 16 columns of 32-bit words from tensor memory (one value per column per thread)
+__device__ __forceinline__ void tmem_ld16(uint32_t *r, uint32_t addr) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(addr));
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -66,7 +76,7 @@ struct TcOut {  // per output prime of the current group, read by whole warps (b
 // input pairs into A, thread 0 issues the MMAs and commits to the mbarrier
 // (phase = tile parity), all wait (bounded), then each warp reads its lane
 // quarter for half of the outputs and writes the reduced results.
-__global__ void __launch_bounds__(kTcThreads) k_bconv_tc(const __grid_constant__ BconvArgs a, const PrimeC *pc,
+__global__ void __launch_bounds__(kTcThreads, 4) k_bconv_tc(const __grid_constant__ BconvArgs a, const PrimeC *pc,
                                                          int logn, unsigned int *status, int npad_max,
                                                          int tiles_per_group) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -122,6 +132,8 @@ __global__ void __launch_bounds__(kTcThreads) k_bconv_tc(const __grid_constant__
   };
   uint4 y = make_uint4(0, 0, 0, 0);
   bool prefetched = false;  // y holds the current tile's inputs
+  bool big_primes = true;   // the current group's output primes all exceed 2^30
+  uint32_t *gout = nullptr; // the current group's output base
   for (int tile = t0; tile < t1 && ok; tile++) {
     const int grp = tile / tiles_per_group;
     const size_t n0 = (size_t)(tile % tiles_per_group) * kTcM;
@@ -135,6 +147,7 @@ __global__ void __launch_bounds__(kTcThreads) k_bconv_tc(const __grid_constant__
       uint4 *dst = reinterpret_cast<uint4 *>(sB);
       const int n16 = npad * (int)kRowBytes / 16;
       for (int i = tid; i < n16; i += kTcThreads) dst[i] = __ldg(src + i);
+      bool big = true;  // every output prime above 2^30: one conditional subtraction suffices
       for (int o = tid; o < n_out; o += kTcThreads) {
         const int2 m = gp->omap[o];
         const PrimeC p = pc[m.y];
@@ -144,7 +157,10 @@ __global__ void __launch_bounds__(kTcThreads) k_bconv_tc(const __grid_constant__
         t.div32 = p.div32;
         t.off = (uint32_t)m.x << logn;
         sO[o] = t;
+        big = big && p.q > (1u << 30);
       }
+      big_primes = __syncthreads_and(big ? 1 : 0) != 0;
+      gout = gp->out;
     }
     // A: row r = coefficient n0 + r; chunk kc holds inputs 2 kc, 2 kc + 1 as the f16
     // values 1024 + byte (byte permutes against 0x64006400), absent inputs as 1024.
@@ -194,32 +210,31 @@ __global__ void __launch_bounds__(kTcThreads) k_bconv_tc(const __grid_constant__
     phase ^= 1u;
     tc_fence_after();
     if (ok) {
-      // epilogue: warp w reads lanes 32 (w % 4).. = coefficients n0 + 32 (w % 4) + lane, and
-      // the 4-output chunks c with c % 2 == w / 4; columns 4 o + b hold 2^23 + S_b[o]
+      // epilogue: warp w reads lanes 32 (w % 4).. = coefficients n0 + 32 (w % 4) + lane; warps
+      // w < 4 take outputs [0, H), the others [H, n_out) (H a multiple of 4), eight outputs
+      // (two 16-column loads, one wait) at a time; columns 4 o + b hold 2^23 + S_b[o]
       const int q4 = warp & 3;
       const uint32_t n = (uint32_t)(n0 + (size_t)q4 * 32 + (tid & 31));
       const uint32_t tbase = taddr + ((uint32_t)(q4 * 32) << 16);
-      for (int o0 = 4 * (warp >> 2); o0 < n_out; o0 += 8) {
-        uint32_t rr[16];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-            "%15}, [%16];"
-            : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]), "=r"(rr[7]),
-              "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]), "=r"(rr[14]),
-              "=r"(rr[15])
-            : "r"(tbase + (uint32_t)(4 * o0)));
+      const int H = ((n_out + 1) / 2 + 3) & ~3;
+      const int o_end = (warp >> 2) ? n_out : min(H, n_out);
+      for (int o0 = (warp >> 2) ? H : 0; o0 < o_end; o0 += 8) {
+        uint32_t rr[32];
+        tmem_ld16(rr, tbase + (uint32_t)(4 * o0));
+        if (o0 + 4 < o_end) tmem_ld16(rr + 16, tbase + (uint32_t)(4 * (o0 + 4)));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int cnt = min(8, o_end - o0);
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
-          const int o = o0 + i;
-          if (o >= n_out) break;
-          const TcOut t = sO[o];
-          // lo, hi < 2^30; the 0x4B000000 of each accumulator cancels modulo 2^32
-          const uint32_t lo = rr[4 * i + 1] * 256u + rr[4 * i] - 0x4B000000u;
-          const uint32_t hi = rr[4 * i + 3] * 256u + rr[4 * i + 2] - 0x4B000000u;
-          const uint32_t s = lo + red2(shoup_lazy(hi, 65536u, t.w16s, t.q), t.q);  // < 2^30 + q
-          const uint32_t v = t.q > (1u << 30) ? red2(s, t.q) : red2(shoup_lazy(s, 1u, t.div32, t.q), t.q);
-          gp->out[t.off + n] = v;
+        for (int i = 0; i < 8; i++) {
+          if (i < cnt) {
+            const TcOut t = sO[o0 + i];
+            // lo, hi < 2^30; the 0x4B000000 of each accumulator cancels modulo 2^32
+            const uint32_t lo = rr[4 * i + 1] * 256u + rr[4 * i] - 0x4B000000u;
+            const uint32_t hi = rr[4 * i + 3] * 256u + rr[4 * i + 2] - 0x4B000000u;
+            const uint32_t sum = lo + red2(shoup_lazy(hi, 65536u, t.w16s, t.q), t.q);  // < 2^30 + q
+            const uint32_t v = big_primes ? red2(sum, t.q) : red2(shoup_lazy(sum, 1u, t.div32, t.q), t.q);
+            gout[t.off + n] = v;
+          }
         }
       }
     } else {
