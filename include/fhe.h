@@ -258,9 +258,11 @@ FHE_API int fhe_ctx_set_batch(fhe_ctx *ctx, size_t l2_budget_bytes, int max_grou
 /*
  * Schedule autotuner (Section IV-A batching, Section IV-C graphs): measures
  * graph-captured plans of n_items (1..64) synthetic key switches at `level`
- * on `stream` for every candidate schedule -- lanes 1..4 and group budgets of
- * 3/4, 1, 2 and 4 times the device's L2 (and, with FHE_TUNE_BCONV, both BConv
- * kernels) -- applies the fastest to the context (fhe_ctx_set_batch and, with
+ * on `stream` for every candidate schedule -- lanes 1..4, group budgets of
+ * 3/4, 1, 2 and 4 times the device's L2, one or two resident CTAs per SM for
+ * the streaming inner product (one leaves room for transforms beside it) and,
+ * with FHE_TUNE_BCONV, both BConv kernels -- applies the fastest to the
+ * context (fhe_ctx_set_batch, the inner product's residency and, with
  * FHE_TUNE_BCONV, fhe_ctx_set_bconv) and describes it in *out.  Allocates and
  * frees its own buffers; without a relinearisation key it installs a filler
  * key for the run and removes it.  Synchronizes the device.  FHE_EINVAL while
@@ -275,8 +277,9 @@ typedef struct {
   int bconv_mode;         /* chosen BConv kernel */
   int n_groups;           /* groups of the measured plan */
   double us_per_ks;       /* measured time per key switch of the chosen schedule, microseconds */
-  double default_us_per_ks; /* the same for the default schedule (2 lanes, 2 x L2), 0 if not measured */
+  double default_us_per_ks; /* the same for the default schedule (2 lanes, 2 x L2, 2 CTAs), 0 if not measured */
   int candidates;         /* distinct schedules measured */
+  int ip_ctas_per_sm;     /* chosen residency of the streaming inner product */
 } fhe_tune_result;
 FHE_API int fhe_autotune(fhe_ctx *ctx, int level, int n_items, int flags, fhe_tune_result *out, fhe_stream stream);
 

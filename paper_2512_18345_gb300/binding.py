@@ -57,7 +57,8 @@ class KernelStat(ctypes.Structure):
 class TuneResult(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_int), ("l2_budget_bytes", ctypes.c_size_t), ("max_group", ctypes.c_int),
                 ("bconv_mode", ctypes.c_int), ("n_groups", ctypes.c_int), ("us_per_ks", ctypes.c_double),
-                ("default_us_per_ks", ctypes.c_double), ("candidates", ctypes.c_int)]
+                ("default_us_per_ks", ctypes.c_double), ("candidates", ctypes.c_int),
+                ("ip_ctas_per_sm", ctypes.c_int)]
 
 
 class KsItem(ctypes.Structure):

@@ -98,9 +98,12 @@ extern "C" int fhe_autotune(fhe_ctx *c, int level, int n_items, int flags, fhe_t
   memset(&best, 0, sizeof best);
   best.us_per_ks = 1e30;
   int rc = FHE_OK, tried = 0;
+  const int saved_ip = c->tabs.ip_ctas_per_sm;
   for (int mode : modes)
+    for (int ipc = 1; ipc <= 2; ipc++)
     for (int lanes = 1; lanes <= 4 && rc == FHE_OK; lanes++)
       for (size_t budget : budgets) {
+        c->tabs.ip_ctas_per_sm = ipc;
         c->bconv_mode = mode;
         c->batch_budget = budget;
         c->batch_lanes = lanes;
@@ -112,8 +115,8 @@ extern "C" int fhe_autotune(fhe_ctx *c, int level, int n_items, int flags, fhe_t
         const int ng = fhe_plan_groups(p, gs.data(), 64);
         gs.resize(std::min(ng, 64));
         const int eff_lanes = std::min(lanes, ng);
-        const bool is_default = mode == saved_mode && lanes == 2 && budget == budgets[2];
-        const auto key = std::make_tuple(mode, eff_lanes, gs);
+        const bool is_default = mode == saved_mode && ipc == 2 && lanes == 2 && budget == budgets[2];
+        const auto key = std::make_tuple(mode * 4 + ipc, eff_lanes, gs);
         auto found = seen.find(key);
         if (found != seen.end()) {  // the same schedule as one already measured
           if (is_default) best.default_us_per_ks = found->second;
@@ -141,6 +144,7 @@ extern "C" int fhe_autotune(fhe_ctx *c, int level, int n_items, int flags, fhe_t
           best.max_group = 0;
           best.bconv_mode = mode;
           best.n_groups = ng;
+          best.ip_ctas_per_sm = ipc;
         }
       }
   if (rc == FHE_OK) rc = fhe_ctx_sync(c);  // an expired bounded device wait voids the timings
@@ -150,8 +154,10 @@ extern "C" int fhe_autotune(fhe_ctx *c, int level, int n_items, int flags, fhe_t
     c->batch_lanes = best.lanes;
     c->batch_max_group = best.max_group;
     c->bconv_mode = best.bconv_mode;
+    c->tabs.ip_ctas_per_sm = best.ip_ctas_per_sm;
     *out = best;
   } else {
+    c->tabs.ip_ctas_per_sm = saved_ip;
     c->batch_budget = saved_budget;
     c->batch_lanes = saved_lanes;
     c->batch_max_group = saved_group;

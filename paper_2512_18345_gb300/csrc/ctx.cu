@@ -253,6 +253,7 @@ static int build_tables(fhe_ctx *c) {
   c->tabs.pc = c->d_pc;
   c->tabs.logn = c->logn;
   c->tabs.tracer = nullptr;
+  c->tabs.ip_ctas_per_sm = 2;
   c->tabs.status = c->d_status;
   return FHE_OK;
 }

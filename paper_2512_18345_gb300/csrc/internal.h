@@ -34,6 +34,7 @@ struct DevTables {
   int logn;
   Tracer *tracer;          // null: no tracing
   unsigned int *status;    // device word: bit 0 set when a bounded device-side wait expired
+  int ip_ctas_per_sm;      // resident CTAs per SM of the streaming inner product (1 or 2; autotuned)
 };
 
 // bracket one launch with trace events when tracing is on

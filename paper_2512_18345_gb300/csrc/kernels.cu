@@ -128,7 +128,8 @@ cudaError_t launch_ip(const DevTables &t, const SegList &sl, bool gather_own, bo
   TraceScope ts(t, "inner_product", s);
   const bool go = gather_own, ge = gather_ext;
   if (!ge && beta_max >= 1 && beta_max <= 4 && (1 << t.logn) % kIpChunk == 0) {
-    // streaming kernel: two CTAs per SM, as many stages as fit half an SM's shared memory
+    // streaming kernel: as many stages as fit half an SM's shared memory; one or two CTAs per
+    // SM (one leaves half of every SM to the transforms running beside it)
     const int stage_bytes = 3 * beta_max * kIpChunk * 4;
     const int per_stage = stage_bytes + 8 + (int)sizeof(IpUnit);
     const int stages = std::min(8, (113 * 1024 - 256) / per_stage);
@@ -144,7 +145,7 @@ cudaError_t launch_ip(const DevTables &t, const SegList &sl, bool gather_own, bo
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int units = sl.total * ((1 << t.logn) / kIpChunk);
-    const unsigned grid = (unsigned)std::min(units, 2 * sms);
+    const unsigned grid = (unsigned)std::min(units, std::max(1, std::min(2, t.ip_ctas_per_sm)) * sms);
     if (go) k_ip_bulk<true><<<grid, kIpThreads, smem, s>>>(sl, t.pc, t.logn, t.status, beta_max, stages);
     else k_ip_bulk<false><<<grid, kIpThreads, smem, s>>>(sl, t.pc, t.logn, t.status, beta_max, stages);
     g_launches++;
