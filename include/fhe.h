@@ -219,11 +219,13 @@ FHE_API int fhe_bconv(fhe_ctx *ctx, const uint32_t *in, const int *in_idx, int n
 /*
  * Batched key switching (Section IV-A multi-polynomial caching and batching,
  * Section IV-C CUDA Graphs): a plan holds a list of independent operations
- * at uneven levels; fhe_batch_plan validates them, sizes the item groups so
- * each group's working set stays in L2, and captures the whole batch into
- * one CUDA graph; fhe_batch_launch replays it on `stream`.  Every item's
- * result is bit-identical to the same operation run alone.  The buffers
- * named by the items must stay valid while the plan is used.
+ * at uneven levels (at least one); fhe_batch_plan validates them (levels, keys, buffers
+ * non-null and 16-byte aligned: FHE_EINVAL; an output overlapping its item's
+ * input: FHE_EALIAS), sizes the item groups (fhe_ctx_set_batch,
+ * fhe_autotune) and captures the whole batch into one CUDA graph;
+ * fhe_batch_launch replays it on `stream`.  Every item's result is
+ * bit-identical to the same operation run alone.  The buffers named by the
+ * items must stay valid while the plan is used.
  */
 #define FHE_OP_KS 0     /* out = KS(in) with key_id = rot (FHE_RELIN_KEY or a rotation index) */
 #define FHE_OP_ROTATE 1 /* out = HRotate(in, rot) */
@@ -282,6 +284,16 @@ typedef struct {
   int ip_ctas_per_sm;     /* chosen residency of the streaming inner product */
 } fhe_tune_result;
 FHE_API int fhe_autotune(fhe_ctx *ctx, int level, int n_items, int flags, fhe_tune_result *out, fhe_stream stream);
+/*
+ * fhe_autotune with a cache file at `path` (a text file, one line per entry):
+ * an entry for this context's (N, level, K, alpha, dnum), n_items, flags and
+ * GPU (name and SM count) is applied without measuring (out->candidates = 0);
+ * otherwise the schedules are measured as by fhe_autotune and the choice is
+ * appended to the file.  Malformed lines are skipped; the last matching entry
+ * wins.  FHE_EINVAL if the file cannot be appended to.
+ */
+FHE_API int fhe_autotune_cached(fhe_ctx *ctx, const char *path, int level, int n_items, int flags,
+                                fhe_tune_result *out, fhe_stream stream);
 
 /*
  * Kernel tracing (measurement support): while enabled, every kernel the

@@ -32,7 +32,7 @@ EXPORTS = (
     "fhe_rotate_hoisted", "fhe_linear_transform", "fhe_pmult", "fhe_add", "fhe_ntt", "fhe_intt", "fhe_modup", "fhe_moddown",
     "fhe_bconv", "fhe_batch_plan", "fhe_batch_launch", "fhe_plan_destroy", "fhe_plan_kernel_count",
     "fhe_plan_groups", "fhe_ctx_set_batch",
-    "fhe_trace_enable", "fhe_trace_read", "fhe_probe_bandwidth", "fhe_autotune", "fhe_selftest_wait_timeout", "fhe_bconv_noalloc", "fhe_last_error",
+    "fhe_trace_enable", "fhe_trace_read", "fhe_probe_bandwidth", "fhe_autotune", "fhe_autotune_cached", "fhe_selftest_wait_timeout", "fhe_bconv_noalloc", "fhe_last_error",
 )
 
 
@@ -118,6 +118,8 @@ def lib() -> ctypes.CDLL:
         "fhe_ctx_set_batch": [vp, ctypes.c_size_t, ctypes.c_int, ctypes.c_int],
         "fhe_selftest_wait_timeout": [vp, vp],
         "fhe_autotune": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(TuneResult), vp],
+        "fhe_autotune_cached": [vp, ctypes.c_char_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                ctypes.POINTER(TuneResult), vp],
         "fhe_trace_enable": [vp, ctypes.c_int],
         "fhe_probe_bandwidth": [ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
@@ -265,10 +267,15 @@ class Context:
         """Enqueue a bounded wait that expires; the next sync reports FHE_ETIMEOUT."""
         check(lib().fhe_selftest_wait_timeout(self.h, _stream(stream)))
 
-    def autotune(self, level: int, n_items: int, flags: int = 0, stream=None) -> dict:
-        """Measure the batched-plan schedules on the device and keep the fastest."""
+    def autotune(self, level: int, n_items: int, flags: int = 0, stream=None, cache: Optional[str] = None) -> dict:
+        """Measure the batched-plan schedules on the device and keep the fastest
+        (with `cache`: reuse or record the choice in that file)."""
         r = TuneResult()
-        check(lib().fhe_autotune(self.h, level, n_items, flags, ctypes.byref(r), _stream(stream)))
+        if cache:
+            check(lib().fhe_autotune_cached(self.h, os.fsencode(cache), level, n_items, flags, ctypes.byref(r),
+                                            _stream(stream)))
+        else:
+            check(lib().fhe_autotune(self.h, level, n_items, flags, ctypes.byref(r), _stream(stream)))
         return {f: getattr(r, f) for f, _ in TuneResult._fields_}
 
     def set_fused(self, fused: bool) -> None:

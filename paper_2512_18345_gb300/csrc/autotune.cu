@@ -12,7 +12,10 @@
 // for every prime of a context) and, when no relinearisation key is set, a
 // temporary filler key is installed for the run and removed afterwards.
 #include <algorithm>
+#include <cstdio>
+#include <cstring>
 #include <map>
+#include <string>
 #include <tuple>
 #include <vector>
 
@@ -165,4 +168,80 @@ extern "C" int fhe_autotune(fhe_ctx *c, int level, int n_items, int flags, fhe_t
   }
   release();
   return rc;
+}
+
+// ---- tuning cache: one text line per (ring, level, special primes, digit size, batch,
+// flags, GPU) -> chosen schedule; the last matching line wins, unreadable lines are skipped.
+
+static std::string tune_key(const fhe_ctx *c, int level, int n_items, int flags) {
+  cudaDeviceProp prop;
+  memset(&prop, 0, sizeof prop);
+  cudaGetDeviceProperties(&prop, c->device);
+  std::string gpu(prop.name);
+  for (char &ch : gpu)
+    if (ch == ' ' || ch == '|') ch = '_';
+  char buf[384];
+  snprintf(buf, sizeof buf, "N=%zu level=%d K=%d alpha=%d dnum=%d items=%d flags=%d gpu=%s sms=%d", (size_t)c->N,
+           level, c->K, c->alpha, c->dnum, n_items, flags, gpu.c_str(), prop.multiProcessorCount);
+  return buf;
+}
+
+static bool tune_parse(const char *rest, fhe_tune_result *r) {
+  fhe_tune_result t;
+  memset(&t, 0, sizeof t);
+  unsigned long long budget = 0;
+  if (sscanf(rest, " lanes=%d budget=%llu group=%d bconv=%d ip=%d us=%lf", &t.lanes, &budget, &t.max_group,
+             &t.bconv_mode, &t.ip_ctas_per_sm, &t.us_per_ks) != 6)
+    return false;
+  if (t.lanes < 1 || t.lanes > 4 || t.ip_ctas_per_sm < 1 || t.ip_ctas_per_sm > 2 ||
+      (t.bconv_mode != FHE_BCONV_SCALAR && t.bconv_mode != FHE_BCONV_TC) || t.max_group < 0)
+    return false;
+  t.l2_budget_bytes = (size_t)budget;
+  *r = t;
+  return true;
+}
+
+extern "C" int fhe_autotune_cached(fhe_ctx *c, const char *path, int level, int n_items, int flags,
+                                   fhe_tune_result *out, fhe_stream stream) {
+  if (!c || !out || !path || !*path) return fhe_fail(FHE_EINVAL, "fhe_autotune_cached: null argument");
+  if (level < 1 || level > c->L) return fhe_fail(FHE_ELEVEL, "fhe_autotune_cached: level %d", level);
+  const std::string key = tune_key(c, level, n_items, flags);
+  fhe_tune_result hit;
+  bool found = false;
+  if (FILE *f = fopen(path, "r")) {
+    char line[1024];
+    while (fgets(line, sizeof line, f)) {
+      const char *bar = strchr(line, '|');
+      if (!bar || (size_t)(bar - line) != key.size() + 1 || strncmp(line, key.c_str(), key.size()) != 0) continue;
+      fhe_tune_result r;
+      if (tune_parse(bar + 1, &r)) {
+        hit = r;
+        found = true;
+      }
+    }
+    fclose(f);
+  }
+  if (found) {
+    if (hit.bconv_mode == FHE_BCONV_TC && fhe_ctx_set_bconv(c, FHE_BCONV_TC) != FHE_OK)
+      hit.bconv_mode = c->bconv_mode;  // not available on this context: keep its kernel
+    c->batch_budget = hit.l2_budget_bytes;
+    c->batch_lanes = hit.lanes;
+    c->batch_max_group = hit.max_group;
+    c->bconv_mode = hit.bconv_mode;
+    c->tabs.ip_ctas_per_sm = hit.ip_ctas_per_sm;
+    hit.candidates = 0;  // served from the cache
+    *out = hit;
+    return FHE_OK;
+  }
+  int rc = fhe_autotune(c, level, n_items, flags, out, stream);
+  if (rc != FHE_OK) return rc;
+  char line[1024];
+  const int len = snprintf(line, sizeof line, "%s | lanes=%d budget=%llu group=%d bconv=%d ip=%d us=%.3f\n",
+                           key.c_str(), out->lanes, (unsigned long long)out->l2_budget_bytes, out->max_group,
+                           out->bconv_mode, out->ip_ctas_per_sm, out->us_per_ks);
+  FILE *f = fopen(path, "a");
+  if (!f) return fhe_fail(FHE_EINVAL, "fhe_autotune_cached: cannot append to %s", path);
+  const bool ok = fwrite(line, 1, (size_t)len, f) == (size_t)len;  // one write per entry
+  fclose(f);
+  return ok ? FHE_OK : fhe_fail(FHE_EINVAL, "fhe_autotune_cached: write to %s failed", path);
 }

@@ -8,6 +8,7 @@
 // and captures all groups into one CUDA graph.  Launching the plan replays
 // the graph on the caller's stream with one host call.
 #include <algorithm>
+#include <cstdint>
 #include <cstring>
 #include <vector>
 
@@ -80,7 +81,7 @@ extern "C" int fhe_ctx_set_batch(fhe_ctx *c, size_t l2_budget_bytes, int max_gro
 }
 
 extern "C" int fhe_batch_plan(fhe_ctx *c, const fhe_ks_item *items, int n, int flags, fhe_plan **out) {
-  if (!c || !out || n < 0 || (n > 0 && !items)) return fhe_fail(FHE_EINVAL, "fhe_batch_plan: bad arguments");
+  if (!c || !out || n < 1 || !items) return fhe_fail(FHE_EINVAL, "fhe_batch_plan: bad arguments (n >= 1 items)");
   *out = nullptr;
   const size_t N = c->N;
   for (int i = 0; i < n; i++) {
@@ -88,6 +89,19 @@ extern "C" int fhe_batch_plan(fhe_ctx *c, const fhe_ks_item *items, int n, int f
     if (it.level < 1 || it.level > c->L) return fhe_fail(FHE_ELEVEL, "fhe_batch_plan: item %d level %d", i, it.level);
     if (!it.in || !it.out || (it.op == FHE_OP_RELIN && !it.in2))
       return fhe_fail(FHE_EINVAL, "fhe_batch_plan: item %d has a null buffer", i);
+    // the stage kernels move 16-byte vectors and bulk copies through these buffers
+    if (((uintptr_t)it.in | (uintptr_t)it.out | (uintptr_t)(it.in2 ? it.in2 : it.in)) & 15)
+      return fhe_fail(FHE_EINVAL, "fhe_batch_plan: item %d has a buffer that is not 16-byte aligned", i);
+    {
+      const size_t poly = (size_t)it.level * c->N * 4;
+      const size_t in_bytes = it.op == FHE_OP_KS ? poly : 2 * poly;
+      auto overlap = [](const void *a, size_t na, const void *b, size_t nb) {
+        const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+        return x < y + nb && y < x + na;
+      };
+      if (overlap(it.out, 2 * poly, it.in, in_bytes) || (it.in2 && overlap(it.out, 2 * poly, it.in2, 2 * poly)))
+        return fhe_fail(FHE_EALIAS, "fhe_batch_plan: item %d output overlaps its input", i);
+    }
     if (it.op < FHE_OP_KS || it.op > FHE_OP_RELIN) return fhe_fail(FHE_EINVAL, "fhe_batch_plan: item %d op %d", i, it.op);
     if (it.op == FHE_OP_RELIN && !c->relin_key) return fhe_fail(FHE_ENOKEY, "fhe_batch_plan: no relinearisation key");
     if ((it.op == FHE_OP_ROTATE && fhe_galois_elt(it.rot, c->N) != 1u) || it.op == FHE_OP_KS)

@@ -84,3 +84,27 @@ def test_autotune_rejects_bad_arguments(fhe_lib, level, n_items, flags, code):
         ctx.autotune(level, n_items, flags)
     assert err.value.code == getattr(binding, code)
     ctx.close()
+
+
+def test_autotune_cache_records_then_serves(fhe_lib, tmp_path):
+    from paper_2512_18345_gb300 import binding
+    P = inputs.workload_params("hmult_relin_rescale_N4096_L4")
+    path = tmp_path / "tune.txt"
+    ctx = binding.Context.from_params(P)
+    r1 = ctx.autotune(P.L, 4, cache=str(path))
+    assert r1["candidates"] >= 2
+    lines = path.read_text().splitlines()
+    assert len(lines) == 1 and "items=4" in lines[0] and f"N={P.N}" in lines[0]
+    ctx.close()
+    ctx2 = binding.Context.from_params(P)
+    r2 = ctx2.autotune(P.L, 4, cache=str(path))
+    assert r2["candidates"] == 0  # served from the file, nothing measured
+    for k in ("lanes", "l2_budget_bytes", "bconv_mode", "ip_ctas_per_sm"):
+        assert r2[k] == r1[k]
+    with open(path, "a") as f:  # a malformed line and another key leave the lookup alone
+        f.write("not an entry\n")
+        f.write(lines[0].replace("items=4", "items=5") + "\n")
+    assert ctx2.autotune(P.L, 4, cache=str(path))["candidates"] == 0
+    r4 = ctx2.autotune(P.L, 3, cache=str(path))  # a new batch size is measured and recorded
+    assert r4["candidates"] >= 2 and len(path.read_text().splitlines()) == 4
+    ctx2.close()
