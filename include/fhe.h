@@ -262,7 +262,8 @@ FHE_API int fhe_ctx_set_batch(fhe_ctx *ctx, size_t l2_budget_bytes, int max_grou
  * graph-captured plans of n_items (1..64) synthetic key switches at `level`
  * on `stream` for every candidate schedule -- lanes 1..4, group budgets of
  * 3/4, 1, 2 and 4 times the device's L2, one or two resident CTAs per SM for
- * the streaming inner product (one leaves room for transforms beside it) and,
+ * the streaming inner product (one leaves room for transforms beside it; it is
+ * chosen only when more than 2 % faster than the best two-CTA schedule) and,
  * with FHE_TUNE_BCONV, both BConv kernels -- applies the fastest to the
  * context (fhe_ctx_set_batch, the inner product's residency and, with
  * FHE_TUNE_BCONV, fhe_ctx_set_bconv) and describes it in *out.  Allocates and

@@ -69,3 +69,40 @@ def test_batch64_mixed_levels(fhe_lib):
         assert np.array_equal(got[idx], want), idx
     plan.close()
     ctx.close()
+
+
+def test_headline_configuration_full_size(fhe_lib):
+    """The benchmark's step as it is timed: 8 rotations at N = 2^16, L = 24 with
+    distinct keys, tensor-core BConv, the autotuned schedule, one CUDA graph,
+    replayed twice; every output equals the oracle's."""
+    from paper_2512_18345_gb300 import binding
+    name = "hrotate_N65536_L24_tc"
+    P = inputs.workload_params(name)
+    OP = oracle.OracleParams.from_params(P)
+    ctx = binding.Context.from_params(P)
+    ctx.set_bconv(binding.FHE_BCONV_TC)
+    g = inputs.rng(inputs.WORKLOADS[name]["seed"] + 77)
+    items, want, used = [], [], set()
+    while len(items) < 8:
+        r = inputs.rotation_index(g)
+        k = pow(5, r % (P.N // 2), 2 * P.N)
+        if k in used:
+            continue
+        used.add(k)
+        key = np.stack([np.stack([inputs.uniform_residues(g, P.primes, P.N) for _ in range(2)])
+                        for _ in range(P.dnum)])
+        ctx.set_rot_key(r, binding.to_device(key))
+        ct = np.stack([inputs.uniform_residues(g, P.q, P.N) for _ in range(2)])
+        items.append(dict(op=binding.FHE_OP_ROTATE, level=P.L, rot=r, **{"in": binding.to_device(ct)},
+                          out=binding.empty((2, P.L, P.N))))
+        want.append(oracle.rotate(OP, ct, P.L, r, key))
+    tune = ctx.autotune(P.L, len(items))
+    assert tune["bconv_mode"] == binding.FHE_BCONV_TC
+    plan = ctx.batch_plan(items, binding.FHE_PLAN_GRAPH)
+    plan.launch()
+    plan.launch()
+    ctx.sync()
+    for it, w in zip(items, want):
+        assert np.array_equal(binding.to_numpy(it["out"]), w)
+    plan.close()
+    ctx.close()
