@@ -277,6 +277,46 @@ def bench_lt(binding, inputs, dev, timed, bconv_mode):
             "diagonals": baby * giant, "diagonal_bytes": diag_bytes}
 
 
+def bench_paper_shapes(binding, inputs, roofline, dev, timed, steps, l2_gbs, B=8):
+    """The paper's key-switching shapes (alpha = K = 12; (l, beta) = (24, 2), (48, 4)):
+    B rotations with distinct keys per step, autotuned schedule, one CUDA graph,
+    CUDA-core conversion (alpha = 12 exceeds the tensor-core bound)."""
+    import numpy as np
+    res = {}
+    for name in ("paper_ks_N65536_L24_a12", "paper_ks_N65536_L48_a12"):
+        P = inputs.workload_params(name)
+        g = inputs.rng(inputs.WORKLOADS[name]["seed"] + 500)
+        ctx = binding.Context.from_params(P, device=dev)
+        ctx.set_bconv(binding.FHE_BCONV_SCALAR)
+        items, used = [], set()
+        while len(items) < B:
+            r = inputs.rotation_index(g)
+            k = pow(5, r % (P.N // 2), 2 * P.N)
+            if k in used:
+                continue
+            used.add(k)
+            ctx.set_rot_key(r, binding.to_device(rand_key_np(inputs, P, g), dev))
+            ct = binding.to_device(np.stack([inputs.uniform_residues(g, P.q, P.N) for _ in range(2)]), dev)
+            items.append(dict(op=binding.FHE_OP_ROTATE, level=P.L, rot=r, **{"in": ct},
+                              out=binding.empty((2, P.L, P.N), dev)))
+        tune = ctx.autotune(P.L, B)
+        plan = ctx.batch_plan(items, binding.FHE_PLAN_GRAPH)
+        for _ in range(3):
+            plan.launch()
+        k = max(3, min(steps, 30))
+        ms = timed(plan.launch, k)
+        ctx.sync()
+        t_ks = ms / 1e3 / (k * B)
+        bks = roofline.ks_bytes(P.N, P.L, P.K, P.alpha)
+        res[f"l{P.L}_alpha{P.alpha}_beta{P.beta(P.L)}"] = {
+            "value": 1.0 / t_ks, "unit": "key-switches/s", "us_per_ks": t_ks * 1e6, "items": B,
+            "bytes_per_ks_model": bks, "l2_roofline_frac": (bks / (l2_gbs * 1e9)) / t_ks,
+            "groups": plan.groups, "autotune": tune, "bconv": "cuda cores"}
+        plan.close()
+        ctx.close()
+    return res
+
+
 def kernel_model(name, P, level, G):
     """Algorithmic bytes and operations of the stage kernel `name` summed over its
     launches in one batched group of G HRotates at `level` (fused pipeline): each
@@ -544,6 +584,7 @@ def main():
         lt = bench_lt(binding, inputs, dev, timed, binding.FHE_BCONV_TC)
         lt["hbm_floor_ms"] = lt["diagonal_bytes"] / (hbm_peak * 1e9) * 1e3
         extra["bsgs_linear_transform_L24"] = lt
+        extra["paper_shapes"] = bench_paper_shapes(binding, inputs, roofline, dev, timed, args.steps, l2_gbs)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -113,6 +113,9 @@ WORKLOADS: Dict[str, dict] = {
                                   items=64, level_lo=4, level_hi=24),
     "bsgs_lt_N65536_L24": dict(N=1 << 16, L=24, K=8, dnum=3, bits=31, seed=20251223,
                                baby=16, giant=8, scale_bits=31),
+    # the paper's own key-switching shapes (Table "ks-param"): alpha = K = 12
+    "paper_ks_N65536_L24_a12": dict(N=1 << 16, L=24, K=12, dnum=2, bits=31, seed=20251224),
+    "paper_ks_N65536_L48_a12": dict(N=1 << 16, L=48, K=12, dnum=4, bits=31, seed=20251225),
 }
 
 
