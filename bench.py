@@ -351,9 +351,10 @@ def kernel_model(name, P, level, G):
 ALU_PEAK = {"bfly": 16 * 152 * 2.07e9, "mac": 23 * 152 * 2.07e9}
 
 
-def measured_traffic_per_item_launch(name):
-    """DRAM bytes per item and launch of kernel `name` from its committed ncu summary,
-    or None when there is none or the kernel's sources changed since the capture."""
+def measured_traffic_per_item(name):
+    """DRAM bytes per item of kernel `name` (summed over its launches in one group) from
+    its committed ncu summary, or None when there is none or the kernel's sources
+    changed since the capture."""
     import hashlib
     import re
     files = {"inner_product": "inner_product_N65536_L24.md"}
@@ -361,7 +362,7 @@ def measured_traffic_per_item_launch(name):
         return None
     try:
         text = open(os.path.join(ROOT, "profiles", files[name])).read()
-        per_item = int(re.search(r"^traffic_bytes_per_item_launch: (\d+)$", text, re.M).group(1))
+        per_item = int(re.search(r"^traffic_bytes_per_item: (\d+)$", text, re.M).group(1))
         want = re.search(r"^kernel_sources_sha256: ([0-9a-f]+)$", text, re.M).group(1)
         srcs = re.search(r"^kernel_sources: (.+)$", text, re.M).group(1).split()
         h = hashlib.sha256()
@@ -381,8 +382,8 @@ def kernel_roofline(name, launches_per_group, launch_ms, P, level, G, hbm_peak):
     gbs = per_launch_bytes / (launch_ms / 1e3) / 1e9
     ach_ops = per_launch_ops / (launch_ms / 1e3)
     f_hbm, f_alu = gbs / hbm_peak, ach_ops / ALU_PEAK[unit]
-    per_item = measured_traffic_per_item_launch(name)
-    common = {"traffic": per_item * G if per_item else None, "kernel": name, "launch_ms": launch_ms,
+    per_item = measured_traffic_per_item(name)
+    common = {"traffic": per_item * G / lpg if per_item else None, "kernel": name, "launch_ms": launch_ms,
               "algorithmic_bytes_per_launch": per_launch_bytes, "algorithmic_ops_per_launch": per_launch_ops,
               "frac_hbm": f_hbm, "frac_alu": f_alu}
     if f_alu >= f_hbm:

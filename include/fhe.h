@@ -125,6 +125,11 @@ FHE_API int fhe_ctx_sync(fhe_ctx *ctx);
 FHE_API int fhe_selftest_wait_timeout(fhe_ctx *ctx, fhe_stream stream);
 /* Fuse stage epilogues (1, default) or run the plain per-kernel pipeline (0).  Same bits. */
 FHE_API int fhe_ctx_set_fused(fhe_ctx *ctx, int fused);
+/* Complementary pipelining (Section IV-B) in the fused pipeline: with `on`
+ * (the default) the inner product of the ciphertext limbs runs on an
+ * auxiliary branch beside ModDown's special-limb chain; without it, one launch
+ * covers all limbs.  Results are identical either way; fhe_autotune sets it. */
+FHE_API int fhe_ctx_set_pipelining(fhe_ctx *ctx, int on);
 
 /*
  * Switching keys ([dnum][2][L + K][N] uint32, NTT form, host or device
@@ -263,7 +268,8 @@ FHE_API int fhe_ctx_set_batch(fhe_ctx *ctx, size_t l2_budget_bytes, int max_grou
  * on `stream` for every candidate schedule -- lanes 1..4, group budgets of
  * 3/4, 1, 2 and 4 times the device's L2, one or two resident CTAs per SM for
  * the streaming inner product (one leaves room for transforms beside it; it is
- * chosen only when more than 2 % faster than the best two-CTA schedule) and,
+ * chosen only when more than 2 % faster than the best two-CTA schedule),
+ * complementary pipelining (Section IV-B) on or off, and,
  * with FHE_TUNE_BCONV, both BConv kernels -- applies the fastest to the
  * context (fhe_ctx_set_batch, the inner product's residency and, with
  * FHE_TUNE_BCONV, fhe_ctx_set_bconv) and describes it in *out.  Allocates and
@@ -283,6 +289,7 @@ typedef struct {
   double default_us_per_ks; /* the same for the default schedule (2 lanes, 2 x L2, 2 CTAs), 0 if not measured */
   int candidates;         /* distinct schedules measured */
   int ip_ctas_per_sm;     /* chosen residency of the streaming inner product */
+  int comp_pipe;          /* 1: complementary pipelining (q-limb inner product on its own branch) */
 } fhe_tune_result;
 FHE_API int fhe_autotune(fhe_ctx *ctx, int level, int n_items, int flags, fhe_tune_result *out, fhe_stream stream);
 /*

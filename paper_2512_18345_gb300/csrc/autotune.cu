@@ -101,14 +101,16 @@ extern "C" int fhe_autotune(fhe_ctx *c, int level, int n_items, int flags, fhe_t
   memset(&best, 0, sizeof best);
   best.us_per_ks = 1e30;
   int rc = FHE_OK, tried = 0;
-  const int saved_ip = c->tabs.ip_ctas_per_sm;
+  const int saved_ip = c->tabs.ip_ctas_per_sm, saved_comp = c->comp_pipe;
   fhe_tune_result by_ip[2];  // fastest schedule with one / two inner-product CTAs per SM
   memset(by_ip, 0, sizeof by_ip);
   by_ip[0].us_per_ks = by_ip[1].us_per_ks = 1e30;
   for (int mode : modes)
+    for (int comp = 0; comp <= 1; comp++)
     for (int ipc = 1; ipc <= 2; ipc++)
     for (int lanes = 1; lanes <= 4 && rc == FHE_OK; lanes++)
       for (size_t budget : budgets) {
+        c->comp_pipe = comp;
         c->tabs.ip_ctas_per_sm = ipc;
         c->bconv_mode = mode;
         c->batch_budget = budget;
@@ -121,8 +123,8 @@ extern "C" int fhe_autotune(fhe_ctx *c, int level, int n_items, int flags, fhe_t
         const int ng = fhe_plan_groups(p, gs.data(), 64);
         gs.resize(std::min(ng, 64));
         const int eff_lanes = std::min(lanes, ng);
-        const bool is_default = mode == saved_mode && ipc == 2 && lanes == 2 && budget == budgets[2];
-        const auto key = std::make_tuple(mode * 4 + ipc, eff_lanes, gs);
+        const bool is_default = mode == saved_mode && comp == 1 && ipc == 2 && lanes == 2 && budget == budgets[2];
+        const auto key = std::make_tuple(mode * 8 + comp * 4 + ipc, eff_lanes, gs);
         auto found = seen.find(key);
         if (found != seen.end()) {  // the same schedule as one already measured
           if (is_default) best.default_us_per_ks = found->second;
@@ -152,6 +154,7 @@ extern "C" int fhe_autotune(fhe_ctx *c, int level, int n_items, int flags, fhe_t
           b.bconv_mode = mode;
           b.n_groups = ng;
           b.ip_ctas_per_sm = ipc;
+          b.comp_pipe = comp;
         }
       }
   // one resident inner-product CTA per SM only when it beats the best two-CTA schedule by
@@ -169,9 +172,11 @@ extern "C" int fhe_autotune(fhe_ctx *c, int level, int n_items, int flags, fhe_t
     c->batch_max_group = best.max_group;
     c->bconv_mode = best.bconv_mode;
     c->tabs.ip_ctas_per_sm = best.ip_ctas_per_sm;
+    c->comp_pipe = best.comp_pipe;
     *out = best;
   } else {
     c->tabs.ip_ctas_per_sm = saved_ip;
+    c->comp_pipe = saved_comp;
     c->batch_budget = saved_budget;
     c->batch_lanes = saved_lanes;
     c->batch_max_group = saved_group;
@@ -201,9 +206,10 @@ static bool tune_parse(const char *rest, fhe_tune_result *r) {
   fhe_tune_result t;
   memset(&t, 0, sizeof t);
   unsigned long long budget = 0;
-  if (sscanf(rest, " lanes=%d budget=%llu group=%d bconv=%d ip=%d us=%lf", &t.lanes, &budget, &t.max_group,
-             &t.bconv_mode, &t.ip_ctas_per_sm, &t.us_per_ks) != 6)
+  if (sscanf(rest, " lanes=%d budget=%llu group=%d bconv=%d ip=%d comp=%d us=%lf", &t.lanes, &budget, &t.max_group,
+             &t.bconv_mode, &t.ip_ctas_per_sm, &t.comp_pipe, &t.us_per_ks) != 7)
     return false;
+  if (t.comp_pipe != 0 && t.comp_pipe != 1) return false;
   if (t.lanes < 1 || t.lanes > 4 || t.ip_ctas_per_sm < 1 || t.ip_ctas_per_sm > 2 ||
       (t.bconv_mode != FHE_BCONV_SCALAR && t.bconv_mode != FHE_BCONV_TC) || t.max_group < 0)
     return false;
@@ -240,6 +246,7 @@ extern "C" int fhe_autotune_cached(fhe_ctx *c, const char *path, int level, int 
     c->batch_max_group = hit.max_group;
     c->bconv_mode = hit.bconv_mode;
     c->tabs.ip_ctas_per_sm = hit.ip_ctas_per_sm;
+    c->comp_pipe = hit.comp_pipe;
     hit.candidates = 0;  // served from the cache
     *out = hit;
     return FHE_OK;
@@ -247,9 +254,9 @@ extern "C" int fhe_autotune_cached(fhe_ctx *c, const char *path, int level, int 
   int rc = fhe_autotune(c, level, n_items, flags, out, stream);
   if (rc != FHE_OK) return rc;
   char line[1024];
-  const int len = snprintf(line, sizeof line, "%s | lanes=%d budget=%llu group=%d bconv=%d ip=%d us=%.3f\n",
+  const int len = snprintf(line, sizeof line, "%s | lanes=%d budget=%llu group=%d bconv=%d ip=%d comp=%d us=%.3f\n",
                            key.c_str(), out->lanes, (unsigned long long)out->l2_budget_bytes, out->max_group,
-                           out->bconv_mode, out->ip_ctas_per_sm, out->us_per_ks);
+                           out->bconv_mode, out->ip_ctas_per_sm, out->comp_pipe, out->us_per_ks);
   FILE *f = fopen(path, "a");
   if (!f) return fhe_fail(FHE_EINVAL, "fhe_autotune_cached: cannot append to %s", path);
   const bool ok = fwrite(line, 1, (size_t)len, f) == (size_t)len;  // one write per entry

@@ -494,6 +494,12 @@ extern "C" int fhe_ctx_sync(fhe_ctx *c) {
   return FHE_OK;
 }
 
+extern "C" int fhe_ctx_set_pipelining(fhe_ctx *c, int on) {
+  if (!c) return fhe_fail(FHE_EINVAL, "fhe_ctx_set_pipelining: null");
+  c->comp_pipe = on ? 1 : 0;
+  return FHE_OK;
+}
+
 extern "C" int fhe_ctx_set_fused(fhe_ctx *c, int fused) {
   if (!c) return fhe_fail(FHE_EINVAL, "fhe_ctx_set_fused: null");
   c->fused = fused ? 1 : 0;

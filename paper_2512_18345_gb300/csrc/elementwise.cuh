@@ -171,8 +171,39 @@ __global__ void __launch_bounds__(kEwThreads) k_ip(const __grid_constant__ SegLi
 // other threads sleep at the CTA barrier.  The own digit of a rotation
 // (sigma_{galois_own} applied on the fly) is gathered with plain loads issued
 // before the wait.
-constexpr int kIpChunk = 1024;  // coefficients per unit: 4 per thread
+constexpr int kIpChunk = 1024;  // coefficients per unit
 constexpr int kIpThreads = 256;
+constexpr int kIpEpt = kIpChunk / kIpThreads;  // coefficients per thread and unit (2 or 4)
+static_assert(kIpEpt == 2 || kIpEpt == 4, "inner product: 2 or 4 coefficients per thread");
+
+// E consecutive words <-> registers (one 8- or 16-byte access)
+template <int E>
+__device__ __forceinline__ void ld_words(const uint32_t *p, uint32_t (&v)[E]) {
+  if constexpr (E == 4) {
+    const uint4 t = *reinterpret_cast<const uint4 *>(p);
+    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+  } else {
+    const uint2 t = *reinterpret_cast<const uint2 *>(p);
+    v[0] = t.x, v[1] = t.y;
+  }
+}
+template <int E>
+__device__ __forceinline__ void ldg_words(const uint32_t *p, uint32_t (&v)[E]) {
+  if constexpr (E == 4) {
+    const uint4 t = __ldg(reinterpret_cast<const uint4 *>(p));
+    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+  } else {
+    const uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
+    v[0] = t.x, v[1] = t.y;
+  }
+}
+template <int E>
+__device__ __forceinline__ void st_words(uint32_t *p, const uint32_t (&v)[E]) {
+  if constexpr (E == 4)
+    *reinterpret_cast<uint4 *>(p) = make_uint4(v[0], v[1], v[2], v[3]);
+  else
+    *reinterpret_cast<uint2 *>(p) = make_uint2(v[0], v[1]);
+}
 
 struct IpUnit {            // one unit, as the consumers need it
   uint32_t *d0;            // u_0 at this unit's first coefficient; u_1 = d0 + d1_off
@@ -247,26 +278,26 @@ __global__ void __launch_bounds__(kIpThreads, 2) k_ip_bulk(const __grid_constant
 
   // the gathered own values of a unit are loaded one unit ahead (after the wait
   // that orders the unit's descriptor), so their latency overlaps a unit's work
-  auto gather = [&](const IpUnit &d) {
-    const uint32_t j = d.j0 + tid * 4;
-    return make_uint4(__ldg(d.gsrc + galois_src(j, d.galois, logn)), __ldg(d.gsrc + galois_src(j + 1, d.galois, logn)),
-                      __ldg(d.gsrc + galois_src(j + 2, d.galois, logn)), __ldg(d.gsrc + galois_src(j + 3, d.galois, logn)));
+  constexpr int E = kIpEpt;
+  auto gather = [&](const IpUnit &d, uint32_t (&v)[E]) {
+    const uint32_t j = d.j0 + tid * E;
+#pragma unroll
+    for (int e = 0; e < E; e++) v[e] = __ldg(d.gsrc + galois_src(j + e, d.galois, logn));
   };
   // pass-through values of a unit (read through sigma_{galois_add}), also one unit ahead
-  auto pass = [&](const IpUnit &d, uint4 &p0, uint4 &p1) {
-    const uint32_t j = d.j0 + tid * 4;
+  auto pass = [&](const IpUnit &d, uint32_t (&p0)[E], uint32_t (&p1)[E]) {
+    const uint32_t j = d.j0 + tid * E;
     if (d.galois_add == 1u) {
-      p0 = __ldg(reinterpret_cast<const uint4 *>(d.add0 + j));
-      if (d.add1) p1 = __ldg(reinterpret_cast<const uint4 *>(d.add0 + d.add1_off + j));
+      ldg_words<E>(d.add0 + j, p0);
+      if (d.add1) ldg_words<E>(d.add0 + d.add1_off + j, p1);
     } else {
-      p0 = make_uint4(__ldg(d.add0 + galois_src(j, d.galois_add, logn)), __ldg(d.add0 + galois_src(j + 1, d.galois_add, logn)),
-                      __ldg(d.add0 + galois_src(j + 2, d.galois_add, logn)),
-                      __ldg(d.add0 + galois_src(j + 3, d.galois_add, logn)));
+#pragma unroll
+      for (int e = 0; e < E; e++) p0[e] = __ldg(d.add0 + galois_src(j + e, d.galois_add, logn));
     }
   };
-  uint4 gnext = make_uint4(0, 0, 0, 0), pnext0 = make_uint4(0, 0, 0, 0), pnext1 = make_uint4(0, 0, 0, 0);
+  uint32_t gnext[E] = {}, pnext0[E] = {}, pnext1[E] = {};
   if ((int)blockIdx.x < total) {
-    if (GOWN && desc[0].gjd >= 0) gnext = gather(desc[0]);
+    if (GOWN && desc[0].gjd >= 0) gather(desc[0], gnext);
     if (desc[0].add0) pass(desc[0], pnext0, pnext1);
   }
   bool ok = true;
@@ -274,51 +305,56 @@ __global__ void __launch_bounds__(kIpThreads, 2) k_ip_bulk(const __grid_constant
   for (int u = blockIdx.x; u < total; u += gridDim.x, k++) {
     const int st = k % stages;
     const IpUnit d = desc[st];
-    const uint4 gv = gnext, pv0 = pnext0, pv1 = pnext1;
+    uint32_t gv[E], pv0[E], pv1[E];
+#pragma unroll
+    for (int e = 0; e < E; e++) gv[e] = gnext[e], pv0[e] = pnext0[e], pv1[e] = pnext1[e];
     if (tid == 0) s_ok = mbar_wait_bounded(&bar[st], (uint32_t)(k / stages) & 1u) ? 1 : 0;
     __syncthreads();
     ok = s_ok != 0;
     if (!ok) break;
     if (u + (int)gridDim.x < total) {  // descriptor of this CTA's next unit, written before this wait
       const IpUnit dn = desc[(k + 1) % stages];
-      if (GOWN && dn.gjd >= 0) gnext = gather(dn);
+      if (GOWN && dn.gjd >= 0) gather(dn, gnext);
       if (dn.add0) pass(dn, pnext0, pnext1);
     }
-    const uint32_t *src = buf + (size_t)st * stage_words + tid * 4;
-    uint64_t a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0};
+    const uint32_t *src = buf + (size_t)st * stage_words + tid * E;
+    uint64_t a0[E] = {}, a1[E] = {};
 #pragma unroll
     for (int jd = 0; jd < 4; jd++) {
       if (jd < d.beta) {
-        const uint4 ev = jd == d.gjd ? gv : *reinterpret_cast<const uint4 *>(src + (size_t)(3 * jd) * kIpChunk);
-        const uint4 k0 = *reinterpret_cast<const uint4 *>(src + (size_t)(3 * jd + 1) * kIpChunk);
-        const uint4 k1 = *reinterpret_cast<const uint4 *>(src + (size_t)(3 * jd + 2) * kIpChunk);
-        const uint32_t e4[4] = {ev.x, ev.y, ev.z, ev.w}, k04[4] = {k0.x, k0.y, k0.z, k0.w},
-                       k14[4] = {k1.x, k1.y, k1.z, k1.w};
+        uint32_t ev[E], k0[E], k1[E];
+        if (jd == d.gjd) {
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
-          a0[i] += (uint64_t)e4[i] * k04[i];
-          a1[i] += (uint64_t)e4[i] * k14[i];
+          for (int e = 0; e < E; e++) ev[e] = gv[e];
+        } else {
+          ld_words<E>(src + (size_t)(3 * jd) * kIpChunk, ev);
+        }
+        ld_words<E>(src + (size_t)(3 * jd + 1) * kIpChunk, k0);
+        ld_words<E>(src + (size_t)(3 * jd + 2) * kIpChunk, k1);
+#pragma unroll
+        for (int i = 0; i < E; i++) {
+          a0[i] += (uint64_t)ev[i] * k0[i];
+          a1[i] += (uint64_t)ev[i] * k1[i];
         }
       }
     }
-    uint32_t r0[4], r1[4];
+    uint32_t r0[E], r1[E];
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
+    for (int i = 0; i < E; i++) {
       r0[i] = reduce_u64(a0[i], d.P);
       r1[i] = reduce_u64(a1[i], d.P);
     }
     if (d.add0) {  // pass-through term: u_c += P * addp_c
-      const uint32_t p0[4] = {pv0.x, pv0.y, pv0.z, pv0.w}, p1[4] = {pv1.x, pv1.y, pv1.z, pv1.w};
       const uint32_t q = d.P.q;
 #pragma unroll
-      for (int i = 0; i < 4; i++) {
-        r0[i] = add_mod(r0[i], shoup(p0[i], d.pm.x, d.pm.y, q), q);
-        if (d.add1) r1[i] = add_mod(r1[i], shoup(p1[i], d.pm.x, d.pm.y, q), q);
+      for (int i = 0; i < E; i++) {
+        r0[i] = add_mod(r0[i], shoup(pv0[i], d.pm.x, d.pm.y, q), q);
+        if (d.add1) r1[i] = add_mod(r1[i], shoup(pv1[i], d.pm.x, d.pm.y, q), q);
       }
     }
-    uint32_t *d0 = d.d0 + tid * 4;
-    *reinterpret_cast<uint4 *>(d0) = make_uint4(r0[0], r0[1], r0[2], r0[3]);
-    *reinterpret_cast<uint4 *>(d0 + d.d1_off) = make_uint4(r1[0], r1[1], r1[2], r1[3]);
+    uint32_t *d0 = d.d0 + tid * E;
+    st_words<E>(d0, r0);
+    st_words<E>(d0 + d.d1_off, r1);
     __syncthreads();  // every thread is done with stage st and its descriptor
     if (tid == 0) {
       const int u2 = u + stages * gridDim.x;

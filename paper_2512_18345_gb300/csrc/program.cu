@@ -250,8 +250,11 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
   }
   ipp.gather_own = ipq.gather_own;
   ipp.gather_ext = ipq.gather_ext;
+  // complementary pipelining (Section IV-B): the q-limb inner product on an auxiliary
+  // branch beside ModDown's special-limb chain; otherwise one launch over all limbs
+  const bool split = fused && c->comp_pipe;
   if (!ipq.segs.empty()) {
-    if (fused) {
+    if (split) {
       P.stages.push_back(marker(Stage::FORK));
       ipq.aux = true;
       P.stages.push_back(ipq);
@@ -267,7 +270,7 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
     if (!fused) P.stages.push_back(msc);
     P.stages.push_back(mbc);
     P.stages.push_back(r1);
-    if (fused) P.stages.push_back(marker(Stage::JOIN_WAIT));
+    if (split) P.stages.push_back(marker(Stage::JOIN_WAIT));
     P.stages.push_back(r2);
     if (!fused) P.stages.push_back(cb);
   }

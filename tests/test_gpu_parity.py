@@ -251,13 +251,16 @@ def test_batch_plan_equals_single_ops(c1):
     plan.close()
 
 
-@pytest.mark.parametrize("budget,max_group,lanes", [(0, 0, 1), (1, 2, 2), (0, 3, 2), (0, 1, 3)])
-def test_batch_plan_full_size_groups(c2, budget, max_group, lanes):
+@pytest.mark.parametrize("budget,max_group,lanes,pipe", [(0, 0, 1, 1), (1, 2, 2, 1), (0, 3, 2, 0), (0, 1, 3, 0),
+                                                        (0, 0, 2, 0)])
+def test_batch_plan_full_size_groups(c2, budget, max_group, lanes, pipe):
     """Mixed rotations / relinearisations / key switches at uneven levels,
-    N = 2^16, split into groups of various sizes: every item bit-exact."""
+    N = 2^16, split into groups of various sizes, on several lanes, with and
+    without complementary pipelining: every item bit-exact."""
     from paper_2512_18345_gb300 import binding
     P, OP, ctx = c2
     ctx.set_batch(budget, max_group, lanes)
+    ctx.set_pipelining(bool(pipe))
     g = inputs.rng(95 + max_group)
     rk = rand_key(P, g)
     ctx.set_relin_key(dev(rk))
@@ -287,6 +290,7 @@ def test_batch_plan_full_size_groups(c2, budget, max_group, lanes):
         assert np.array_equal(host(it["out"]), w), f"item {i} {specs[i]}"
     plan.close()
     ctx.set_batch(0, 0, 0)
+    ctx.set_pipelining(True)
 
 
 # ------------------------------------------------------------------ CKKS semantics through the GPU path
