@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--lanes", type=int, default=0, help="concurrent lanes of the batched plans (0: library default)")
     ap.add_argument("--l2-budget-mb", type=int, default=0,
                     help="L2 budget that sizes a plan's item groups, in MB (0: library default)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="kernel-utilisation sweep (NTT over 10..250 limbs, BConv over output counts, key-switch "
+                         "batch sizes) as one JSON line instead of the benchmark line")
     ap.add_argument("--profile-run", choices=["scalar", "tc"], default=None,
                     help="only launch the batched stage programs (one lane, no graph) warmup + steps times, "
                          "in a fixed launch order for profilers; prints no JSON line")
@@ -317,6 +320,94 @@ def bench_paper_shapes(binding, inputs, roofline, dev, timed, steps, l2_gbs, B=8
     return res
 
 
+def run_sweep(args, dev):
+    """Throughput of the stage kernels against the amount of work per launch (the
+    paper's kernel-utilisation and batching study, Section III-B): NTT passes over
+    10..250 limbs, BConv with 12 (CUDA cores) or 8 (both kernels) inputs over the
+    output count, and batched key switches at l = 24 over the batch size.  Kernel
+    times come from the library's trace (CUDA events around each launch)."""
+    import numpy as np
+    import torch
+    from paper_2512_18345_gb300 import binding, inputs
+    out = {"ntt": [], "bconv": [], "batch": []}
+    alu = ALU_PEAK["bfly"]
+
+    def traced(ctx, fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ctx.trace(True)
+        for _ in range(reps):
+            fn()
+        stats = ctx.trace_read()
+        ctx.trace(False)
+        return stats
+
+    P = inputs.workload_params("paper_ks_N65536_L48_a12")  # 60 primes
+    ctx = binding.Context.from_params(P, device=dev)
+    g = inputs.rng(4242)
+    nprime = len(P.primes)
+    for L in (10, 24, 48, 96, 160, 250):
+        a = binding.to_device(g.integers(0, 1 << 20, size=(L, P.N), dtype=np.uint32), dev)
+        idx = [i % nprime for i in range(L)]
+        stats = traced(ctx, lambda: ctx.ntt(a, idx), 10)
+        row = {"limbs": L}
+        for name, (n, ms) in stats.items():
+            us = 1e3 * ms / n
+            bfly = L * (P.N // 2) * 8
+            row[name] = {"us": us, "tbutterflies_per_s": bfly / (us * 1e-6) / 1e12, "frac_alu": bfly / (us * 1e-6) / alu}
+        out["ntt"].append(row)
+    for n_in, n_outs, modes in ((12, (12, 24, 36, 48), ("scalar",)),):
+        for n_out in n_outs:
+            x = binding.to_device(g.integers(0, 1 << 20, size=(n_in, P.N), dtype=np.uint32), dev)
+            in_idx = list(range(nprime - n_in, nprime))
+            out_idx = list(range(n_out))
+            stats = traced(ctx, lambda: ctx.bconv(x, in_idx, out_idx), 5)
+            n, ms = stats["bconv"]
+            us = 1e3 * ms / n
+            out["bconv"].append({"n_in": n_in, "n_out": n_out, "kernel": "cuda cores", "us": us,
+                                 "tmac_per_s": n_in * n_out * P.N / (us * 1e-6) / 1e12})
+    ctx.close()
+    P8 = inputs.workload_params("hrotate_N65536_L24_tc")  # alpha = K = 8: both kernels
+    ctx = binding.Context.from_params(P8, device=dev)
+    for mode, name in ((binding.FHE_BCONV_SCALAR, "bconv"), (binding.FHE_BCONV_TC, "bconv_tc")):
+        ctx.set_bconv(mode)
+        for n_out in (8, 16, 24):
+            x = binding.to_device(g.integers(0, 1 << 20, size=(8, P8.N), dtype=np.uint32), dev)
+            in_idx = list(range(24, 32))
+            out_idx = list(range(n_out))
+            stats = traced(ctx, lambda: ctx.bconv(x, in_idx, out_idx), 5)
+            n, ms = stats[name]
+            us = 1e3 * ms / n
+            out["bconv"].append({"n_in": 8, "n_out": n_out, "kernel": "tensor cores" if name == "bconv_tc" else
+                                 "cuda cores", "us": us, "tmac_per_s": 8 * n_out * P8.N / (us * 1e-6) / 1e12})
+    # batched key switches at l = 24 over the batch size (default schedule, graph)
+    ctx.set_bconv(binding.FHE_BCONV_TC)
+    keys, cts = [], []
+    for b in range(16):
+        r = 1 + 37 * b
+        ctx.set_rot_key(r, binding.to_device(rand_key_np(inputs, P8, g), dev))
+        cts.append((r, binding.to_device(np.stack([inputs.uniform_residues(g, P8.q, P8.N) for _ in range(2)]), dev)))
+    for B in (1, 2, 4, 8, 16):
+        items = [dict(op=binding.FHE_OP_ROTATE, level=P8.L, rot=r, **{"in": c}, out=binding.empty((2, P8.L, P8.N), dev))
+                 for r, c in cts[:B]]
+        plan = ctx.batch_plan(items, binding.FHE_PLAN_GRAPH)
+        for _ in range(3):
+            plan.launch()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20
+        e0.record()
+        for _ in range(reps):
+            plan.launch()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out["batch"].append({"batch": B, "groups": plan.groups, "us_per_ks": 1e3 * ms / B, "ks_per_s": B / (ms / 1e3)})
+        plan.close()
+    ctx.close()
+    print(json.dumps({"sweep": out}), flush=True)
+
+
 def kernel_model(name, P, level, G):
     """Algorithmic bytes and operations of the stage kernel `name` summed over its
     launches in one batched group of G HRotates at `level` (fused pipeline): each
@@ -432,6 +523,11 @@ def main():
     items = [dict(op=binding.FHE_OP_ROTATE, level=level, rot=r, **{"in": c}, out=o) for r, c, o in zip(rots, cts, outs)]
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
+
+    if args.sweep:
+        run_sweep(args, dev)
+        ctx.close()
+        return
 
     if args.profile_run:
         ctx.set_fused(True)
