@@ -274,10 +274,16 @@ def bench_lt(binding, inputs, dev, timed, bconv_mode):
     k = 5
     ms = timed(lambda: ctx.linear_transform(ct, level, diags, baby, giant, out=out), k)
     ctx.sync()
+    # per-kernel breakdown of one call (trace; the auxiliary branch serialised)
+    ctx.trace(True)
+    ctx.linear_transform(ct, level, diags, baby, giant, out=out)
+    stats = ctx.trace_read()
+    ctx.trace(False)
     diag_bytes = baby * giant * level * P.N * 4
     ctx.close()
     return {"ms": ms / k, "key_switches": (baby - 1) + (giant - 1), "nominal_steps": [baby, giant],
-            "diagonals": baby * giant, "diagonal_bytes": diag_bytes}
+            "diagonals": baby * giant, "diagonal_bytes": diag_bytes,
+            "kernels_ms": {k2: round(v[1], 4) for k2, v in sorted(stats.items(), key=lambda kv: -kv[1][1])}}
 
 
 def bench_paper_shapes(binding, inputs, roofline, dev, timed, steps, l2_gbs, B=8):

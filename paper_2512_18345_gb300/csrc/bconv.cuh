@@ -34,7 +34,7 @@ struct BconvGroup {
 constexpr int kTcM = 128, kTcK = 48, kTcMaxIn = 8;
 __host__ __device__ constexpr int tc_npad(int n_out) { return (4 * n_out + 15) / 16 * 16; }
 
-constexpr int kMaxBconvGroups = 8;
+constexpr int kMaxBconvGroups = 48;
 struct BconvArgs {
   int ngroups;
   const BconvGroup *dev;  // device array (batched plans), else g[]

@@ -8,7 +8,7 @@
 namespace fhe {
 
 constexpr int kMaxPrimes = 64;
-constexpr int kMaxSeg = 16;       // segments passed by value per launch
+constexpr int kMaxSeg = 96;       // segments passed by value per launch (kernel parameters up to 32 KB)
 constexpr int kTile = 4096;       // elements per NTT tile (16 KB)
 constexpr int kNttThreads = 256;  // 16 elements per thread
 
@@ -96,7 +96,7 @@ struct KsArgs {
   int add_c1;            // addp's second polynomial also goes to c = 1 (HMult); a rotation adds c0 only
 };
 
-constexpr int kMaxInlineItems = 4;
+constexpr int kMaxInlineItems = 16;
 
 // A launch's work list: segments and per-item arguments, either inline (by
 // value, single operations) or in device memory (batched plans).

@@ -208,6 +208,8 @@ __device__ __forceinline__ void st_words(uint32_t *p, const uint32_t (&v)[E]) {
 struct IpUnit {            // one unit, as the consumers need it
   uint32_t *d0;            // u_0 at this unit's first coefficient; u_1 = d0 + d1_off
   const uint32_t *gsrc;    // own limb read through the automorphism (nullptr: none)
+  const uint32_t *esrc[4]; // GEXT: every digit's limb, read through its automorphism
+  uint32_t egal[4];        // GEXT: that automorphism's Galois element
   const uint32_t *add0;    // pass-through limb added (times P) to u_0, or nullptr; add1 = add0 + add1_off
   PrimeC P;
   uint2 pm;                // P mod the unit's prime (Shoup pair)
@@ -215,7 +217,10 @@ struct IpUnit {            // one unit, as the consumers need it
   int beta, gjd, add1;
 };
 
-template <bool GOWN>
+// GEXT (hoisted rotations: the ModUp digits themselves are read through the
+// automorphism): only the key chunks stream through the stages; every digit's values
+// are gathered with plain loads one unit ahead (the shared digits stay in L2).
+template <bool GOWN, bool GEXT>
 __global__ void __launch_bounds__(kIpThreads, 2) k_ip_bulk(const __grid_constant__ SegList sl, const PrimeC *pc,
                                                            int logn, unsigned int *status, int beta_max, int stages) {
   extern __shared__ __align__(128) uint8_t smem[];
@@ -241,8 +246,14 @@ __global__ void __launch_bounds__(kIpThreads, 2) k_ip_bulk(const __grid_constant
     d.d1_off = (uint32_t)((size_t)ks.n_ext * N);
     d.P = pc[sg.prime + within];
     d.beta = ks.beta;
-    d.gjd = (GOWN && t < ks.level) ? t / ks.alpha : -1;
+    d.gjd = (GOWN && !GEXT && t < ks.level) ? t / ks.alpha : -1;
     d.gsrc = d.gjd >= 0 ? ks.own + (size_t)t * N : nullptr;
+    if (GEXT)
+      for (int jd = 0; jd < 4; jd++) {
+        const bool own = t < ks.level && t >= jd * ks.alpha && t < (jd + 1) * ks.alpha;
+        d.esrc[jd] = jd >= ks.beta ? nullptr : own ? ks.own + (size_t)t * N : ks.ext + ((size_t)jd * ks.n_ext + t) * N;
+        d.egal[jd] = own ? ks.galois_own : ks.galois_ext;
+      }
     d.galois = ks.galois_own;
     d.j0 = (uint32_t)c0;
     const bool add = ks.addp && t < ks.level;
@@ -253,11 +264,11 @@ __global__ void __launch_bounds__(kIpThreads, 2) k_ip_bulk(const __grid_constant
     d.pm = add ? ks.pmod[t] : make_uint2(0, 0);
     desc[st] = d;
     const size_t kstride = (size_t)2 * (ks.L + ks.K) * N, half = (size_t)(ks.L + ks.K) * N;
-    const uint32_t copies = 3u * (uint32_t)ks.beta - (d.gjd >= 0 ? 1u : 0u);
+    const uint32_t copies = GEXT ? 2u * (uint32_t)ks.beta : 3u * (uint32_t)ks.beta - (d.gjd >= 0 ? 1u : 0u);
     mbar_arrive_expect_tx(&bar[st], copies * kIpChunk * 4u);
     uint32_t *dst = buf + (size_t)st * stage_words;
     for (int jd = 0; jd < ks.beta; jd++) {
-      if (jd != d.gjd) {
+      if (!GEXT && jd != d.gjd) {
         const bool own = t < ks.level && t >= jd * ks.alpha && t < (jd + 1) * ks.alpha;
         const uint32_t *e = own ? ks.own + (size_t)t * N : ks.ext + ((size_t)jd * ks.n_ext + t) * N;
         bulk_g2s(dst + (size_t)(3 * jd) * kIpChunk, e + c0, kIpChunk * 4u, &bar[st]);
@@ -295,9 +306,20 @@ __global__ void __launch_bounds__(kIpThreads, 2) k_ip_bulk(const __grid_constant
       for (int e = 0; e < E; e++) p0[e] = __ldg(d.add0 + galois_src(j + e, d.galois_add, logn));
     }
   };
-  uint32_t gnext[E] = {}, pnext0[E] = {}, pnext1[E] = {};
+  // GEXT: every digit's values of a unit, one unit ahead
+  constexpr int XD = GEXT ? 4 : 1;
+  auto gather_all = [&](const IpUnit &d, uint32_t (&v)[XD][E]) {
+    const uint32_t j = d.j0 + tid * E;
+#pragma unroll
+    for (int jd = 0; jd < XD; jd++)
+      if (jd < d.beta)
+#pragma unroll
+        for (int e = 0; e < E; e++) v[jd][e] = __ldg(d.esrc[jd] + galois_src(j + e, d.egal[jd], logn));
+  };
+  uint32_t gnext[E] = {}, pnext0[E] = {}, pnext1[E] = {}, xnext[XD][E] = {};
   if ((int)blockIdx.x < total) {
     if (GOWN && desc[0].gjd >= 0) gather(desc[0], gnext);
+    if (GEXT) gather_all(desc[0], xnext);
     if (desc[0].add0) pass(desc[0], pnext0, pnext1);
   }
   bool ok = true;
@@ -305,9 +327,13 @@ __global__ void __launch_bounds__(kIpThreads, 2) k_ip_bulk(const __grid_constant
   for (int u = blockIdx.x; u < total; u += gridDim.x, k++) {
     const int st = k % stages;
     const IpUnit d = desc[st];
-    uint32_t gv[E], pv0[E], pv1[E];
+    uint32_t gv[E], pv0[E], pv1[E], xv[XD][E];
 #pragma unroll
     for (int e = 0; e < E; e++) gv[e] = gnext[e], pv0[e] = pnext0[e], pv1[e] = pnext1[e];
+#pragma unroll
+    for (int jd = 0; jd < XD; jd++)
+#pragma unroll
+      for (int e = 0; e < E; e++) xv[jd][e] = xnext[jd][e];
     if (tid == 0) s_ok = mbar_wait_bounded(&bar[st], (uint32_t)(k / stages) & 1u) ? 1 : 0;
     __syncthreads();
     ok = s_ok != 0;
@@ -315,6 +341,7 @@ __global__ void __launch_bounds__(kIpThreads, 2) k_ip_bulk(const __grid_constant
     if (u + (int)gridDim.x < total) {  // descriptor of this CTA's next unit, written before this wait
       const IpUnit dn = desc[(k + 1) % stages];
       if (GOWN && dn.gjd >= 0) gather(dn, gnext);
+      if (GEXT) gather_all(dn, xnext);
       if (dn.add0) pass(dn, pnext0, pnext1);
     }
     const uint32_t *src = buf + (size_t)st * stage_words + tid * E;
@@ -323,7 +350,10 @@ __global__ void __launch_bounds__(kIpThreads, 2) k_ip_bulk(const __grid_constant
     for (int jd = 0; jd < 4; jd++) {
       if (jd < d.beta) {
         uint32_t ev[E], k0[E], k1[E];
-        if (jd == d.gjd) {
+        if (GEXT) {
+#pragma unroll
+          for (int e = 0; e < E; e++) ev[e] = xv[jd < XD ? jd : 0][e];
+        } else if (jd == d.gjd) {
 #pragma unroll
           for (int e = 0; e < E; e++) ev[e] = gv[e];
         } else {

@@ -127,27 +127,37 @@ cudaError_t launch_ip(const DevTables &t, const SegList &sl, bool gather_own, bo
   if (sl.total == 0) return cudaSuccess;
   TraceScope ts(t, "inner_product", s);
   const bool go = gather_own, ge = gather_ext;
-  if (!ge && beta_max >= 1 && beta_max <= 4 && (1 << t.logn) % kIpChunk == 0) {
+  if (beta_max >= 1 && beta_max <= 4 && (1 << t.logn) % kIpChunk == 0) {
     // streaming kernel: as many stages as fit half an SM's shared memory; one or two CTAs per
     // SM (one leaves half of every SM to the transforms running beside it)
     const int stage_bytes = 3 * beta_max * kIpChunk * 4;
     const int per_stage = stage_bytes + 8 + (int)sizeof(IpUnit);
     const int stages = std::min(8, (113 * 1024 - 256) / per_stage);
     const int smem = stages * per_stage;
-    static bool configured[2] = {false, false};
-    if (!configured[go]) {
-      cudaError_t e = go ? cudaFuncSetAttribute(k_ip_bulk<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 113 * 1024)
-                         : cudaFuncSetAttribute(k_ip_bulk<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 113 * 1024);
+    static bool configured[4] = {false, false, false, false};
+    const int variant = (go ? 1 : 0) + (ge ? 2 : 0);
+    if (!configured[variant]) {
+      cudaError_t e = cudaSuccess;
+      switch (variant) {
+        case 0: e = cudaFuncSetAttribute(k_ip_bulk<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 113 * 1024); break;
+        case 1: e = cudaFuncSetAttribute(k_ip_bulk<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 113 * 1024); break;
+        case 2: e = cudaFuncSetAttribute(k_ip_bulk<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 113 * 1024); break;
+        default: e = cudaFuncSetAttribute(k_ip_bulk<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 113 * 1024); break;
+      }
       if (e != cudaSuccess) return e;
-      configured[go] = true;
+      configured[variant] = true;
     }
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int units = sl.total * ((1 << t.logn) / kIpChunk);
     const unsigned grid = (unsigned)std::min(units, std::max(1, std::min(2, t.ip_ctas_per_sm)) * sms);
-    if (go) k_ip_bulk<true><<<grid, kIpThreads, smem, s>>>(sl, t.pc, t.logn, t.status, beta_max, stages);
-    else k_ip_bulk<false><<<grid, kIpThreads, smem, s>>>(sl, t.pc, t.logn, t.status, beta_max, stages);
+    switch (variant) {
+      case 0: k_ip_bulk<false, false><<<grid, kIpThreads, smem, s>>>(sl, t.pc, t.logn, t.status, beta_max, stages); break;
+      case 1: k_ip_bulk<true, false><<<grid, kIpThreads, smem, s>>>(sl, t.pc, t.logn, t.status, beta_max, stages); break;
+      case 2: k_ip_bulk<false, true><<<grid, kIpThreads, smem, s>>>(sl, t.pc, t.logn, t.status, beta_max, stages); break;
+      default: k_ip_bulk<true, true><<<grid, kIpThreads, smem, s>>>(sl, t.pc, t.logn, t.status, beta_max, stages); break;
+    }
     g_launches++;
     return cudaGetLastError();
   }

@@ -6,7 +6,8 @@
 // automorphism on the extended digits, inner product and ModDown); the
 // diagonal multiply-accumulate reads every baby rotation once and every
 // diagonal once (the diagonals stream from HBM: G B l limbs); the G - 1 giant
-// rotations are ordinary rotations, run as one batched stage program per four.
+// rotations are ordinary rotations, run as batched stage programs; one pass sums
+// the giant-step outputs.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -30,42 +31,77 @@ struct DiagArgs {
 };
 
 // out_g[c][i][n] = sum_b diag[g nb + b][i][n] babies[b][c][i][n] mod q_i; one thread per
-// coefficient of one limb, each baby value read once, accumulators reduced every three
-// products (a reduced value plus three 62-bit products stays below 2^64).
+// coefficient of one limb and group of kGsub giant steps (blockIdx.y; the groups re-read
+// the baby values from L2); two baby steps' loads are issued before their
+// multiply-accumulates, and the accumulators are reduced after every second baby step
+// (a reduced value plus two 62-bit products stays below 2^64).
+constexpr int kGsub = 4;
 __global__ void __launch_bounds__(256) k_diagmac(const __grid_constant__ DiagArgs a, const PrimeC *pc, int logn) {
   const size_t N = (size_t)1 << logn;
   const int per_limb = (int)(N / 256);
   const int i = blockIdx.x / per_limb;
   const size_t n = (size_t)(blockIdx.x % per_limb) * 256 + threadIdx.x;
+  const int g0 = blockIdx.y * kGsub, ng = min(kGsub, a.giant - g0);
   const PrimeC P = pc[i];
   const size_t poly = (size_t)a.level * N;
-  uint64_t acc[2][kMaxGiant];
+  const uint32_t *dbase = a.diags + (size_t)i * N + n;
+  uint64_t acc[2][kGsub];
 #pragma unroll
-  for (int g = 0; g < kMaxGiant; g++) acc[0][g] = acc[1][g] = 0;
-  for (int b = 0; b < a.nb; b++) {
-    const uint32_t x0 = __ldg(a.babies[b] + (size_t)i * N + n);
-    const uint32_t x1 = __ldg(a.babies[b] + poly + (size_t)i * N + n);
+  for (int g = 0; g < kGsub; g++) acc[0][g] = acc[1][g] = 0;
+  for (int b = 0; b < a.nb; b += 2) {
+    const bool two = b + 1 < a.nb;
+    uint32_t x[2][2], d[2][kGsub];
 #pragma unroll
-    for (int g = 0; g < kMaxGiant; g++) {
-      if (g < a.giant) {
-        const uint32_t d = __ldg(a.diags + ((size_t)(g * a.nb + b) * a.level + i) * N + n);
-        acc[0][g] += (uint64_t)d * x0;
-        acc[1][g] += (uint64_t)d * x1;
+    for (int h = 0; h < 2; h++) {
+      const int bb = two ? b + h : b;
+      x[h][0] = __ldg(a.babies[bb] + (size_t)i * N + n);
+      x[h][1] = __ldg(a.babies[bb] + poly + (size_t)i * N + n);
+#pragma unroll
+      for (int g = 0; g < kGsub; g++)
+        d[h][g] = g < ng ? __ldg(dbase + (size_t)((g0 + g) * a.nb + bb) * poly) : 0u;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      if (h == 1 && !two) break;
+#pragma unroll
+      for (int g = 0; g < kGsub; g++) {
+        acc[0][g] += (uint64_t)d[h][g] * x[h][0];
+        acc[1][g] += (uint64_t)d[h][g] * x[h][1];
       }
     }
-    if (b % 3 == 2) {
 #pragma unroll
-      for (int g = 0; g < kMaxGiant; g++)
-        if (g < a.giant) {
-          acc[0][g] = reduce_u64(acc[0][g], P);
-          acc[1][g] = reduce_u64(acc[1][g], P);
-        }
+    for (int g = 0; g < kGsub; g++) {
+      acc[0][g] = reduce_u64(acc[0][g], P);
+      acc[1][g] = reduce_u64(acc[1][g], P);
     }
   }
 #pragma unroll
-  for (int g = 0; g < kMaxGiant; g++)
-    if (g < a.giant)
-      for (int c = 0; c < 2; c++) a.out[((size_t)g * 2 + c) * poly + (size_t)i * N + n] = reduce_u64(acc[c][g], P);
+  for (int g = 0; g < kGsub; g++)
+    if (g < ng)
+#pragma unroll
+      for (int c = 0; c < 2; c++) a.out[((size_t)(g0 + g) * 2 + c) * poly + (size_t)i * N + n] = (uint32_t)acc[c][g];
+}
+
+// out[c][i][n] = sum_{g < count} in_g[c][i][n] mod q_i (the giant-step outputs), one thread
+// per coefficient of one limb of both polynomials
+struct SumArgs {
+  const uint32_t *in[kMaxGiant];  // [2][level][N] each
+  uint32_t *out;
+  int count, level;
+};
+__global__ void __launch_bounds__(256) k_sum(const __grid_constant__ SumArgs a, const PrimeC *pc, int logn) {
+  const size_t N = (size_t)1 << logn;
+  const int per_limb = (int)(N / 256);
+  const int i = blockIdx.x / per_limb;
+  const size_t n = (size_t)(blockIdx.x % per_limb) * 256 + threadIdx.x;
+  const uint32_t q = pc[i].q;
+  const size_t poly = (size_t)a.level * N;
+#pragma unroll
+  for (int c = 0; c < 2; c++) {
+    uint32_t acc = 0;
+    for (int g = 0; g < a.count; g++) acc = add_mod(acc, __ldg(a.in[g] + c * poly + (size_t)i * N + n), q);
+    a.out[c * poly + (size_t)i * N + n] = acc;
+  }
 }
 
 }  // namespace fhe
@@ -121,7 +157,8 @@ extern "C" int fhe_linear_transform(fhe_ctx *c, const uint32_t *ct, int level, c
   da.level = level;
   {
     TraceScope ts(c->tabs, "diag_mac", s);
-    k_diagmac<<<(unsigned)(level * (N / 256)), 256, 0, s>>>(da, c->d_pc, c->logn);
+    const dim3 grid((unsigned)(level * (N / 256)), (unsigned)((giant + kGsub - 1) / kGsub));
+    k_diagmac<<<grid, 256, 0, s>>>(da, c->d_pc, c->logn);
     note_launch();
     if (cudaGetLastError() != cudaSuccess) return fhe_fail(FHE_ECUDA, "fhe_linear_transform: diagonal kernel");
   }
@@ -146,12 +183,19 @@ extern "C" int fhe_linear_transform(fhe_ctx *c, const uint32_t *ct, int level, c
   }
   rc = run_items_chunked(c, its, 0, s);
   if (rc != FHE_OK) return rc;
-  // out = inner_0 + sum_g rot_{B g}(inner_g)
-  if (cudaMemcpyAsync(out, inner, 4 * ct_words, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-    return fhe_fail(FHE_ECUDA, "fhe_linear_transform: copy");
-  for (int g = 1; g < giant; g++) {
-    rc = fhe_add(c, out, grot + g * ct_words, 2, level, out, stream);
-    if (rc != FHE_OK) return rc;
+  // out = inner_0 + sum_g rot_{B g}(inner_g), in one pass
+  SumArgs sa;
+  memset(&sa, 0, sizeof sa);
+  sa.in[0] = inner;
+  for (int g = 1; g < giant; g++) sa.in[g] = grot + g * ct_words;
+  sa.count = giant;
+  sa.out = out;
+  sa.level = level;
+  {
+    TraceScope ts(c->tabs, "lt_sum", s);
+    k_sum<<<(unsigned)(level * (N / 256)), 256, 0, s>>>(sa, c->d_pc, c->logn);
+    note_launch();
+    if (cudaGetLastError() != cudaSuccess) return fhe_fail(FHE_ECUDA, "fhe_linear_transform: sum kernel");
   }
   return FHE_OK;
 }

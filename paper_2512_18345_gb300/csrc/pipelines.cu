@@ -251,7 +251,7 @@ extern "C" int fhe_rotate_hoisted(fhe_ctx *c, const uint32_t *ct, int level, con
   cudaStream_t s = (cudaStream_t)stream;
   c->order_stream(s);
   // one shared ModUp of c1 (slot 0), then the rotations' ModDowns batched
-  // kMaxInlineItems - 1 at a time, each with its own slot
+  // as many at a time as fit the by-value launch arguments, each with its own slot
   std::vector<Item> todo;
   for (int r = 0; r < n; r++) {
     const uint32_t k = fhe_galois_elt(rots[r], c->N);
