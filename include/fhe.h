@@ -194,6 +194,35 @@ FHE_API int fhe_rotate_hoisted(fhe_ctx *ctx, const uint32_t *ct, int level, cons
 FHE_API int fhe_linear_transform(fhe_ctx *ctx, const uint32_t *ct, int level, const uint32_t *diags, int baby,
                                  int giant, uint32_t *out, fhe_stream stream);
 
+/*
+ * Double-hoisted baby-step / giant-step transform, the form of the CoeffToSlot /
+ * SlotToCoeff levels of bootstrapping (radix-merged FFT levels with few nonzero
+ * diagonals; the hoisting literature cited in Section V-C):
+ *   out = sum_{g < n_giant} rot_{giant[g]}( sum_{b < n_baby} diags[idx[g n_baby + b]] (.) rot_{baby[b]}(ct) )
+ * Every baby rotation shares one ModUp of c1 and stays in the extended basis
+ * Q_level u P (no ModDown); the inner sums are formed there; the c1 half of
+ * each rotating giant step's inner sum is brought down to Q_level, decomposed
+ * again and key-switched, still without ModDown; one ModDown of both halves
+ * ends the transform.  Bit-exact against that sequence of exact RNS steps.
+ *   ct     [2][level][N] NTT form, device, 16-byte aligned;
+ *   baby   [n_baby], giant [n_giant] rotation indices (host); one whose Galois
+ *          element is 1 (0 mod N/2) is the identity and needs no key, every other
+ *          one needs its rotation key; n_baby <= 32, n_giant <= 16;
+ *   diags  [n_diag][level+K][N] NTT-form plaintexts over q_0..q_{level-1} and
+ *          p_0..p_{K-1} (device; the extended basis, since they multiply
+ *          extended-basis rotations);
+ *   idx    [n_giant][n_baby] (host) index into diags, or -1 where the pair has
+ *          no diagonal;
+ *   out    [2][level][N] (device), must not overlap ct or diags.
+ * No rescale.  The context grows a scratch buffer of (n_baby + 2 n_giant + 1)
+ * extended-basis ciphertexts plus n_giant polynomials.  Errors: FHE_EINVAL (null,
+ * misaligned, counts or idx out of range, n_diag > 32767), FHE_ELEVEL, FHE_ENOKEY, FHE_EALIAS,
+ * FHE_ENOMEM, FHE_ECUDA.
+ */
+FHE_API int fhe_linear_transform_dh(fhe_ctx *ctx, const uint32_t *ct, int level, const int32_t *baby, int n_baby,
+                                    const int32_t *giant, int n_giant, const uint32_t *diags, int n_diag,
+                                    const int32_t *idx, uint32_t *out, fhe_stream stream);
+
 /* Plaintext multiply: out_c = ct_c * pt ([level][N] NTT form), c = 0, 1. out may equal ct. */
 FHE_API int fhe_pmult(fhe_ctx *ctx, const uint32_t *ct, const uint32_t *pt, int level, uint32_t *out, fhe_stream stream);
 /* Addition of two [npoly][level][N] arrays (npoly = 2 for ciphertexts). out may equal a or b. */

@@ -29,7 +29,7 @@ FHE_TUNE_BCONV = 1
 EXPORTS = (
     "fhe_ctx_create", "fhe_ctx_destroy", "fhe_ctx_info", "fhe_ctx_set_bconv", "fhe_ctx_set_fused", "fhe_ctx_sync",
     "fhe_set_relin_key", "fhe_set_rot_key", "fhe_keyswitch", "fhe_rotate", "fhe_hmult", "fhe_rescale",
-    "fhe_rotate_hoisted", "fhe_linear_transform", "fhe_pmult", "fhe_add", "fhe_ntt", "fhe_intt", "fhe_modup", "fhe_moddown",
+    "fhe_rotate_hoisted", "fhe_linear_transform", "fhe_linear_transform_dh", "fhe_pmult", "fhe_add", "fhe_ntt", "fhe_intt", "fhe_modup", "fhe_moddown",
     "fhe_bconv", "fhe_batch_plan", "fhe_batch_launch", "fhe_plan_destroy", "fhe_plan_kernel_count",
     "fhe_plan_groups", "fhe_ctx_set_batch",
     "fhe_trace_enable", "fhe_trace_read", "fhe_probe_bandwidth", "fhe_autotune", "fhe_autotune_cached", "fhe_ctx_set_pipelining", "fhe_selftest_wait_timeout", "fhe_bconv_noalloc", "fhe_last_error",
@@ -103,6 +103,9 @@ def lib() -> ctypes.CDLL:
         "fhe_rotate_hoisted": [vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_int,
                                ctypes.POINTER(vp), vp],
         "fhe_linear_transform": [vp, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp, vp],
+        "fhe_linear_transform_dh": [vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_int32), ctypes.c_int, vp, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_int32), vp, vp],
         "fhe_pmult": [vp, vp, vp, ctypes.c_int, vp, vp],
         "fhe_add": [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp, vp],
         "fhe_ntt": [vp, vp, ip, ctypes.c_int, vp],
@@ -335,6 +338,19 @@ class Context:
     def linear_transform(self, ct, level: int, diags, baby: int, giant: int, out=None, stream=None):
         out = self._out(out, (2, level, self.N))
         check(lib().fhe_linear_transform(self.h, _ptr(ct), level, _ptr(diags), baby, giant, _ptr(out), _stream(stream)))
+        return out
+
+    def linear_transform_dh(self, ct, level: int, baby, giant, diags, idx, out=None, stream=None):
+        """Double-hoisted transform; diags [n_diag][level+K][N] (device), idx [n_giant][n_baby] host ints."""
+        out = self._out(out, (2, level, self.N))
+        baby, giant = list(baby), list(giant)
+        flat = [int(x) for row in idx for x in row]
+        b = (ctypes.c_int32 * len(baby))(*baby)
+        g = (ctypes.c_int32 * len(giant))(*giant)
+        ix = (ctypes.c_int32 * len(flat))(*flat)
+        n_diag = int(diags.shape[0])
+        check(lib().fhe_linear_transform_dh(self.h, _ptr(ct), level, b, len(baby), g, len(giant), _ptr(diags), n_diag,
+                                            ix, _ptr(out), _stream(stream)))
         return out
 
     def pmult(self, ct, pt, level: int, out=None, stream=None):

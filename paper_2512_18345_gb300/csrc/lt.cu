@@ -24,15 +24,18 @@ namespace fhe {
 
 constexpr int kMaxBaby = 32, kMaxGiant = 16;
 struct DiagArgs {
-  const uint32_t *babies[kMaxBaby];  // [2][level][N] each
-  const uint32_t *diags;             // [giant * nb][level][N]
-  uint32_t *out;                     // [giant][2][level][N]
-  int nb, giant, level;
+  const uint32_t *babies[kMaxBaby];  // [2][nlimb][N] each
+  const uint32_t *diags;             // [n_diag][nlimb][N]
+  uint32_t *out;                     // [giant][2][nlimb][N]
+  int nb, giant, nlimb, level, L;    // limb i < level is modulo q_i, limb i >= level modulo p_{i - level}
+  int16_t didx[kMaxGiant * kMaxBaby];  // [giant][nb]: index into diags, -1 where the pair has no diagonal
 };
 
-// out_g[c][i][n] = sum_b diag[g nb + b][i][n] babies[b][c][i][n] mod q_i; one thread per
-// coefficient of one limb and group of kGsub giant steps (blockIdx.y; the groups re-read
-// the baby values from L2); two baby steps' loads are issued before their
+__device__ __forceinline__ int limb_prime(int i, int level, int L) { return i < level ? i : L + (i - level); }
+
+// out_g[c][i][n] = sum_b diag[didx[g][b]][i][n] babies[b][c][i][n] mod (prime of limb i); one
+// thread per coefficient of one limb and group of kGsub giant steps (blockIdx.y; the groups
+// re-read the baby values from L2); two baby steps' loads are issued before their
 // multiply-accumulates, and the accumulators are reduced after every second baby step
 // (a reduced value plus two 62-bit products stays below 2^64).
 constexpr int kGsub = 4;
@@ -42,8 +45,8 @@ __global__ void __launch_bounds__(256) k_diagmac(const __grid_constant__ DiagArg
   const int i = blockIdx.x / per_limb;
   const size_t n = (size_t)(blockIdx.x % per_limb) * 256 + threadIdx.x;
   const int g0 = blockIdx.y * kGsub, ng = min(kGsub, a.giant - g0);
-  const PrimeC P = pc[i];
-  const size_t poly = (size_t)a.level * N;
+  const PrimeC P = pc[limb_prime(i, a.level, a.L)];
+  const size_t poly = (size_t)a.nlimb * N;
   const uint32_t *dbase = a.diags + (size_t)i * N + n;
   uint64_t acc[2][kGsub];
 #pragma unroll
@@ -57,8 +60,10 @@ __global__ void __launch_bounds__(256) k_diagmac(const __grid_constant__ DiagArg
       x[h][0] = __ldg(a.babies[bb] + (size_t)i * N + n);
       x[h][1] = __ldg(a.babies[bb] + poly + (size_t)i * N + n);
 #pragma unroll
-      for (int g = 0; g < kGsub; g++)
-        d[h][g] = g < ng ? __ldg(dbase + (size_t)((g0 + g) * a.nb + bb) * poly) : 0u;
+      for (int g = 0; g < kGsub; g++) {
+        const int k = g < ng ? a.didx[(g0 + g) * a.nb + bb] : -1;
+        d[h][g] = k >= 0 ? __ldg(dbase + (size_t)k * poly) : 0u;
+      }
     }
 #pragma unroll
     for (int h = 0; h < 2; h++) {
@@ -80,6 +85,56 @@ __global__ void __launch_bounds__(256) k_diagmac(const __grid_constant__ DiagArg
     if (g < ng)
 #pragma unroll
       for (int c = 0; c < 2; c++) a.out[((size_t)(g0 + g) * 2 + c) * poly + (size_t)i * N + n] = (uint32_t)acc[c][g];
+}
+
+// The identity baby step of a double-hoisted transform, in the extended basis:
+// out[c] = P ct[c] on the q-limbs and 0 on the special limbs (ModDown of it returns ct exactly).
+__global__ void __launch_bounds__(256) k_lift(const uint32_t *ct, uint32_t *out, const uint2 *pmod, const PrimeC *pc,
+                                              int level, int nlimb, int logn) {
+  const size_t N = (size_t)1 << logn;
+  const int per_limb = (int)(N / 256);
+  const int i = blockIdx.x / per_limb;
+  const size_t n = (size_t)(blockIdx.x % per_limb) * 256 + threadIdx.x;
+#pragma unroll
+  for (int c = 0; c < 2; c++) {
+    uint32_t v = 0;
+    if (i < level) v = shoup(__ldg(ct + ((size_t)c * level + i) * N + n), pmod[i], pc[i].q);
+    out[((size_t)c * nlimb + i) * N + n] = v;
+  }
+}
+
+// Giant-step accumulation of a double-hoisted transform, in the extended basis:
+//   out_0 = sum_g sigma_g(inner_g,0) + v_g,0,   out_1 = sum_g v_g,1,
+// where v_g is the extended-basis key switch of sigma_g applied to ModDown(inner_g,1); a giant
+// step without rotation (v_g null) adds inner_g itself.
+struct GsumArgs {
+  const uint32_t *inner[kMaxGiant];  // [2][nlimb][N]
+  const uint32_t *v[kMaxGiant];      // [2][nlimb][N] or null
+  uint32_t galois[kMaxGiant];
+  uint32_t *out;                     // [2][nlimb][N]
+  int count, nlimb, level, L;
+};
+__global__ void __launch_bounds__(256) k_gsum(const __grid_constant__ GsumArgs a, const PrimeC *pc, int logn) {
+  const size_t N = (size_t)1 << logn;
+  const int per_limb = (int)(N / 256);
+  const int i = blockIdx.x / per_limb;
+  const uint32_t n = (uint32_t)((blockIdx.x % per_limb) * 256 + threadIdx.x);
+  const uint32_t q = pc[limb_prime(i, a.level, a.L)].q;
+  const size_t poly = (size_t)a.nlimb * N, off = (size_t)i * N;
+  uint32_t a0 = 0, a1 = 0;
+  for (int g = 0; g < a.count; g++) {
+    const uint32_t *in = a.inner[g] + off;
+    if (!a.v[g]) {
+      a0 = add_mod(a0, __ldg(in + n), q);
+      a1 = add_mod(a1, __ldg(in + poly + n), q);
+    } else {
+      a0 = add_mod(a0, __ldg(in + galois_src(n, a.galois[g], logn)), q);
+      a0 = add_mod(a0, __ldg(a.v[g] + off + n), q);
+      a1 = add_mod(a1, __ldg(a.v[g] + poly + off + n), q);
+    }
+  }
+  a.out[off + n] = a0;
+  a.out[poly + off + n] = a1;
 }
 
 // out[c][i][n] = sum_{g < count} in_g[c][i][n] mod q_i (the giant-step outputs), one thread
@@ -105,6 +160,17 @@ __global__ void __launch_bounds__(256) k_sum(const __grid_constant__ SumArgs a, 
 }
 
 }  // namespace fhe
+
+static bool ranges_overlap(const void *a, size_t abytes, const void *b, size_t bbytes) {
+  const char *x = (const char *)a, *y = (const char *)b;
+  return x < y + bbytes && y < x + abytes;
+}
+
+#define LT_CHECK(x)                \
+  do {                             \
+    const int rc_ = (x);           \
+    if (rc_ != FHE_OK) return rc_; \
+  } while (0)
 
 static int ensure_lt_scratch(fhe_ctx *c, size_t words) {
   if (c->lt_words >= words) return FHE_OK;
@@ -154,7 +220,10 @@ extern "C" int fhe_linear_transform(fhe_ctx *c, const uint32_t *ct, int level, c
   da.out = inner;
   da.nb = baby;
   da.giant = giant;
+  da.nlimb = level;
   da.level = level;
+  da.L = c->L;
+  for (int k = 0; k < baby * giant; k++) da.didx[k] = (int16_t)k;
   {
     TraceScope ts(c->tabs, "diag_mac", s);
     const dim3 grid((unsigned)(level * (N / 256)), (unsigned)((giant + kGsub - 1) / kGsub));
@@ -197,5 +266,182 @@ extern "C" int fhe_linear_transform(fhe_ctx *c, const uint32_t *ct, int level, c
     note_launch();
     if (cudaGetLastError() != cudaSuccess) return fhe_fail(FHE_ECUDA, "fhe_linear_transform: sum kernel");
   }
+  return FHE_OK;
+}
+
+// Double-hoisted baby-step / giant-step transform (the hoisting of the
+// linear-transform literature the paper cites in Section V-C, with ModDown
+// hoisted as well as ModUp):
+//   out = sum_g rot_{giant[g]}( sum_b pt[idx[g][b]] (.) rot_{baby[b]}(ct) ).
+// (1) one ModUp of c1; every baby rotation's inner product stays in the
+//     extended basis Q_l u P, with P sigma_b(c0) folded onto its q-limbs
+//     (IT_IPX); a baby step without rotation is P ct (k_lift);
+// (2) the inner sums are formed in the extended basis (k_diagmac over l + K limbs);
+// (3) per rotating giant step, the c1 half of its inner sum goes down to Q_l
+//     (IT_MDX), is decomposed again (IT_MODUP) and key-switched with sigma_g on the
+//     extended digits (IT_IPX), again without ModDown;
+// (4) k_gsum adds sigma_g of the c0 halves and the key-switch outputs;
+// (5) one ModDown of both halves (IT_MDX).
+extern "C" int fhe_linear_transform_dh(fhe_ctx *c, const uint32_t *ct, int level, const int32_t *baby, int n_baby,
+                                       const int32_t *giant, int n_giant, const uint32_t *diags, int n_diag,
+                                       const int32_t *idx, uint32_t *out, fhe_stream stream) {
+  const char *fn = "fhe_linear_transform_dh";
+  if (!c) return fhe_fail(FHE_EINVAL, "%s: null ctx", fn);
+  if (level < 1 || level > c->L) return fhe_fail(FHE_ELEVEL, "%s: level %d", fn, level);
+  if (!ct || !diags || !out || (((uintptr_t)ct | (uintptr_t)diags | (uintptr_t)out) & 15))
+    return fhe_fail(FHE_EINVAL, "%s: null or misaligned buffer", fn);
+  if (!baby || !giant || !idx) return fhe_fail(FHE_EINVAL, "%s: null rotation or index list", fn);
+  if (n_baby < 1 || n_baby > kMaxBaby || n_giant < 1 || n_giant > kMaxGiant)
+    return fhe_fail(FHE_EINVAL, "%s: n_baby %d (1..%d), n_giant %d (1..%d)", fn, n_baby, kMaxBaby, n_giant, kMaxGiant);
+  if (n_diag < 1 || n_diag > 32767) return fhe_fail(FHE_EINVAL, "%s: n_diag %d outside [1, 32767]", fn, n_diag);
+  for (int k = 0; k < n_baby * n_giant; k++)
+    if (idx[k] < -1 || idx[k] >= n_diag) return fhe_fail(FHE_EINVAL, "%s: idx[%d] = %d outside [-1, %d)", fn, k, idx[k], n_diag);
+  const int K = c->K, n_ext = level + K;
+  const size_t N = c->N, poly = (size_t)level * N, xpoly = (size_t)n_ext * N;
+  if (ranges_overlap(out, 2 * poly * 4, ct, 2 * poly * 4) || ranges_overlap(out, 2 * poly * 4, diags, (size_t)n_diag * xpoly * 4))
+    return fhe_fail(FHE_EALIAS, "%s: output overlaps an input", fn);
+  std::vector<uint32_t> gb(n_baby), gg(n_giant);
+  std::vector<const uint32_t *> kb(n_baby, nullptr), kg(n_giant, nullptr);
+  for (int b = 0; b < n_baby; b++) {
+    gb[b] = fhe_galois_elt(baby[b], c->N);
+    if (gb[b] != 1u && !(kb[b] = c->find_key(baby[b])))
+      return fhe_fail(FHE_ENOKEY, "%s: no rotation key for baby step %d", fn, baby[b]);
+  }
+  for (int g = 0; g < n_giant; g++) {
+    gg[g] = fhe_galois_elt(giant[g], c->N);
+    if (gg[g] != 1u && !(kg[g] = c->find_key(giant[g])))
+      return fhe_fail(FHE_ENOKEY, "%s: no rotation key for giant step %d", fn, giant[g]);
+  }
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->order_stream(s);
+  // scratch: baby rotations, inner sums and giant key switches (extended basis, two
+  // halves each), the giant steps' c1 halves in Q_l, the accumulator
+  const size_t xct = 2 * xpoly;
+  int rc = ensure_lt_scratch(c, xct * ((size_t)n_baby + 2 * n_giant + 1) + poly * n_giant);
+  if (rc != FHE_OK) return rc;
+  uint32_t *bab = c->lt_scratch, *inner = bab + n_baby * xct, *v = inner + n_giant * xct, *acc = v + n_giant * xct,
+           *c1d = acc + xct;
+  const unsigned grid_x = (unsigned)(n_ext * (N / 256));
+
+  // (1) baby steps
+  std::vector<Item> its;
+  for (int b = 0; b < n_baby; b++) {
+    if (gb[b] == 1u) {
+      TraceScope ts(c->tabs, "lt_lift", s);
+      k_lift<<<grid_x, 256, 0, s>>>(ct, bab + b * xct, c->d_pmod, c->d_pc, level, n_ext, c->logn);
+      note_launch();
+      if (cudaGetLastError() != cudaSuccess) return fhe_fail(FHE_ECUDA, "%s: lift kernel", fn);
+      continue;
+    }
+    Item it;
+    it.kind = IT_IPX;
+    it.level = level;
+    it.galois = gb[b];
+    it.in = ct + poly;
+    it.in2 = ct;
+    it.out = bab + b * xct;
+    it.key = kb[b];
+    it.ext_slot = 0;
+    its.push_back(it);
+  }
+  if (!its.empty()) {
+    Item up;
+    up.kind = IT_MODUP;
+    up.level = level;
+    up.in = ct + poly;
+    up.slot = 0;
+    its.insert(its.begin(), up);
+    LT_CHECK(run_items_chunked(c, its, 1, s));
+  }
+
+  // (2) inner sums in the extended basis
+  DiagArgs da;
+  memset(&da, 0, sizeof da);
+  for (int b = 0; b < n_baby; b++) da.babies[b] = bab + b * xct;
+  da.diags = diags;
+  da.out = inner;
+  da.nb = n_baby;
+  da.giant = n_giant;
+  da.nlimb = n_ext;
+  da.level = level;
+  da.L = c->L;
+  for (int k = 0; k < n_baby * n_giant; k++) da.didx[k] = (int16_t)idx[k];
+  {
+    TraceScope ts(c->tabs, "diag_mac", s);
+    const dim3 grid(grid_x, (unsigned)((n_giant + kGsub - 1) / kGsub));
+    k_diagmac<<<grid, 256, 0, s>>>(da, c->d_pc, c->logn);
+    note_launch();
+    if (cudaGetLastError() != cudaSuccess) return fhe_fail(FHE_ECUDA, "%s: diagonal kernel", fn);
+  }
+
+  // (3) rotating giant steps: ModDown of the c1 halves, then ModUp + extended-basis key switch
+  std::vector<int> rg;
+  for (int g = 0; g < n_giant; g++)
+    if (gg[g] != 1u) rg.push_back(g);
+  if (!rg.empty()) {
+    std::vector<Item> md;
+    for (int g : rg) {
+      Item it;
+      it.kind = IT_MDX;
+      it.level = level;
+      it.npoly = 1;
+      it.in = inner + g * xct + xpoly;
+      it.out = c1d + g * poly;
+      md.push_back(it);
+    }
+    LT_CHECK(run_items_chunked(c, md, 1, s));
+    std::vector<Item> ks;
+    const int ng = (int)rg.size();
+    for (int j = 0; j < ng; j++) {
+      Item up;
+      up.kind = IT_MODUP;
+      up.level = level;
+      up.in = c1d + rg[j] * poly;
+      up.slot = 1 + j;
+      ks.push_back(up);
+    }
+    for (int j = 0; j < ng; j++) {
+      const int g = rg[j];
+      Item it;
+      it.kind = IT_IPX;
+      it.level = level;
+      it.galois = gg[g];
+      it.in = c1d + g * poly;
+      it.out = v + g * xct;
+      it.key = kg[g];
+      it.ext_slot = 1 + j;
+      ks.push_back(it);
+    }
+    LT_CHECK(run_items_chunked(c, ks, 1 + ng, s));
+  }
+
+  // (4) giant-step accumulation, (5) one ModDown of both halves
+  GsumArgs ga;
+  memset(&ga, 0, sizeof ga);
+  for (int g = 0; g < n_giant; g++) {
+    ga.inner[g] = inner + g * xct;
+    ga.v[g] = gg[g] != 1u ? v + g * xct : nullptr;
+    ga.galois[g] = gg[g];
+  }
+  ga.out = acc;
+  ga.count = n_giant;
+  ga.nlimb = n_ext;
+  ga.level = level;
+  ga.L = c->L;
+  {
+    TraceScope ts(c->tabs, "lt_gsum", s);
+    k_gsum<<<grid_x, 256, 0, s>>>(ga, c->d_pc, c->logn);
+    note_launch();
+    if (cudaGetLastError() != cudaSuccess) return fhe_fail(FHE_ECUDA, "%s: giant-step sum kernel", fn);
+  }
+  Item fin;
+  fin.kind = IT_MDX;
+  fin.level = level;
+  fin.npoly = 2;
+  fin.in = acc;
+  fin.out = out;
+  std::vector<Item> f{fin};
+  LT_CHECK(run_items_chunked(c, f, 1, s));
   return FHE_OK;
 }

@@ -89,7 +89,10 @@ int run_items_chunked(fhe_ctx *c, const std::vector<Item> &items, int first_slot
     size_t j = i;
     while (j < items.size()) {
       Item it = items[j];
-      if (it.kind != IT_MODUP) it.slot = first_slot + nslot;
+      // an extended-basis inner product needs no workspace of its own: it reads its ModUp's slot
+      const bool own_slot = it.kind != IT_MODUP && it.kind != IT_IPX;
+      if (it.kind == IT_IPX) it.slot = it.ext_slot;
+      if (own_slot) it.slot = first_slot + nslot;
       chunk.push_back(it);
       Program Q;
       const int rc = build_program(c, chunk, c->fused != 0, Q);
@@ -99,7 +102,7 @@ int run_items_chunked(fhe_ctx *c, const std::vector<Item> &items, int first_slot
         break;
       }
       best = std::move(Q);
-      if (it.kind != IT_MODUP) nslot++;
+      if (own_slot) nslot++;
       j++;
     }
     if (chunk.empty()) return fhe_fail(FHE_EINVAL, "internal: one item does not fit the launch arguments");

@@ -100,8 +100,15 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
         k.galois_own = k.galois_ext = k.galois_add = it.galois;
         k.addp = it.in;
         break;
+      case IT_IPX:
+        k.ext = c->slots[it.ext_slot].EXT;
+        k.galois_own = k.galois_ext = k.galois_add = it.galois;
+        k.addp = it.in2;
+        break;
+      case IT_MDX:
+        break;
     }
-    k.own = it.kind == IT_MODDOWN ? it.in + poly : dpoly[i];
+    k.own = it.kind == IT_MODDOWN ? it.in + poly : it.kind == IT_IPX ? it.in : dpoly[i];
     // the plain pipeline gathers the rotated polynomial into TMP first
     if (!fused && it.kind == IT_ROTATE && it.galois != 1u) {
       k.own = S.TMP;
@@ -109,8 +116,9 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
     }
     P.ks.push_back(k);
   }
-  auto has_modup = [](const Item &it) { return it.kind != IT_MODDOWN; };
-  auto has_moddown = [](const Item &it) { return it.kind != IT_MODUP; };
+  auto has_modup = [](const Item &it) { return it.kind != IT_MODDOWN && it.kind != IT_IPX && it.kind != IT_MDX; };
+  auto has_ip = [](const Item &it) { return it.kind != IT_MODUP && it.kind != IT_MDX; };
+  auto has_moddown = [](const Item &it) { return it.kind != IT_MODUP && it.kind != IT_IPX; };
 
   // ---- HMult tensor
   Stage tensor = ew_stage(EW_TENSOR);
@@ -200,23 +208,28 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
   Stage cb = ew_stage(EW_COMBINE);
   for (size_t i = 0; i < items.size(); i++) {
     const Item &it = items[i];
-    if (!has_moddown(it)) continue;
     const fhe_ctx::Slot &S = c->slots[it.slot];
     const int level = it.level, n_ext = level + K;
     const KsArgs &k = P.ks[i];
-    ipq.gather_own |= k.galois_own != 1u;
-    ipq.gather_ext |= k.galois_ext != 1u;
-    Seg a = seg(nullptr, S.U, level, 0, (int)i);
-    a.t0 = 0;
-    a.key_row0 = 0;
-    add(ipq, a);
-    Seg b = seg(nullptr, S.U + (size_t)level * N, K, L, (int)i);
-    b.t0 = level;
-    b.key_row0 = L;
-    add(ipp, b);
-    for (int cc = 0; cc < 2; cc++) {
+    // u: the slot's workspace, the caller's extended-basis output (IPX) or input (MDX)
+    uint32_t *U = it.kind == IT_IPX ? it.out : it.kind == IT_MDX ? const_cast<uint32_t *>(it.in) : S.U;
+    if (has_ip(it)) {
+      ipq.gather_own |= k.galois_own != 1u;
+      ipq.gather_ext |= k.galois_ext != 1u;
+      Seg a = seg(nullptr, U, level, 0, (int)i);
+      a.t0 = 0;
+      a.key_row0 = 0;
+      add(ipq, a);
+      Seg b = seg(nullptr, U + (size_t)level * N, K, L, (int)i);
+      b.t0 = level;
+      b.key_row0 = L;
+      add(ipp, b);
+    }
+    if (!has_moddown(it)) continue;
+    const int npoly = it.kind == IT_MDX ? it.npoly : 2;
+    for (int cc = 0; cc < npoly; cc++) {
       uint32_t *uc = S.UC + (size_t)cc * K * N, *r = S.R + (size_t)cc * level * N;
-      add(m1, seg(S.U + ((size_t)cc * n_ext + level) * N, uc, K, L, (int)i));
+      add(m1, seg(U + ((size_t)cc * n_ext + level) * N, uc, K, L, (int)i));
       Seg x = seg(uc, uc, K, L, (int)i);
       if (fused) x.scale = c->d_md_scale;
       add(m2, x);
@@ -239,10 +252,10 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
       mbc.max_out = std::max(mbc.max_out, level);
       add(r1, seg(r, r, level, 0, (int)i));
       Seg z = fused ? seg(r, it.out + (size_t)cc * level * N, level, 0, (int)i) : seg(r, r, level, 0, (int)i);
-      z.src2 = S.U + (size_t)cc * n_ext * N;
+      z.src2 = U + (size_t)cc * n_ext * N;
       z.c = cc;
       add(r2, z);
-      Seg w = seg(S.U + (size_t)cc * n_ext * N, it.out + (size_t)cc * level * N, level, 0, (int)i);
+      Seg w = seg(U + (size_t)cc * n_ext * N, it.out + (size_t)cc * level * N, level, 0, (int)i);
       w.src2 = r;
       w.c = cc;
       add(cb, w);
@@ -252,7 +265,8 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
   ipp.gather_ext = ipq.gather_ext;
   // complementary pipelining (Section IV-B): the q-limb inner product on an auxiliary
   // branch beside ModDown's special-limb chain; otherwise one launch over all limbs
-  const bool split = fused && c->comp_pipe;
+  const bool has_md = !m1.segs.empty();
+  const bool split = fused && c->comp_pipe && has_md && !ipq.segs.empty();
   if (!ipq.segs.empty()) {
     if (split) {
       P.stages.push_back(marker(Stage::FORK));
@@ -265,6 +279,8 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
       all.segs.insert(all.segs.end(), ipp.segs.begin(), ipp.segs.end());
       P.stages.push_back(all);
     }
+  }
+  if (has_md) {
     P.stages.push_back(m1);
     P.stages.push_back(m2);
     if (!fused) P.stages.push_back(msc);

@@ -8,18 +8,24 @@
 
 #include "ctx.h"
 
-enum ItemKind { IT_KS = 0, IT_ROTATE = 1, IT_RELIN = 2, IT_MODUP = 3, IT_MODDOWN = 4 };
+// IT_IPX: the inner product of a shared ModUp (slot ext_slot, read through sigma_galois) left in
+// the extended basis: out [2][level+K][N] = u, plus P sigma(in2) on the q-limbs of u_0 when in2 is
+// given (double hoisting keeps the rotation in Q_l u P).  IT_MDX: ModDown alone of `npoly`
+// extended-basis polynomials in [npoly][level+K][N] to out [npoly][level][N].
+enum ItemKind { IT_KS = 0, IT_ROTATE = 1, IT_RELIN = 2, IT_MODUP = 3, IT_MODDOWN = 4, IT_IPX = 5, IT_MDX = 6 };
 
 struct Item {
   int kind = IT_KS;
   int level = 0;
   uint32_t galois = 1;             // rotation Galois element (1: none)
-  const uint32_t *in = nullptr;    // KS / MODUP: d [level][N]; ROTATE / MODDOWN: ct [2][level][N]; RELIN: a
-  const uint32_t *in2 = nullptr;   // RELIN: b
+  const uint32_t *in = nullptr;    // KS / MODUP: d [level][N]; ROTATE / MODDOWN: ct [2][level][N]; RELIN: a;
+                                   // IPX: the polynomial that was ModUp'ed [level][N]; MDX: [npoly][level+K][N]
+  const uint32_t *in2 = nullptr;   // RELIN: b; IPX: pass-through c0 [level][N] or null
   uint32_t *out = nullptr;         // [2][level][N] (not for MODUP)
   const uint32_t *key = nullptr;   // switching key (not for MODUP)
   int slot = 0;                    // workspace slot of this item
-  int ext_slot = 0;                // MODDOWN: slot whose EXT holds the shared ModUp output
+  int ext_slot = 0;                // MODDOWN / IPX: slot whose EXT holds the shared ModUp output
+  int npoly = 2;                   // MDX: polynomials brought down (1 or 2)
 };
 
 struct Stage {

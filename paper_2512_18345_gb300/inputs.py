@@ -116,6 +116,15 @@ WORKLOADS: Dict[str, dict] = {
     # the paper's own key-switching shapes (Table "ks-param"): alpha = K = 12
     "paper_ks_N65536_L24_a12": dict(N=1 << 16, L=24, K=12, dnum=2, bits=31, seed=20251224),
     "paper_ks_N65536_L48_a12": dict(N=1 << 16, L=48, K=12, dnum=4, bits=31, seed=20251225),
+    # bootstrapping linear transforms (CoeffToSlot / SlotToCoeff, radix levels, double
+    # hoisting) at the paper's bootstrapping parameters (Table "parameter": N = 2^16,
+    # L <= 48, dnum = 4; alpha = K = 12): CoeffToSlot from the top level, SlotToCoeff
+    # from `stc_level` (the levels in between belong to EvalMod, which is not modelled)
+    "cts_stc_N65536_L48_a12": dict(N=1 << 16, L=48, K=12, dnum=4, bits=31, seed=20251226,
+                                   levels=3, cts_level=48, stc_level=33),
+    # the same transforms on a ring the oracle finishes in seconds
+    "cts_stc_N4096_L8": dict(N=1 << 12, L=8, K=2, dnum=4, bits=30, seed=20251227,
+                             levels=3, cts_level=8, stc_level=5, scale_bits=28),
 }
 
 
@@ -170,3 +179,81 @@ def batch_items(g: np.random.Generator, items: int, level_lo: int, level_hi: int
         rot = rotation_index(g)
         out.append(dict(op=op, level=level, rot=rot))
     return out
+
+
+# ------------------------------------------------------------------ bootstrapping transform structure
+
+def radix_levels(log_slots: int, n_levels: int) -> List[tuple]:
+    """Split the butterfly stages 1..log_slots (stage s has half-width 2^(s-1)) into n_levels
+    consecutive groups, as even as possible, the larger groups first: [(s_lo, s_hi)] ascending."""
+    base, extra = divmod(log_slots, n_levels)
+    out, s = [], 1
+    for i in range(n_levels):
+        r = base + (1 if i < extra else 0)
+        out.append((s, s + r - 1))
+        s += r
+    return out
+
+
+@dataclasses.dataclass(frozen=True)
+class BsgsPlan:
+    """Baby-step / giant-step split of one radix level: the level's diagonal offsets are
+    d * step (mod n) with |d| <= D; offset k = giant[g] + baby[b] is diagonal idx[g][b]
+    (-1: that pair covers no new offset); offsets[j] is diagonal j's offset (mod n)."""
+    step: int
+    baby: tuple
+    giant: tuple
+    idx: tuple
+    offsets: tuple
+
+    @property
+    def n_diag(self) -> int:
+        return len(self.offsets)
+
+    def rotations(self) -> List[int]:
+        return sorted({r for r in self.baby + self.giant if r})
+
+
+def bsgs_plan(n_slots: int, s_lo: int, s_hi: int) -> BsgsPlan:
+    """Offsets of stages s_lo..s_hi multiplied together are sums of e_s 2^(s-1), e_s in
+    {-1, 0, 1}: the multiples d 2^(s_lo - 1), |d| <= D = 2^(s_hi - s_lo + 1) - 1.  Baby steps
+    b step (b < n1, n1 the power of two at or above sqrt(2D + 1)); giant steps (g n1 - c) step
+    with c = n1 ceil(D / n1), so one giant step is the identity; each offset (mod n) goes to
+    the first pair that reaches it, and giant steps that reach none are dropped."""
+    step = 1 << (s_lo - 1)
+    D = (1 << (s_hi - s_lo + 1)) - 1
+    n1 = 1
+    while n1 * n1 < 2 * D + 1:
+        n1 *= 2
+    c = n1 * (-(-D // n1))
+    n2 = (D + c) // n1 + 1
+    seen: Dict[int, int] = {}
+    rows, giants = [], []
+    for g in range(n2):
+        row = []
+        for b in range(n1):
+            d = g * n1 - c + b
+            k = (d * step) % n_slots
+            if abs(d) <= D and k not in seen:
+                seen[k] = len(seen)
+                row.append(seen[k])
+            else:
+                row.append(-1)
+        if any(j >= 0 for j in row):
+            rows.append(tuple(row))
+            giants.append(((g * n1 - c) * step) % n_slots)
+    offsets = tuple(sorted(seen, key=seen.get))
+    return BsgsPlan(step=step, baby=tuple(b * step for b in range(n1)), giant=tuple(giants), idx=tuple(rows),
+                    offsets=offsets)
+
+
+def transform_plans(N: int, n_levels: int, kind: str) -> List[BsgsPlan]:
+    """The levels of CoeffToSlot ("cts": the highest stages first) or SlotToCoeff ("stc":
+    the lowest first), in evaluation order, on n = N/2 slots."""
+    n = N // 2
+    lv = radix_levels(n.bit_length() - 1, n_levels)
+    if kind == "cts":
+        lv = lv[::-1]
+    elif kind != "stc":
+        raise ValueError(kind)
+    return [bsgs_plan(n, lo, hi) for lo, hi in lv]
