@@ -48,9 +48,10 @@ def parse():
     ap.add_argument("--sweep", action="store_true",
                     help="kernel-utilisation sweep (NTT over 10..250 limbs, BConv over output counts, key-switch "
                          "batch sizes) as one JSON line instead of the benchmark line")
-    ap.add_argument("--profile-run", choices=["scalar", "tc"], default=None,
+    ap.add_argument("--profile-run", choices=["scalar", "tc", "cts"], default=None,
                     help="only launch the batched stage programs (one lane, no graph) warmup + steps times, "
-                         "in a fixed launch order for profilers; prints no JSON line")
+                         "in a fixed launch order for profilers ('cts': the CoeffToSlot chain at N = 2^16, "
+                         "L = 48 instead); prints no JSON line")
     return ap.parse_args()
 
 
@@ -286,6 +287,91 @@ def bench_lt(binding, inputs, dev, timed, bconv_mode):
             "kernels_ms": {k2: round(v[1], 4) for k2, v in sorted(stats.items(), key=lambda kv: -kv[1][1])}}
 
 
+def bench_bootstrap_lt(binding, inputs, dev, timed, hbm_peak, only=None, runs=0):
+    """Bootstrapping linear transforms at the paper's bootstrapping parameters (N = 2^16,
+    L = 48, alpha = K = 12, dnum = 4): CoeffToSlot from l = 48 and SlotToCoeff from l = 33,
+    each three radix-32 levels of the special FFT, every level one double-hoisted
+    baby-step / giant-step transform plus a rescale.  Keys, ciphertext and diagonals are
+    uniform residues (timing does not depend on their values; the diagonals and keys are
+    distinct device buffers, so they stream from HBM as real ones would).  With `runs`, the
+    chain `only` names runs that many times untimed (a profiler's target) and nothing is
+    returned."""
+    import numpy as np
+    import torch
+    name = "cts_stc_N65536_L48_a12"
+    w = inputs.WORKLOADS[name]
+    P = inputs.workload_params(name)
+    g = inputs.rng(w["seed"])
+    ctx = binding.Context.from_params(P, device=dev)
+    ctx.set_bconv(binding.FHE_BCONV_SCALAR)  # alpha = 12 exceeds the tensor-core bound
+    key = binding.to_device(rand_key_np(inputs, P, g), dev)
+    tg = torch.Generator(device=f"cuda:{dev}")
+    tg.manual_seed(w["seed"])
+    res = {}
+    for kind, start in (("cts", w["cts_level"]), ("stc", w["stc_level"])):
+        if only and kind != only:
+            continue
+        plans = inputs.transform_plans(P.N, w["levels"], kind)
+        for pl in plans:
+            for r in pl.rotations():
+                ctx.set_rot_key(r, key)  # the context keeps its own copy per rotation
+        levels, pts = [], []
+        for i, pl in enumerate(plans):
+            level = start - i
+            primes = tuple(P.q[:level]) + tuple(P.p)
+            d = torch.empty((pl.n_diag, len(primes), P.N), dtype=torch.int64, device=f"cuda:{dev}")
+            for j, q in enumerate(primes):
+                d[:, j].random_(0, q, generator=tg)
+            pts.append(d.to(torch.int32).contiguous())
+            del d
+            levels.append(level)
+        ct = binding.to_device(np.stack([inputs.uniform_residues(g, P.q[:start], P.N) for _ in range(2)]), dev)
+        outs = [binding.empty((2, lv, P.N), dev) for lv in levels]
+        resc = [binding.empty((2, lv - 1, P.N), dev) for lv in levels]
+
+        def chain():
+            x = ct
+            for pl, lv, pt, o, r in zip(plans, levels, pts, outs, resc):
+                ctx.linear_transform_dh(x, lv, pl.baby, pl.giant, pt, pl.idx, out=o)
+                ctx.rescale(o, lv, out=r)
+                x = r
+
+        if runs:
+            for _ in range(runs):
+                chain()
+            ctx.sync()
+            print(f"profile run: {runs} {kind} chains at N={P.N}, levels {levels}", file=sys.stderr)
+            continue
+        for _ in range(2):
+            chain()
+        k = 5
+        ms = timed(chain, k) / k
+        ctx.sync()
+        ctx.trace(True)
+        chain()
+        stats = ctx.trace_read()
+        ctx.trace(False)
+        n_ks = sum(sum(1 for r in pl.baby if r % (P.N // 2)) + sum(1 for r in pl.giant if r % (P.N // 2))
+                   for pl in plans)
+        diag_bytes = sum(pl.n_diag * (lv + P.K) * P.N * 4 for pl, lv in zip(plans, levels))
+        # the diagonal kernel's algorithmic bytes: each diagonal once, each baby rotation once per
+        # group of 4 giant steps, each inner sum written once (extended basis, both halves)
+        mac_bytes = sum((pl.n_diag + 2 * len(pl.baby) * -(-len(pl.giant) // 4) + 2 * len(pl.giant)) *
+                        (lv + P.K) * P.N * 4 for pl, lv in zip(plans, levels))
+        mac_ms = stats.get("diag_mac", (0, 0.0))[1]
+        res[kind] = {
+            "ms": ms, "levels": levels, "key_switches": n_ks, "ks_per_s": n_ks / (ms / 1e3),
+            "diagonals": [pl.n_diag for pl in plans], "baby_giant": [[len(pl.baby), len(pl.giant)] for pl in plans],
+            "diagonal_bytes": diag_bytes, "hbm_floor_ms": diag_bytes / (hbm_peak * 1e9) * 1e3,
+            "diag_mac": {"bytes": mac_bytes, "ms_traced": mac_ms,
+                         "gbs": mac_bytes / (mac_ms / 1e3) / 1e9 if mac_ms else None,
+                         "frac_of_measured_hbm": (mac_bytes / (mac_ms / 1e3) / 1e9) / hbm_peak if mac_ms else None},
+            "kernels_ms": {k2: round(v[1], 4) for k2, v in sorted(stats.items(), key=lambda kv: -kv[1][1])}}
+        del pts, outs, resc
+    ctx.close()
+    return None if runs else res
+
+
 def bench_paper_shapes(binding, inputs, roofline, dev, timed, steps, l2_gbs, B=8):
     """The paper's key-switching shapes (alpha = K = 12; (l, beta) = (24, 2), (48, 4)):
     B rotations with distinct keys per step, autotuned schedule, one CUDA graph,
@@ -507,6 +593,9 @@ def main():
     build.build_library()
     dev = local
     torch.cuda.set_device(dev)
+    if args.profile_run == "cts":  # the CoeffToSlot chain alone, for a profiler
+        bench_bootstrap_lt(binding, inputs, dev, None, 0.0, only="cts", runs=max(3, args.warmup) + args.steps)
+        return
     P = inputs.workload_params(WORKLOAD)
     level, B = P.L, args.batch
     g = inputs.rng(rank_seed(inputs.WORKLOADS[WORKLOAD]["seed"], rank))
@@ -726,6 +815,7 @@ def main():
         lt["hbm_floor_ms"] = lt["diagonal_bytes"] / (hbm_peak * 1e9) * 1e3
         extra["bsgs_linear_transform_L24"] = lt
         extra["paper_shapes"] = bench_paper_shapes(binding, inputs, roofline, dev, timed, args.steps, l2_gbs)
+        extra["bootstrap_linear_transforms_L48"] = bench_bootstrap_lt(binding, inputs, dev, timed, hbm_peak)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

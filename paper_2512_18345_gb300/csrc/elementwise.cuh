@@ -234,6 +234,9 @@ __global__ void __launch_bounds__(kIpThreads, 2) k_ip_bulk(const __grid_constant
   IpUnit *desc = reinterpret_cast<IpUnit *>(bar + stages);
   __shared__ int s_ok;
 
+  // keys are read exactly once: evict them first, so that ModUp outputs (and the digits shared
+  // by hoisted rotations) stay in L2
+  const uint64_t key_policy = l2_evict_first_policy();
   // thread 0: describe unit u and stream its operands into stage st
   auto issue = [&](int u, int st) {
     int within;
@@ -274,8 +277,8 @@ __global__ void __launch_bounds__(kIpThreads, 2) k_ip_bulk(const __grid_constant
         bulk_g2s(dst + (size_t)(3 * jd) * kIpChunk, e + c0, kIpChunk * 4u, &bar[st]);
       }
       const uint32_t *kp = ks.key + jd * kstride + (size_t)row * N + c0;
-      bulk_g2s(dst + (size_t)(3 * jd + 1) * kIpChunk, kp, kIpChunk * 4u, &bar[st]);
-      bulk_g2s(dst + (size_t)(3 * jd + 2) * kIpChunk, kp + half, kIpChunk * 4u, &bar[st]);
+      bulk_g2s_hint(dst + (size_t)(3 * jd + 1) * kIpChunk, kp, kIpChunk * 4u, &bar[st], key_policy);
+      bulk_g2s_hint(dst + (size_t)(3 * jd + 2) * kIpChunk, kp + half, kIpChunk * 4u, &bar[st], key_policy);
     }
   };
   if (tid == 0) {
@@ -290,6 +293,7 @@ __global__ void __launch_bounds__(kIpThreads, 2) k_ip_bulk(const __grid_constant
   // the gathered own values of a unit are loaded one unit ahead (after the wait
   // that orders the unit's descriptor), so their latency overlaps a unit's work
   constexpr int E = kIpEpt;
+  static_assert(E == 4, "the sigma reads fetch aligned groups of four slots");
   auto gather = [&](const IpUnit &d, uint32_t (&v)[E]) {
     const uint32_t j = d.j0 + tid * E;
 #pragma unroll

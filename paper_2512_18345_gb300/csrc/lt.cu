@@ -34,58 +34,109 @@ struct DiagArgs {
 __device__ __forceinline__ int limb_prime(int i, int level, int L) { return i < level ? i : L + (i - level); }
 
 // out_g[c][i][n] = sum_b diag[didx[g][b]][i][n] babies[b][c][i][n] mod (prime of limb i); one
-// thread per coefficient of one limb and group of kGsub giant steps (blockIdx.y; the groups
-// re-read the baby values from L2); two baby steps' loads are issued before their
-// multiply-accumulates, and the accumulators are reduced after every second baby step
-// (a reduced value plus two 62-bit products stays below 2^64).
+// thread per V consecutive coefficients of one limb (vector loads) and group of kGsub giant
+// steps (blockIdx.y; the groups re-read the baby values); two baby steps' loads are issued
+// before their multiply-accumulates, and the accumulators are reduced after every second
+// baby step (a reduced value plus two 62-bit products stays below 2^64).
 constexpr int kGsub = 4;
+template <int V>
+struct VecU32;
+template <>
+struct VecU32<1> {
+  static __device__ __forceinline__ void load(const uint32_t *p, uint32_t *v) { v[0] = __ldg(p); }
+  static __device__ __forceinline__ void store(uint32_t *p, const uint32_t *v) { p[0] = v[0]; }
+};
+template <>
+struct VecU32<2> {
+  static __device__ __forceinline__ void load(const uint32_t *p, uint32_t *v) {
+    const uint2 w = __ldg(reinterpret_cast<const uint2 *>(p));
+    v[0] = w.x;
+    v[1] = w.y;
+  }
+  static __device__ __forceinline__ void store(uint32_t *p, const uint32_t *v) {
+    *reinterpret_cast<uint2 *>(p) = make_uint2(v[0], v[1]);
+  }
+};
+template <>
+struct VecU32<4> {
+  static __device__ __forceinline__ void load(const uint32_t *p, uint32_t *v) {
+    const uint4 w = __ldg(reinterpret_cast<const uint4 *>(p));
+    v[0] = w.x;
+    v[1] = w.y;
+    v[2] = w.z;
+    v[3] = w.w;
+  }
+  static __device__ __forceinline__ void store(uint32_t *p, const uint32_t *v) {
+    *reinterpret_cast<uint4 *>(p) = make_uint4(v[0], v[1], v[2], v[3]);
+  }
+};
+
+template <int V>
 __global__ void __launch_bounds__(256) k_diagmac(const __grid_constant__ DiagArgs a, const PrimeC *pc, int logn) {
+  using Vec = VecU32<V>;
   const size_t N = (size_t)1 << logn;
-  const int per_limb = (int)(N / 256);
+  const int per_limb = (int)(N / (256 * V));
   const int i = blockIdx.x / per_limb;
-  const size_t n = (size_t)(blockIdx.x % per_limb) * 256 + threadIdx.x;
+  const size_t n = ((size_t)(blockIdx.x % per_limb) * 256 + threadIdx.x) * V;
   const int g0 = blockIdx.y * kGsub, ng = min(kGsub, a.giant - g0);
   const PrimeC P = pc[limb_prime(i, a.level, a.L)];
   const size_t poly = (size_t)a.nlimb * N;
   const uint32_t *dbase = a.diags + (size_t)i * N + n;
-  uint64_t acc[2][kGsub];
+  uint64_t acc[2][kGsub][V];
 #pragma unroll
-  for (int g = 0; g < kGsub; g++) acc[0][g] = acc[1][g] = 0;
+  for (int g = 0; g < kGsub; g++)
+#pragma unroll
+    for (int e = 0; e < V; e++) acc[0][g][e] = acc[1][g][e] = 0;
   for (int b = 0; b < a.nb; b += 2) {
     const bool two = b + 1 < a.nb;
-    uint32_t x[2][2], d[2][kGsub];
+    uint32_t x[2][2][V], d[2][kGsub][V];
 #pragma unroll
     for (int h = 0; h < 2; h++) {
       const int bb = two ? b + h : b;
-      x[h][0] = __ldg(a.babies[bb] + (size_t)i * N + n);
-      x[h][1] = __ldg(a.babies[bb] + poly + (size_t)i * N + n);
+      Vec::load(a.babies[bb] + (size_t)i * N + n, x[h][0]);
+      Vec::load(a.babies[bb] + poly + (size_t)i * N + n, x[h][1]);
 #pragma unroll
       for (int g = 0; g < kGsub; g++) {
         const int k = g < ng ? a.didx[(g0 + g) * a.nb + bb] : -1;
-        d[h][g] = k >= 0 ? __ldg(dbase + (size_t)k * poly) : 0u;
+        if (k >= 0) {
+          Vec::load(dbase + (size_t)k * poly, d[h][g]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < V; e++) d[h][g][e] = 0u;
+        }
       }
     }
 #pragma unroll
     for (int h = 0; h < 2; h++) {
       if (h == 1 && !two) break;
 #pragma unroll
-      for (int g = 0; g < kGsub; g++) {
-        acc[0][g] += (uint64_t)d[h][g] * x[h][0];
-        acc[1][g] += (uint64_t)d[h][g] * x[h][1];
-      }
+      for (int g = 0; g < kGsub; g++)
+#pragma unroll
+        for (int e = 0; e < V; e++) {
+          acc[0][g][e] += (uint64_t)d[h][g][e] * x[h][0][e];
+          acc[1][g][e] += (uint64_t)d[h][g][e] * x[h][1][e];
+        }
     }
 #pragma unroll
-    for (int g = 0; g < kGsub; g++) {
-      acc[0][g] = reduce_u64(acc[0][g], P);
-      acc[1][g] = reduce_u64(acc[1][g], P);
-    }
+    for (int g = 0; g < kGsub; g++)
+#pragma unroll
+      for (int e = 0; e < V; e++) {
+        acc[0][g][e] = reduce_u64(acc[0][g][e], P);
+        acc[1][g][e] = reduce_u64(acc[1][g][e], P);
+      }
   }
 #pragma unroll
   for (int g = 0; g < kGsub; g++)
     if (g < ng)
 #pragma unroll
-      for (int c = 0; c < 2; c++) a.out[((size_t)(g0 + g) * 2 + c) * poly + (size_t)i * N + n] = (uint32_t)acc[c][g];
+      for (int c = 0; c < 2; c++) {
+        uint32_t o[V];
+#pragma unroll
+        for (int e = 0; e < V; e++) o[e] = (uint32_t)acc[c][g][e];
+        Vec::store(a.out + ((size_t)(g0 + g) * 2 + c) * poly + (size_t)i * N + n, o);
+      }
 }
+constexpr int kDiagVec = 2;  // coefficients per thread of the diagonal kernel
 
 // The identity baby step of a double-hoisted transform, in the extended basis:
 // out[c] = P ct[c] on the q-limbs and 0 on the special limbs (ModDown of it returns ct exactly).
@@ -226,8 +277,8 @@ extern "C" int fhe_linear_transform(fhe_ctx *c, const uint32_t *ct, int level, c
   for (int k = 0; k < baby * giant; k++) da.didx[k] = (int16_t)k;
   {
     TraceScope ts(c->tabs, "diag_mac", s);
-    const dim3 grid((unsigned)(level * (N / 256)), (unsigned)((giant + kGsub - 1) / kGsub));
-    k_diagmac<<<grid, 256, 0, s>>>(da, c->d_pc, c->logn);
+    const dim3 grid((unsigned)(level * (N / (256 * kDiagVec))), (unsigned)((giant + kGsub - 1) / kGsub));
+    k_diagmac<kDiagVec><<<grid, 256, 0, s>>>(da, c->d_pc, c->logn);
     note_launch();
     if (cudaGetLastError() != cudaSuccess) return fhe_fail(FHE_ECUDA, "fhe_linear_transform: diagonal kernel");
   }
@@ -369,8 +420,8 @@ extern "C" int fhe_linear_transform_dh(fhe_ctx *c, const uint32_t *ct, int level
   for (int k = 0; k < n_baby * n_giant; k++) da.didx[k] = (int16_t)idx[k];
   {
     TraceScope ts(c->tabs, "diag_mac", s);
-    const dim3 grid(grid_x, (unsigned)((n_giant + kGsub - 1) / kGsub));
-    k_diagmac<<<grid, 256, 0, s>>>(da, c->d_pc, c->logn);
+    const dim3 grid((unsigned)(n_ext * (N / (256 * kDiagVec))), (unsigned)((n_giant + kGsub - 1) / kGsub));
+    k_diagmac<kDiagVec><<<grid, 256, 0, s>>>(da, c->d_pc, c->logn);
     note_launch();
     if (cudaGetLastError() != cudaSuccess) return fhe_fail(FHE_ECUDA, "%s: diagonal kernel", fn);
   }

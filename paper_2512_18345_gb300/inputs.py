@@ -214,17 +214,24 @@ class BsgsPlan:
         return sorted({r for r in self.baby + self.giant if r})
 
 
-def bsgs_plan(n_slots: int, s_lo: int, s_hi: int) -> BsgsPlan:
+def bsgs_plan(n_slots: int, s_lo: int, s_hi: int, giant_cost: float = 3.0) -> BsgsPlan:
     """Offsets of stages s_lo..s_hi multiplied together are sums of e_s 2^(s-1), e_s in
     {-1, 0, 1}: the multiples d 2^(s_lo - 1), |d| <= D = 2^(s_hi - s_lo + 1) - 1.  Baby steps
-    b step (b < n1, n1 the power of two at or above sqrt(2D + 1)); giant steps (g n1 - c) step
-    with c = n1 ceil(D / n1), so one giant step is the identity; each offset (mod n) goes to
-    the first pair that reaches it, and giant steps that reach none are dropped."""
+    b step (b < n1); giant steps (g n1 - c) step with c = n1 ceil(D / n1), so one giant step is
+    the identity; each offset (mod n) goes to the first pair that reaches it, and giant steps
+    that reach none are dropped.  n1 is the power of two (at most 32) that minimises
+    (n1 - 1) + giant_cost (ceil((2D + 1) / n1) - 1): with double hoisting a baby step costs one
+    inner product, a giant step a ModDown, a ModUp and an inner product."""
     step = 1 << (s_lo - 1)
     D = (1 << (s_hi - s_lo + 1)) - 1
-    n1 = 1
-    while n1 * n1 < 2 * D + 1:
-        n1 *= 2
+    count = min(2 * D + 1, n_slots)
+    n1, best = 1, None
+    c1 = 1
+    while c1 <= min(32, 2 * count):
+        cost = (c1 - 1) + giant_cost * (-(-count // c1) - 1)
+        if best is None or cost < best:
+            n1, best = c1, cost
+        c1 *= 2
     c = n1 * (-(-D // n1))
     n2 = (D + c) // n1 + 1
     seen: Dict[int, int] = {}

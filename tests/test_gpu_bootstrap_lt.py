@@ -121,8 +121,9 @@ def test_chain_small_ring_bit_exact_and_decodes(fhe_lib):
 @pytest.mark.parametrize("kind,which,level_key", [("cts", 0, "cts_level"), ("stc", 1, "stc_level")])
 def test_level_parity_bootstrapping_shape(fhe_lib, kind, which, level_key):
     """N = 2^16, L = 48, K = 12, dnum = 4: the first CoeffToSlot level at l = 48 (32 diagonals,
-    7 baby and 3 rotating giant steps) and the middle SlotToCoeff level at l = 33 (63 diagonals,
-    7 + 7); CUDA-core BConv (the tensor-core kernel takes at most 8 input limbs)."""
+    15 rotating baby steps and one rotating giant step) and the middle SlotToCoeff level at
+    l = 33 (63 diagonals, 15 + 3); CUDA-core BConv (the tensor-core kernel takes at most 8
+    input limbs)."""
     from paper_2512_18345_gb300 import binding
     name = "cts_stc_N65536_L48_a12"
     P = inputs.workload_params(name)
