@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the 64-item batch and linear-transform lines")
     ap.add_argument("--lanes", type=int, default=0, help="concurrent lanes of the batched plans (0: library default)")
+    ap.add_argument("--ntt", choices=["auto", "0", "1", "2", "3"], default="auto",
+                    help="NTT kernel variant (fhe_ctx_set_ntt flags: 1 on-the-fly twiddles, 2 single pass); "
+                         "auto: measured by the autotuner")
     ap.add_argument("--l2-budget-mb", type=int, default=0,
                     help="L2 budget that sizes a plan's item groups, in MB (0: library default)")
     ap.add_argument("--sweep", action="store_true",
@@ -628,6 +631,8 @@ def main():
         ctx.set_fused(True)
         ctx.set_bconv(binding.FHE_BCONV_TC if args.profile_run == "tc" else binding.FHE_BCONV_SCALAR)
         ctx.set_batch(0, 0, 1)
+        if args.ntt != "auto":
+            ctx.set_ntt(int(args.ntt))
         plan_p = ctx.batch_plan(items, 0)
         for _ in range(args.warmup + args.steps):
             plan_p.launch()
@@ -662,7 +667,9 @@ def main():
         ctx.set_batch(args.l2_budget_mb << 20, 0, args.lanes)
     else:
         ctx.set_bconv(binding.FHE_BCONV_TC)
-        tune = ctx.autotune(level, B)
+        tune = ctx.autotune(level, B, binding.FHE_TUNE_NTT if args.ntt == "auto" else 0)
+    if args.ntt != "auto":
+        ctx.set_ntt(int(args.ntt))
     budget = tune["l2_budget_bytes"] if tune else args.l2_budget_mb << 20
     # --- batched fused pipeline in one CUDA graph, CUDA-core base conversion (comparison)
     ctx.set_bconv(binding.FHE_BCONV_SCALAR)

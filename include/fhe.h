@@ -130,6 +130,20 @@ FHE_API int fhe_ctx_set_fused(fhe_ctx *ctx, int fused);
  * auxiliary branch beside ModDown's special-limb chain; without it, one launch
  * covers all limbs.  Results are identical either way; fhe_autotune sets it. */
 FHE_API int fhe_ctx_set_pipelining(fhe_ctx *ctx, int on);
+/* NTT kernel variants (flags; 0 = the two-pass kernels, the default):
+ *   FHE_NTT_OTF: the block passes (the last eight stages, the paper's second
+ *     NTT kernel, Section III-A) form most of their register twiddles on the fly
+ *     from one loaded twiddle and a staged 8-entry table instead of loading each;
+ *   FHE_NTT_SINGLE_PASS: each 2^16-point transform of a stage program runs as
+ *     one launch with a cluster of 16 CTAs per limb, the first pass's tiles
+ *     staying in shared memory for the second (no global round trip).
+ * Results are identical in every mode.  Programs and plans built after the call
+ * use the new mode.  FHE_EUNSUPPORTED for FHE_NTT_SINGLE_PASS at N != 2^16 or on
+ * a device that cannot hold a 16-CTA cluster of the kernel; FHE_EINVAL for
+ * unknown flags.  fhe_autotune with FHE_TUNE_NTT measures the modes. */
+#define FHE_NTT_OTF 1
+#define FHE_NTT_SINGLE_PASS 2
+FHE_API int fhe_ctx_set_ntt(fhe_ctx *ctx, int flags);
 
 /*
  * Switching keys ([dnum][2][L + K][N] uint32, NTT form, host or device
@@ -308,6 +322,7 @@ FHE_API int fhe_ctx_set_batch(fhe_ctx *ctx, size_t l2_budget_bytes, int max_grou
  * context's settings are then left as they were).
  */
 #define FHE_TUNE_BCONV 1 /* also choose between the CUDA-core and tensor-core BConv */
+#define FHE_TUNE_NTT 2   /* then also measure the NTT variants (fhe_ctx_set_ntt) under the chosen schedule */
 typedef struct {
   int lanes;              /* chosen lane count */
   size_t l2_budget_bytes; /* chosen group budget */
@@ -319,6 +334,7 @@ typedef struct {
   int candidates;         /* distinct schedules measured */
   int ip_ctas_per_sm;     /* chosen residency of the streaming inner product */
   int comp_pipe;          /* 1: complementary pipelining (q-limb inner product on its own branch) */
+  int ntt_mode;           /* chosen fhe_ctx_set_ntt flags (with FHE_TUNE_NTT; else the context's) */
 } fhe_tune_result;
 FHE_API int fhe_autotune(fhe_ctx *ctx, int level, int n_items, int flags, fhe_tune_result *out, fhe_stream stream);
 /*

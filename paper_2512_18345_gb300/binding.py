@@ -24,6 +24,8 @@ FHE_BCONV_SCALAR, FHE_BCONV_TC = 0, 1
 FHE_OP_KS, FHE_OP_ROTATE, FHE_OP_RELIN = 0, 1, 2
 FHE_PLAN_GRAPH = 1
 FHE_TUNE_BCONV = 1
+FHE_TUNE_NTT = 2
+FHE_NTT_OTF, FHE_NTT_SINGLE_PASS = 1, 2
 
 # every entry point declared in include/fhe.h
 EXPORTS = (
@@ -32,7 +34,7 @@ EXPORTS = (
     "fhe_rotate_hoisted", "fhe_linear_transform", "fhe_linear_transform_dh", "fhe_pmult", "fhe_add", "fhe_ntt", "fhe_intt", "fhe_modup", "fhe_moddown",
     "fhe_bconv", "fhe_batch_plan", "fhe_batch_launch", "fhe_plan_destroy", "fhe_plan_kernel_count",
     "fhe_plan_groups", "fhe_ctx_set_batch",
-    "fhe_trace_enable", "fhe_trace_read", "fhe_probe_bandwidth", "fhe_autotune", "fhe_autotune_cached", "fhe_ctx_set_pipelining", "fhe_selftest_wait_timeout", "fhe_bconv_noalloc", "fhe_last_error",
+    "fhe_trace_enable", "fhe_trace_read", "fhe_probe_bandwidth", "fhe_autotune", "fhe_autotune_cached", "fhe_ctx_set_pipelining", "fhe_ctx_set_ntt", "fhe_selftest_wait_timeout", "fhe_bconv_noalloc", "fhe_last_error",
 )
 
 
@@ -58,7 +60,7 @@ class TuneResult(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_int), ("l2_budget_bytes", ctypes.c_size_t), ("max_group", ctypes.c_int),
                 ("bconv_mode", ctypes.c_int), ("n_groups", ctypes.c_int), ("us_per_ks", ctypes.c_double),
                 ("default_us_per_ks", ctypes.c_double), ("candidates", ctypes.c_int),
-                ("ip_ctas_per_sm", ctypes.c_int), ("comp_pipe", ctypes.c_int)]
+                ("ip_ctas_per_sm", ctypes.c_int), ("comp_pipe", ctypes.c_int), ("ntt_mode", ctypes.c_int)]
 
 
 class KsItem(ctypes.Structure):
@@ -121,6 +123,7 @@ def lib() -> ctypes.CDLL:
         "fhe_ctx_set_batch": [vp, ctypes.c_size_t, ctypes.c_int, ctypes.c_int],
         "fhe_selftest_wait_timeout": [vp, vp],
         "fhe_ctx_set_pipelining": [vp, ctypes.c_int],
+        "fhe_ctx_set_ntt": [vp, ctypes.c_int],
         "fhe_autotune": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(TuneResult), vp],
         "fhe_autotune_cached": [vp, ctypes.c_char_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                 ctypes.POINTER(TuneResult), vp],
@@ -281,6 +284,10 @@ class Context:
         else:
             check(lib().fhe_autotune(self.h, level, n_items, flags, ctypes.byref(r), _stream(stream)))
         return {f: getattr(r, f) for f, _ in TuneResult._fields_}
+
+    def set_ntt(self, flags: int) -> None:
+        """NTT kernel variants: 0, FHE_NTT_OTF, FHE_NTT_SINGLE_PASS or both."""
+        check(lib().fhe_ctx_set_ntt(self.h, int(flags)))
 
     def set_pipelining(self, on: bool) -> None:
         check(lib().fhe_ctx_set_pipelining(self.h, 1 if on else 0))

@@ -40,7 +40,7 @@ extern "C" int fhe_autotune(fhe_ctx *c, int level, int n_items, int flags, fhe_t
   if (!c || !out) return fhe_fail(FHE_EINVAL, "fhe_autotune: null argument");
   if (level < 1 || level > c->L) return fhe_fail(FHE_ELEVEL, "fhe_autotune: level %d", level);
   if (n_items < 1 || n_items > 64) return fhe_fail(FHE_EINVAL, "fhe_autotune: n_items %d (1..64)", n_items);
-  if (flags & ~FHE_TUNE_BCONV) return fhe_fail(FHE_EINVAL, "fhe_autotune: flags %d", flags);
+  if (flags & ~(FHE_TUNE_BCONV | FHE_TUNE_NTT)) return fhe_fail(FHE_EINVAL, "fhe_autotune: flags %d", flags);
   cudaSetDevice(c->device);
   cudaStream_t s = (cudaStream_t)stream;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -102,9 +102,24 @@ extern "C" int fhe_autotune(fhe_ctx *c, int level, int n_items, int flags, fhe_t
   best.us_per_ks = 1e30;
   int rc = FHE_OK, tried = 0;
   const int saved_ip = c->tabs.ip_ctas_per_sm, saved_comp = c->comp_pipe;
+  const int saved_ntt = (c->tabs.ntt_otf ? FHE_NTT_OTF : 0) | (c->tabs.ntt_single ? FHE_NTT_SINGLE_PASS : 0);
   fhe_tune_result by_ip[2];  // fastest schedule with one / two inner-product CTAs per SM
   memset(by_ip, 0, sizeof by_ip);
   by_ip[0].us_per_ks = by_ip[1].us_per_ks = 1e30;
+  // time a graph plan of the items: two warm-up launches, then five
+  auto measure = [&](fhe_plan *p, double &us) -> int {
+    const int reps = 5;
+    int r = FHE_OK;
+    for (int w = 0; w < 2 && r == FHE_OK; w++) r = fhe_batch_launch(p, stream);
+    cudaEventRecord(e0, s);
+    for (int k = 0; k < reps && r == FHE_OK; k++) r = fhe_batch_launch(p, stream);
+    cudaEventRecord(e1, s);
+    float ms = 0.f;
+    if (r == FHE_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      r = fhe_fail(FHE_ECUDA, "fhe_autotune: timing");
+    us = 1e3 * ms / (reps * n_items);
+    return r;
+  };
   for (int mode : modes)
     for (int comp = 0; comp <= 1; comp++)
     for (int ipc = 1; ipc <= 2; ipc++)
@@ -131,18 +146,11 @@ extern "C" int fhe_autotune(fhe_ctx *c, int level, int n_items, int flags, fhe_t
           fhe_plan_destroy(p);
           continue;
         }
-        const int reps = 5;
-        for (int w = 0; w < 2 && rc == FHE_OK; w++) rc = fhe_batch_launch(p, stream);
-        cudaEventRecord(e0, s);
-        for (int r = 0; r < reps && rc == FHE_OK; r++) rc = fhe_batch_launch(p, stream);
-        cudaEventRecord(e1, s);
-        float ms = 0.f;
-        if (rc == FHE_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-          rc = fhe_fail(FHE_ECUDA, "fhe_autotune: timing");
+        double us = 0;
+        rc = measure(p, us);
         fhe_plan_destroy(p);
         if (rc != FHE_OK) break;
         tried++;
-        const double us = 1e3 * ms / (reps * n_items);
         seen[key] = us;
         if (is_default) best.default_us_per_ks = us;
         fhe_tune_result &b = by_ip[ipc - 1];
@@ -164,6 +172,36 @@ extern "C" int fhe_autotune(fhe_ctx *c, int level, int n_items, int flags, fhe_t
     best = by_ip[0].us_per_ks < 0.98 * by_ip[1].us_per_ks ? by_ip[0] : by_ip[1];
     best.default_us_per_ks = dflt;
   }
+  best.ntt_mode = saved_ntt;
+  // the NTT variants under the chosen schedule: another mode only when it is faster by more
+  // than the timing noise (1 %)
+  if (rc == FHE_OK && tried > 0 && (flags & FHE_TUNE_NTT)) {
+    c->batch_budget = best.l2_budget_bytes;
+    c->batch_lanes = best.lanes;
+    c->batch_max_group = best.max_group;
+    c->bconv_mode = best.bconv_mode;
+    c->tabs.ip_ctas_per_sm = best.ip_ctas_per_sm;
+    c->comp_pipe = best.comp_pipe;
+    const double base = best.us_per_ks;
+    for (int m : {0, FHE_NTT_OTF, FHE_NTT_SINGLE_PASS, FHE_NTT_SINGLE_PASS | FHE_NTT_OTF}) {
+      if (m == saved_ntt || fhe_ctx_set_ntt(c, m) != FHE_OK) continue;
+      fhe_plan *p = nullptr;
+      rc = fhe_batch_plan(c, items.data(), n_items, FHE_PLAN_GRAPH, &p);
+      if (rc != FHE_OK) break;
+      int ng = fhe_plan_groups(p, nullptr, 0);
+      double us = 0;
+      rc = measure(p, us);
+      fhe_plan_destroy(p);
+      if (rc != FHE_OK) break;
+      tried++;
+      if (us < 0.99 * base && us < best.us_per_ks) {
+        best.us_per_ks = us;
+        best.ntt_mode = m;
+        best.n_groups = ng;
+      }
+    }
+    fhe_ctx_set_ntt(c, saved_ntt);
+  }
   if (rc == FHE_OK) rc = fhe_ctx_sync(c);  // an expired bounded device wait voids the timings
   if (rc == FHE_OK && tried > 0) {
     best.candidates = tried;
@@ -173,10 +211,12 @@ extern "C" int fhe_autotune(fhe_ctx *c, int level, int n_items, int flags, fhe_t
     c->bconv_mode = best.bconv_mode;
     c->tabs.ip_ctas_per_sm = best.ip_ctas_per_sm;
     c->comp_pipe = best.comp_pipe;
+    fhe_ctx_set_ntt(c, best.ntt_mode);
     *out = best;
   } else {
     c->tabs.ip_ctas_per_sm = saved_ip;
     c->comp_pipe = saved_comp;
+    fhe_ctx_set_ntt(c, saved_ntt);
     c->batch_budget = saved_budget;
     c->batch_lanes = saved_lanes;
     c->batch_max_group = saved_group;
@@ -206,10 +246,11 @@ static bool tune_parse(const char *rest, fhe_tune_result *r) {
   fhe_tune_result t;
   memset(&t, 0, sizeof t);
   unsigned long long budget = 0;
-  if (sscanf(rest, " lanes=%d budget=%llu group=%d bconv=%d ip=%d comp=%d us=%lf", &t.lanes, &budget, &t.max_group,
-             &t.bconv_mode, &t.ip_ctas_per_sm, &t.comp_pipe, &t.us_per_ks) != 7)
+  if (sscanf(rest, " lanes=%d budget=%llu group=%d bconv=%d ip=%d comp=%d ntt=%d us=%lf", &t.lanes, &budget,
+             &t.max_group, &t.bconv_mode, &t.ip_ctas_per_sm, &t.comp_pipe, &t.ntt_mode, &t.us_per_ks) != 8)
     return false;
   if (t.comp_pipe != 0 && t.comp_pipe != 1) return false;
+  if (t.ntt_mode & ~(FHE_NTT_OTF | FHE_NTT_SINGLE_PASS)) return false;
   if (t.lanes < 1 || t.lanes > 4 || t.ip_ctas_per_sm < 1 || t.ip_ctas_per_sm > 2 ||
       (t.bconv_mode != FHE_BCONV_SCALAR && t.bconv_mode != FHE_BCONV_TC) || t.max_group < 0)
     return false;
@@ -247,6 +288,7 @@ extern "C" int fhe_autotune_cached(fhe_ctx *c, const char *path, int level, int 
     c->bconv_mode = hit.bconv_mode;
     c->tabs.ip_ctas_per_sm = hit.ip_ctas_per_sm;
     c->comp_pipe = hit.comp_pipe;
+    if (fhe_ctx_set_ntt(c, hit.ntt_mode) != FHE_OK) hit.ntt_mode = 0, fhe_ctx_set_ntt(c, 0);
     hit.candidates = 0;  // served from the cache
     *out = hit;
     return FHE_OK;
@@ -254,9 +296,10 @@ extern "C" int fhe_autotune_cached(fhe_ctx *c, const char *path, int level, int 
   int rc = fhe_autotune(c, level, n_items, flags, out, stream);
   if (rc != FHE_OK) return rc;
   char line[1024];
-  const int len = snprintf(line, sizeof line, "%s | lanes=%d budget=%llu group=%d bconv=%d ip=%d comp=%d us=%.3f\n",
-                           key.c_str(), out->lanes, (unsigned long long)out->l2_budget_bytes, out->max_group,
-                           out->bconv_mode, out->ip_ctas_per_sm, out->comp_pipe, out->us_per_ks);
+  const int len = snprintf(line, sizeof line,
+                           "%s | lanes=%d budget=%llu group=%d bconv=%d ip=%d comp=%d ntt=%d us=%.3f\n", key.c_str(),
+                           out->lanes, (unsigned long long)out->l2_budget_bytes, out->max_group, out->bconv_mode,
+                           out->ip_ctas_per_sm, out->comp_pipe, out->ntt_mode, out->us_per_ks);
   FILE *f = fopen(path, "a");
   if (!f) return fhe_fail(FHE_EINVAL, "fhe_autotune_cached: cannot append to %s", path);
   const bool ok = fwrite(line, 1, (size_t)len, f) == (size_t)len;  // one write per entry

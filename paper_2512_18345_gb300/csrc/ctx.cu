@@ -254,6 +254,8 @@ static int build_tables(fhe_ctx *c) {
   c->tabs.logn = c->logn;
   c->tabs.tracer = nullptr;
   c->tabs.ip_ctas_per_sm = 2;
+  c->tabs.ntt_otf = 0;
+  c->tabs.ntt_single = 0;
   c->tabs.status = c->d_status;
   return FHE_OK;
 }
@@ -497,6 +499,20 @@ extern "C" int fhe_ctx_sync(fhe_ctx *c) {
 extern "C" int fhe_ctx_set_pipelining(fhe_ctx *c, int on) {
   if (!c) return fhe_fail(FHE_EINVAL, "fhe_ctx_set_pipelining: null");
   c->comp_pipe = on ? 1 : 0;
+  return FHE_OK;
+}
+
+extern "C" int fhe_ctx_set_ntt(fhe_ctx *c, int flags) {
+  if (!c) return fhe_fail(FHE_EINVAL, "fhe_ctx_set_ntt: null");
+  if (flags & ~(FHE_NTT_OTF | FHE_NTT_SINGLE_PASS)) return fhe_fail(FHE_EINVAL, "fhe_ctx_set_ntt: flags 0x%x", flags);
+  if (flags & FHE_NTT_SINGLE_PASS) {
+    if (c->logn != 16) return fhe_fail(FHE_EUNSUPPORTED, "fhe_ctx_set_ntt: the single-pass NTT needs N = 2^16");
+    cudaSetDevice(c->device);
+    if (fhe::ntt_single_pass_clusters() < 1)
+      return fhe_fail(FHE_EUNSUPPORTED, "fhe_ctx_set_ntt: no 16-CTA cluster of the single-pass NTT fits this device");
+  }
+  c->tabs.ntt_otf = (flags & FHE_NTT_OTF) ? 1 : 0;
+  c->tabs.ntt_single = (flags & FHE_NTT_SINGLE_PASS) ? 1 : 0;
   return FHE_OK;
 }
 

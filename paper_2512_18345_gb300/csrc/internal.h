@@ -35,6 +35,8 @@ struct DevTables {
   Tracer *tracer;          // null: no tracing
   unsigned int *status;    // device word: bit 0 set when a bounded device-side wait expired
   int ip_ctas_per_sm;      // resident CTAs per SM of the streaming inner product (1 or 2; autotuned)
+  int ntt_otf;             // block passes form their register twiddles on the fly
+  int ntt_single;          // 2^16-point transforms in one cluster launch instead of two passes
 };
 
 // bracket one launch with trace events when tracing is on
@@ -59,6 +61,13 @@ cudaError_t launch_ntt_pass(const DevTables &t, bool column, bool fwd, int pro, 
 // inverse = block (pro, lazy) then column (plain, epi).  In place after the first pass (dst of sl).
 cudaError_t launch_ntt(const DevTables &t, bool fwd, int pro, int epi, const SegList &first, const SegList &second,
                        cudaStream_t s);
+// Both passes in one cluster launch (first / second enumerate the same limbs); only for the
+// (pro, epi) pairs ntt_single_pass_ok accepts, at N = 2^16.
+bool ntt_single_pass_ok(const DevTables &t, int pro, int epi, bool fwd);
+cudaError_t launch_ntt_single(const DevTables &t, bool fwd, int pro, int epi, const SegList &first,
+                              const SegList &second, cudaStream_t s);
+// how many 16-CTA clusters of the single-pass NTT the current device holds at once (0: none)
+int ntt_single_pass_clusters();
 cudaError_t launch_bconv(const DevTables &t, const BconvArgs &a, int max_in, int max_out, cudaStream_t s);
 cudaError_t launch_bconv_tc(const DevTables &t, const BconvArgs &a, int max_in, int max_out, cudaStream_t s);
 cudaError_t launch_ew(const DevTables &t, int op, const SegList &sl, cudaStream_t s);

@@ -33,20 +33,21 @@ Tracer::~Tracer() {
 
 void note_launch() { g_launches++; }
 
-template <int LOGN, bool COLUMN, bool FWD, int PRO, int EPI>
+template <int LOGN, bool COLUMN, bool FWD, int PRO, int EPI, bool OTF>
 static const char *ntt_name() {
   static const char *pro[] = {"", "+gather", "+reduce"};
   static const char *epi[] = {"", "", "+scale", "+combine", "+rescale"};
   static char buf[64];
   static bool init = false;
   if (!init) {
-    snprintf(buf, sizeof buf, "%s_%s%s%s", FWD ? "ntt" : "intt", COLUMN ? "col" : "blk", pro[PRO], epi[EPI]);
+    snprintf(buf, sizeof buf, "%s_%s%s%s%s", FWD ? "ntt" : "intt", COLUMN ? "col" : "blk", pro[PRO], epi[EPI],
+             OTF ? "+otf" : "");
     init = true;
   }
   return buf;
 }
 
-template <int LOGN, bool COLUMN, bool FWD, int PRO, int EPI>
+template <int LOGN, bool COLUMN, bool FWD, int PRO, int EPI, bool OTF>
 static cudaError_t ntt_go(const DevTables &t, const SegList &sl, cudaStream_t s) {
   using G = NttGeom<LOGN, COLUMN>;
   const unsigned grid = (unsigned)(sl.total * G::TILES);
@@ -54,23 +55,30 @@ static cudaError_t ntt_go(const DevTables &t, const SegList &sl, cudaStream_t s)
   constexpr int smem = ntt_twiddle_smem(COLUMN, G::S);
   static bool configured = false;  // opt in to > 48 KB of shared memory once per instantiation
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_ntt<LOGN, COLUMN, FWD, PRO, EPI>,
+    cudaError_t e = cudaFuncSetAttribute(k_ntt<LOGN, COLUMN, FWD, PRO, EPI, OTF>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  TraceScope ts(t, ntt_name<LOGN, COLUMN, FWD, PRO, EPI>(), s);
-  k_ntt<LOGN, COLUMN, FWD, PRO, EPI><<<grid, kNttThreads, smem, s>>>(sl, t.ntt);
+  TraceScope ts(t, ntt_name<LOGN, COLUMN, FWD, PRO, EPI, OTF>(), s);
+  k_ntt<LOGN, COLUMN, FWD, PRO, EPI, OTF><<<grid, kNttThreads, smem, s>>>(sl, t.ntt);
   g_launches++;
   return cudaGetLastError();
 }
 
-// The (column, fwd, pro, epi) combinations the library uses.
+// The (column, fwd, pro, epi) combinations the library uses; on-the-fly twiddles apply to
+// the block passes.
 template <int LOGN>
 static cudaError_t ntt_dispatch(const DevTables &t, bool column, bool fwd, int pro, int epi, const SegList &sl,
                                 cudaStream_t s) {
-#define NTT_CASE(COL, FWDV, P, E) \
-  if (column == COL && fwd == FWDV && pro == P && epi == E) return ntt_go<LOGN, COL, FWDV, P, E>(t, sl, s);
+  const bool otf = t.ntt_otf != 0;
+#define NTT_CASE(COL, FWDV, P, E)                                                              \
+  if (column == COL && fwd == FWDV && pro == P && epi == E) {                                  \
+    if constexpr (!COL) {                                                                      \
+      if (otf) return ntt_go<LOGN, COL, FWDV, P, E, true>(t, sl, s);                           \
+    }                                                                                          \
+    return ntt_go<LOGN, COL, FWDV, P, E, false>(t, sl, s);                                     \
+  }
   NTT_CASE(true, true, PRO_PLAIN, EPI_LAZY)
   NTT_CASE(true, true, PRO_REDUCE, EPI_LAZY)
   NTT_CASE(false, true, PRO_PLAIN, EPI_PLAIN)
@@ -92,8 +100,78 @@ cudaError_t launch_ntt_pass(const DevTables &t, bool column, bool fwd, int pro, 
   }
 }
 
+template <bool FWD, int PRO, int EPI, bool OTF>
+static cudaError_t ntt1_go(const DevTables &t, const SegList &first, const SegList &second, cudaStream_t s) {
+  const unsigned grid = (unsigned)(first.total * 16);
+  if (grid == 0) return cudaSuccess;
+  constexpr int smem = ntt_twiddle_smem(true, 256);  // the larger of the two passes' tables
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_ntt1<FWD, PRO, EPI, OTF>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  static const char *name = FWD ? (OTF ? "ntt1+otf" : "ntt1") : (OTF ? "intt1+otf" : "intt1");
+  TraceScope ts(t, name, s);
+  k_ntt1<FWD, PRO, EPI, OTF><<<grid, kNttThreads, smem, s>>>(first, second, t.ntt);
+  g_launches++;
+  return cudaGetLastError();
+}
+
+int ntt_single_pass_clusters() {
+  auto kern = k_ntt1<true, PRO_PLAIN, EPI_PLAIN, false>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) return 0;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = 16;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.gridDim = dim3(16 * 64);
+  cfg.blockDim = dim3(kNttThreads);
+  cfg.dynamicSmemBytes = ntt_twiddle_smem(true, 256);
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+bool ntt_single_pass_ok(const DevTables &t, int pro, int epi, bool fwd) {
+  if (t.logn != 16) return false;
+  if (fwd) return (pro == PRO_PLAIN && (epi == EPI_PLAIN || epi == EPI_COMBINE)) || (pro == PRO_REDUCE && epi == EPI_RESCALE);
+  return (pro == PRO_PLAIN || pro == PRO_GATHER) && epi == EPI_SCALE;
+}
+
+cudaError_t launch_ntt_single(const DevTables &t, bool fwd, int pro, int epi, const SegList &first,
+                              const SegList &second, cudaStream_t s) {
+  const bool otf = t.ntt_otf != 0;
+#define NTT1_CASE(FWDV, P, E)                                                  \
+  if (fwd == FWDV && pro == P && epi == E)                                     \
+    return otf ? ntt1_go<FWDV, P, E, true>(t, first, second, s) : ntt1_go<FWDV, P, E, false>(t, first, second, s);
+  NTT1_CASE(true, PRO_PLAIN, EPI_PLAIN)
+  NTT1_CASE(true, PRO_PLAIN, EPI_COMBINE)
+  NTT1_CASE(true, PRO_REDUCE, EPI_RESCALE)
+  NTT1_CASE(false, PRO_PLAIN, EPI_SCALE)
+  NTT1_CASE(false, PRO_GATHER, EPI_SCALE)
+#undef NTT1_CASE
+  return cudaErrorInvalidValue;
+}
+
+static bool same_limbs(const SegList &a, const SegList &b) {
+  if (a.dev || b.dev || a.nseg != b.nseg || a.total != b.total) return false;
+  for (int i = 0; i < a.nseg; i++)
+    if (a.seg[i].n != b.seg[i].n || a.seg[i].prime != b.seg[i].prime) return false;
+  return true;
+}
+
 cudaError_t launch_ntt(const DevTables &t, bool fwd, int pro, int epi, const SegList &first, const SegList &second,
                        cudaStream_t s) {
+  if (t.ntt_single && ntt_single_pass_ok(t, pro, epi, fwd) && same_limbs(first, second))
+    return launch_ntt_single(t, fwd, pro, epi, first, second, s);
   cudaError_t e;
   if (fwd) {
     if ((e = launch_ntt_pass(t, true, true, pro, EPI_LAZY, first, s)) != cudaSuccess) return e;

@@ -15,7 +15,18 @@
 //   (16 KB of shared memory), 256 threads, 16 elements per thread held in
 //   registers through 4 butterfly stages per shared-memory round trip.
 //   Butterflies keep values lazily in [0, 2q) (q < 2^31).
+//
+// Variants (chosen per context, measured by the autotuner):
+//   * on-the-fly twiddles (Section III-A cites them for the second NTT kernel):
+//     the block pass's register twiddles of a run of 2^m consecutive indices are
+//     formed as w_0 * psi^brv(k) from one loaded twiddle and a staged 8-entry
+//     table instead of 2^m loads;
+//   * single pass: one launch per limb group with a cluster of 16 CTAs (one per
+//     tile); the first pass leaves its tile in shared memory and the second
+//     reads its tile from the cluster's shared memory (no global round trip).
 #pragma once
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 namespace fhe {
@@ -77,24 +88,28 @@ __device__ __forceinline__ int kmap(bool hi, int e, int tau) {
 // dynamic shared memory of a pass: its staged twiddles (the column pass: the S - 1
 // twiddles of its R stages, shared by every column; the block pass: the 240
 // twiddles of its first four stages for its 16 blocks, 16 2^sigma at 16 (2^sigma - 1))
-__host__ __device__ constexpr int ntt_twiddle_smem(bool column, int S) { return (column ? S : 240) * 8; }
+__host__ __device__ constexpr int ntt_twiddle_smem(bool column, int S) { return (column ? S : 248) * 8; }
 
-template <int LOGN, bool COLUMN, bool FWD, int PRO, int EPI>
-__global__ void __launch_bounds__(kNttThreads) k_ntt(const __grid_constant__ SegList sl, const NttTables tb) {
+// Where a pass reads its round-0 elements and writes its results.
+enum : int { SRC_GLOBAL = 0, SRC_CLUSTER = 1 };
+enum : int { DST_GLOBAL = 0, DST_LOCAL = 1 };
+
+// Number of staged twiddle entries of a pass (see ntt_twiddle_smem) plus, for on-the-fly
+// twiddles, the 8 entries psi^brv(k), k < 8.
+constexpr int kOtfSmall = 8;
+
+// One pass over tile `tile` of a limb.  The single-pass kernel's transfer layouts (row r =
+// index >> 8, column col = index & 255 of the 256 x 256 view of a 2^16 limb):
+//   forward, after the column pass of column tile t (columns 16 t .. 16 t + 15):
+//     xfer[r * 16 + (col & 15)];
+//   inverse, after the block pass of row tile t (rows 16 t .. 16 t + 15):
+//     xfer[(r & 15) * 256 + col];
+// and the second pass reads the value of (r, col) from the CTA that owns it.
+template <int LOGN, bool COLUMN, bool FWD, int PRO, int EPI, bool OTF, int SRCM, int DSTM>
+__device__ __forceinline__ void ntt_pass(const Seg &sg, const KsArgs &ks, int within, int prime, const NttTables &tb,
+                                         int tile, uint32_t *sm, uint2 *tws, uint32_t *xfer) {
   using G = NttGeom<LOGN, COLUMN>;
   constexpr int R = G::R, N = G::N, S0 = COLUMN ? 0 : LOGN - 8;
-  // staged twiddles: the column pass needs the S - 1 twiddles of stages 0..R-1 (shared
-  // by all columns); the block pass needs, per stage sigma of its 8, the 16 2^sigma
-  // twiddles of its 16 blocks, stored at 16 (2^sigma - 1).
-  __shared__ uint32_t sm[R == 8 ? G::SMEM : 1];
-  extern __shared__ uint2 tws[];  // dynamic: ntt_twiddle_smem(COLUMN, S) bytes
-
-  const int v = blockIdx.x / G::TILES, tile = blockIdx.x % G::TILES;
-  int within;
-  const int si = seg_find(sl, v, within);
-  const Seg &sg = seg_at(sl, si);
-  const KsArgs &ks = item_ks(sl, sg);
-  const int prime = sg.prime + within;
   const PrimeC P = tb.pc[prime];
   const uint32_t q = P.q;
   const uint2 *tw = (FWD ? tb.tw_fwd : tb.tw_inv) + (size_t)prime * N;
@@ -112,6 +127,7 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt(const __grid_constant__ Seg
       const uint2 *from = tw + (1 << (S0 + sig)) + (blk0 << sig);
       if (tid < cnt) tws[16 * ((1 << sig) - 1) + tid] = __ldg(from + tid);
     }
+    if (OTF && tid < kOtfSmall) tws[240 + tid] = __ldg(tw + tid);
   }
 
   int c, tau;
@@ -133,7 +149,7 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt(const __grid_constant__ Seg
   // consecutive twiddles 2^(S0+sigma) + ((blk0 + c) << sigma) + (tau << m) + [0, 2^m), each
   // exactly once; prefetch them into registers (tl[2^m - 1 + k]) with vector loads.
   uint2 tl[COLUMN ? 1 : 15];
-  if (!COLUMN) {
+  if (!COLUMN && !OTF) {
     const int blk = tile * 16 + c;
 #pragma unroll
     for (int m = 0; m < 4; m++) {
@@ -151,10 +167,30 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt(const __grid_constant__ Seg
       }
     }
   }
+  uint2 tbase[OTF && !COLUMN ? 4 : 1];
+  if (!COLUMN && OTF) {
+    const int blk = tile * 16 + c;
+#pragma unroll
+    for (int m = 0; m < 4; m++) tbase[m] = __ldg(tw + (1 << (S0 + 4 + m)) + (blk << (4 + m)) + (tau << m));
+  }
 
-  // ---- round-0 elements straight from global memory (prologue applied)
+  // ---- round-0 elements (prologue applied)
   uint32_t x[16];
-  if (!COLUMN && !hi0 && PRO == PRO_PLAIN) {
+  if constexpr (SRCM == SRC_CLUSTER) {
+    static_assert(LOGN == 16, "the single-pass kernel splits a 2^16 limb into 16 tiles");
+    cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+#pragma unroll
+    for (int e = 0; e < 16; e++) {
+      if (FWD) {  // block pass: element (r, col) = ((16 tile + c), 16 e + tau), owned by column tile e
+        const uint32_t *peer = cl.map_shared_rank(xfer, e);
+        x[e] = peer[(tile * 16 + c) * 16 + tau];
+      } else {  // column pass: element (16 tau + e, 16 tile + c), owned by row tile tau
+        const uint32_t *peer = cl.map_shared_rank(xfer, tau);
+        x[e] = peer[e * 256 + tile * 16 + c];
+      }
+    }
+    cl.sync();  // every CTA has read what it needs from the others' transfer buffers
+  } else if (!COLUMN && !hi0 && PRO == PRO_PLAIN) {
     // inverse block pass: a thread's 16 elements are contiguous
     const uint4 *p = reinterpret_cast<const uint4 *>(src + G::gidx(tile, c, kmap<R>(false, 0, tau)));
 #pragma unroll
@@ -178,6 +214,27 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt(const __grid_constant__ Seg
     }
   }
   __syncthreads();  // staged twiddles
+
+  // on-the-fly register twiddles: the run 2^(S0+sigma) + t0 + k (t0 = 0 mod 2^m, k < 2^m)
+  // has psi^brv = psi^brv(2^(S0+sigma) + t0) psi^brv(k) (disjoint bits), so each is the
+  // loaded base times a staged small twiddle, with its Shoup companion
+  // floor(w 2^32 / q) = w floor(2^32 / q) + floor(w (2^32 mod q) / q) (the last quotient
+  // from a Shoup estimate and one correction).
+  if (!COLUMN && OTF) {
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+      tl[(1 << m) - 1] = tbase[m];
+#pragma unroll
+      for (int k = 1; k < (1 << m); k++) {
+        const uint2 sk = tws[240 + k];
+        const uint32_t w = shoup(tbase[m].x, sk.x, sk.y, q);
+        uint32_t qh = __umulhi(w, P.r32s);
+        const uint32_t rem = w * P.r32 - qh * q;  // w (2^32 mod q) - qh q, in [0, 2q)
+        qh += rem >= q ? 1u : 0u;
+        tl[(1 << m) - 1 + k] = make_uint2(w, w * P.div32 + qh);
+      }
+    }
+  }
 
 #pragma unroll
   for (int rho = 0; rho < ROUNDS; rho++) {
@@ -224,6 +281,16 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt(const __grid_constant__ Seg
 
   // ---- epilogue straight from registers
   const bool hiL = (R == 8) && !FWD;  // the last round
+  if constexpr (DSTM == DST_LOCAL) {  // single-pass kernel: the tile stays in shared memory (lazy values)
+    static_assert(LOGN == 16, "the single-pass kernel splits a 2^16 limb into 16 tiles");
+#pragma unroll
+    for (int e = 0; e < 16; e++) {
+      const int k = kmap<R>(hiL, e, tau);
+      if (COLUMN) xfer[k * 16 + c] = x[e];  // (r, col & 15) = (k, c)
+      else xfer[c * 256 + k] = x[e];         // (r & 15, col) = (c, k)
+    }
+    return;
+  }
   uint2 scale = make_uint2(0, 0);
   if (EPI == EPI_SCALE || EPI == EPI_RESCALE) scale = sg.scale ? sg.scale[within] : tb.ninv[prime];
   uint2 pinv = make_uint2(0, 0);
@@ -249,7 +316,6 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt(const __grid_constant__ Seg
   }
 #pragma unroll
   for (int e = 0; e < 16; e++) {
-    const uint32_t j = contiguous ? j0 + e : G::gidx(tile, c, kmap<R>(hiL, e, tau));
     const uint32_t val = x[e];
     uint32_t o;
     if (EPI == EPI_LAZY) {
@@ -273,6 +339,64 @@ __global__ void __launch_bounds__(kNttThreads) k_ntt(const __grid_constant__ Seg
 #pragma unroll
     for (int e = 0; e < 16; e++) dst[G::gidx(tile, c, kmap<R>(hiL, e, tau))] = x[e];
   }
+}
+
+// Resident CTAs per SM asked of the register allocator for each pass (the occupancy the
+// passes were measured at: 8 for the forward column passes, 6 for the inverse column pass
+// and ModUp's forward block pass, 5 or 4 for the other block passes).
+template <bool COLUMN, bool FWD, int PRO, int EPI, bool OTF>
+constexpr int ntt_min_blocks() {
+  if (COLUMN) return FWD ? 8 : 6;
+  if (!FWD) return 5;
+  if (EPI == EPI_PLAIN) return OTF ? 5 : 6;
+  return EPI == EPI_RESCALE ? 4 : 5;
+}
+
+template <int LOGN, bool COLUMN, bool FWD, int PRO, int EPI, bool OTF>
+__global__ void __launch_bounds__(kNttThreads, ntt_min_blocks<COLUMN, FWD, PRO, EPI, OTF>())
+    k_ntt(const __grid_constant__ SegList sl, const NttTables tb) {
+  using G = NttGeom<LOGN, COLUMN>;
+  constexpr int R = G::R;
+  // staged twiddles: the column pass needs the S - 1 twiddles of stages 0..R-1 (shared
+  // by all columns); the block pass needs, per stage sigma of its 8, the 16 2^sigma
+  // twiddles of its 16 blocks, stored at 16 (2^sigma - 1).
+  __shared__ uint32_t sm[R == 8 ? G::SMEM : 1];
+  extern __shared__ uint2 tws[];  // dynamic: ntt_twiddle_smem(COLUMN, S) bytes (+ the small table)
+
+  const int v = blockIdx.x / G::TILES, tile = blockIdx.x % G::TILES;
+  int within;
+  const int si = seg_find(sl, v, within);
+  const Seg &sg = seg_at(sl, si);
+  const KsArgs &ks = item_ks(sl, sg);
+  ntt_pass<LOGN, COLUMN, FWD, PRO, EPI, OTF, SRC_GLOBAL, DST_GLOBAL>(sg, ks, within, sg.prime + within, tb, tile, sm,
+                                                                     tws, nullptr);
+}
+
+// Both passes of a 2^16-point transform in one launch: a cluster of 16 CTAs per limb, CTA
+// t does the first pass on tile t into its shared memory, the cluster synchronises, and CTA
+// t does the second pass on tile t reading from the 16 CTAs' shared memory.  `first` and
+// `second` enumerate the same limbs (same segment sizes and primes): the first pass's
+// source and prologue come from `first`, the second pass's destination and epilogue from
+// `second`.
+template <bool FWD, int PRO, int EPI, bool OTF>
+__global__ void __cluster_dims__(16, 1, 1) __launch_bounds__(kNttThreads)
+    k_ntt1(const __grid_constant__ SegList first, const __grid_constant__ SegList second, const NttTables tb) {
+  constexpr int LOGN = 16;
+  using GB = NttGeom<LOGN, false>;
+  __shared__ uint32_t sm[GB::SMEM];
+  __shared__ uint32_t xfer[kTile];
+  extern __shared__ uint2 tws[];  // the larger of the two passes' staged twiddles
+  const int v = blockIdx.x / 16, tile = blockIdx.x % 16;
+  int w1, w2;
+  const Seg &s1 = seg_at(first, seg_find(first, v, w1));
+  const Seg &s2 = seg_at(second, seg_find(second, v, w2));
+  const KsArgs &k1 = item_ks(first, s1);
+  const KsArgs &k2 = item_ks(second, s2);
+  const int prime = s1.prime + w1;
+  // forward: column pass then block pass; inverse: block pass then column pass
+  ntt_pass<LOGN, FWD, FWD, PRO, EPI_LAZY, OTF, SRC_GLOBAL, DST_LOCAL>(s1, k1, w1, prime, tb, tile, sm, tws, xfer);
+  cooperative_groups::this_cluster().sync();  // every tile of the first pass is in shared memory
+  ntt_pass<LOGN, !FWD, FWD, PRO_PLAIN, EPI, OTF, SRC_CLUSTER, DST_GLOBAL>(s2, k2, w2, prime, tb, tile, sm, tws, xfer);
 }
 
 }  // namespace fhe

@@ -49,6 +49,21 @@ static Stage marker(Stage::Kind k) {
   return s;
 }
 
+// the two passes of one transform: one single-pass cluster stage when the context asks for
+// it and the kernel exists for the pair's prologue and epilogue, else two stages
+static void push_transform(fhe_ctx *c, Program &P, const Stage &first, const Stage &second) {
+  if (c->tabs.ntt_single && fhe::ntt_single_pass_ok(c->tabs, first.pro, second.epi, first.fwd)) {
+    Stage f = first;
+    f.kind = Stage::NTT1;
+    f.epi = second.epi;
+    f.segs2 = second.segs;
+    P.stages.push_back(f);
+    return;
+  }
+  P.stages.push_back(first);
+  P.stages.push_back(second);
+}
+
 int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Program &P) {
   const size_t N = c->N;
   const int L = c->L, K = c->K, A = c->alpha;
@@ -183,15 +198,13 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
   }
   if (!i1.segs.empty()) {
     if (!fused && !gather.segs.empty()) P.stages.push_back(gather);
-    P.stages.push_back(i1);
-    P.stages.push_back(i2);
+    push_transform(c, P, i1, i2);
     if (!fused) P.stages.push_back(sc);
     P.stages.push_back(bc);
-    P.stages.push_back(n1);
     Stage n2 = n1;
     n2.column = false;
     n2.epi = EPI_PLAIN;
-    P.stages.push_back(n2);
+    push_transform(c, P, n1, n2);
   }
 
   // ---- stages 2 and 3: inner product, ModDown
@@ -281,13 +294,18 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
     }
   }
   if (has_md) {
-    P.stages.push_back(m1);
-    P.stages.push_back(m2);
+    push_transform(c, P, m1, m2);
     if (!fused) P.stages.push_back(msc);
     P.stages.push_back(mbc);
-    P.stages.push_back(r1);
-    if (split) P.stages.push_back(marker(Stage::JOIN_WAIT));
-    P.stages.push_back(r2);
+    if (c->tabs.ntt_single && fhe::ntt_single_pass_ok(c->tabs, r1.pro, r2.epi, true)) {
+      // the single-pass transform reads u's q-limbs in its epilogue: join before it
+      if (split) P.stages.push_back(marker(Stage::JOIN_WAIT));
+      push_transform(c, P, r1, r2);
+    } else {
+      P.stages.push_back(r1);
+      if (split) P.stages.push_back(marker(Stage::JOIN_WAIT));
+      P.stages.push_back(r2);
+    }
     if (!fused) P.stages.push_back(cb);
   }
   return FHE_OK;
@@ -296,7 +314,7 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
 // ------------------------------------------------------------------ execution
 
 static cudaError_t launch_stage(fhe_ctx *c, const Stage &st, const SegList &sl, const BconvArgs &ba,
-                                cudaStream_t s, int lane) {
+                                cudaStream_t s, int lane, const SegList *sl2) {
   cudaStream_t aux = lane > 0 ? c->lanes[lane].aux : c->aux;
   cudaEvent_t ev_fork = lane > 0 ? c->lanes[lane].fork : c->ev_fork;
   cudaEvent_t ev_join = lane > 0 ? c->lanes[lane].join : c->ev_join;
@@ -308,6 +326,7 @@ static cudaError_t launch_stage(fhe_ctx *c, const Stage &st, const SegList &sl, 
     return cudaSuccess;
   switch (st.kind) {
     case Stage::NTT: return launch_ntt_pass(c->tabs, st.column, st.fwd, st.pro, st.epi, sl, q);
+    case Stage::NTT1: return launch_ntt_single(c->tabs, st.fwd, st.pro, st.epi, sl, *sl2, q);
     case Stage::EW: return launch_ew(c->tabs, st.ewop, sl, q);
     case Stage::IP: return launch_ip(c->tabs, sl, st.gather_own, st.gather_ext, c->dnum, q);
     case Stage::BCONV:
@@ -332,18 +351,23 @@ bool program_fits_inline(const Program &P) {
 
 int run_program_inline(fhe_ctx *c, const Program &P, cudaStream_t s) {
   if (!program_fits_inline(P)) return fhe_fail(FHE_EINVAL, "internal: program does not fit inline launch arguments");
-  SegList sl;
+  SegList sl, sl2;
   BconvArgs ba;
   for (const Stage &st : P.stages) {
     memset(&sl, 0, sizeof sl);
+    memset(&sl2, 0, sizeof sl2);
     memset(&ba, 0, sizeof ba);
     for (const Seg &x : st.segs) {
       sl.seg[sl.nseg++] = x;
       sl.total += x.n;
     }
-    for (size_t i = 0; i < P.ks.size(); i++) sl.ks[i] = P.ks[i];
+    for (const Seg &x : st.segs2) {
+      sl2.seg[sl2.nseg++] = x;
+      sl2.total += x.n;
+    }
+    for (size_t i = 0; i < P.ks.size(); i++) sl.ks[i] = sl2.ks[i] = P.ks[i];
     for (const BconvGroup &g : st.groups) ba.g[ba.ngroups++] = g;
-    cudaError_t e = launch_stage(c, st, sl, ba, s, 0);
+    cudaError_t e = launch_stage(c, st, sl, ba, s, 0, &sl2);
     if (e != cudaSuccess) return fhe_fail(FHE_ECUDA, "stage launch: %s", cudaGetErrorString(e));
   }
   return FHE_OK;
@@ -355,16 +379,22 @@ int upload_program(fhe_ctx *c, const Program &P, DevProgram &D) {
   auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
   bytes = align(bytes);
   std::vector<size_t> seg_off(P.stages.size()), map_off(P.stages.size()), grp_off(P.stages.size());
+  std::vector<size_t> seg2_off(P.stages.size()), map2_off(P.stages.size());
   for (size_t i = 0; i < P.stages.size(); i++) {
     const Stage &st = P.stages[i];
-    int total = 0;
+    int total = 0, total2 = 0;
     for (const Seg &x : st.segs) total += x.n;
+    for (const Seg &x : st.segs2) total2 += x.n;
     seg_off[i] = bytes;
     bytes = align(bytes + sizeof(Seg) * st.segs.size());
     map_off[i] = bytes;
     bytes = align(bytes + sizeof(int2) * total);
     grp_off[i] = bytes;
     bytes = align(bytes + sizeof(BconvGroup) * st.groups.size());
+    seg2_off[i] = bytes;
+    bytes = align(bytes + sizeof(Seg) * st.segs2.size());
+    map2_off[i] = bytes;
+    bytes = align(bytes + sizeof(int2) * total2);
   }
   std::vector<char> host(bytes, 0);
   memcpy(host.data(), P.ks.data(), sizeof(KsArgs) * P.ks.size());
@@ -376,12 +406,18 @@ int upload_program(fhe_ctx *c, const Program &P, DevProgram &D) {
     for (size_t sidx = 0; sidx < st.segs.size(); sidx++)
       for (int w = 0; w < st.segs[sidx].n; w++) m[v++] = make_int2((int)sidx, w);
     memcpy(host.data() + grp_off[i], st.groups.data(), sizeof(BconvGroup) * st.groups.size());
+    memcpy(host.data() + seg2_off[i], st.segs2.data(), sizeof(Seg) * st.segs2.size());
+    int2 *m2 = reinterpret_cast<int2 *>(host.data() + map2_off[i]);
+    int v2 = 0;
+    for (size_t sidx = 0; sidx < st.segs2.size(); sidx++)
+      for (int w = 0; w < st.segs2[sidx].n; w++) m2[v2++] = make_int2((int)sidx, w);
   }
   if (cudaMalloc(&D.buf, bytes) != cudaSuccess) return fhe_fail(FHE_ENOMEM, "program upload: %zu bytes", bytes);
   if (cudaMemcpy(D.buf, host.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess)
     return fhe_fail(FHE_ECUDA, "program upload copy");
   char *base = static_cast<char *>(D.buf);
   D.lists.assign(P.stages.size(), SegList{});
+  D.lists2.assign(P.stages.size(), SegList{});
   D.bargs.assign(P.stages.size(), BconvArgs{});
   for (size_t i = 0; i < P.stages.size(); i++) {
     const Stage &st = P.stages[i];
@@ -392,6 +428,13 @@ int upload_program(fhe_ctx *c, const Program &P, DevProgram &D) {
     sl.dev = reinterpret_cast<const Seg *>(base + seg_off[i]);
     sl.vmap = reinterpret_cast<const int2 *>(base + map_off[i]);
     sl.ksdev = reinterpret_cast<const KsArgs *>(base);
+    SegList &sl2 = D.lists2[i];
+    memset(&sl2, 0, sizeof sl2);
+    sl2.nseg = (int)st.segs2.size();
+    for (const Seg &x : st.segs2) sl2.total += x.n;
+    sl2.dev = reinterpret_cast<const Seg *>(base + seg2_off[i]);
+    sl2.vmap = reinterpret_cast<const int2 *>(base + map2_off[i]);
+    sl2.ksdev = reinterpret_cast<const KsArgs *>(base);
     BconvArgs &ba = D.bargs[i];
     memset(&ba, 0, sizeof ba);
     ba.ngroups = (int)st.groups.size();
@@ -403,7 +446,7 @@ int upload_program(fhe_ctx *c, const Program &P, DevProgram &D) {
 
 int run_program_dev(fhe_ctx *c, const Program &P, const DevProgram &D, cudaStream_t s, int lane) {
   for (size_t i = 0; i < P.stages.size(); i++) {
-    cudaError_t e = launch_stage(c, P.stages[i], D.lists[i], D.bargs[i], s, lane);
+    cudaError_t e = launch_stage(c, P.stages[i], D.lists[i], D.bargs[i], s, lane, &D.lists2[i]);
     if (e != cudaSuccess) return fhe_fail(FHE_ECUDA, "stage launch: %s", cudaGetErrorString(e));
   }
   return FHE_OK;

@@ -29,13 +29,16 @@ struct Item {
 };
 
 struct Stage {
-  enum Kind { NTT, BCONV, IP, EW, FORK, JOIN_RECORD, JOIN_WAIT } kind = NTT;
+  // NTT1: both passes of a transform in one cluster launch (segs: the first pass's limbs
+  // and prologue; segs2: the same limbs with the second pass's destination and epilogue)
+  enum Kind { NTT, BCONV, IP, EW, FORK, JOIN_RECORD, JOIN_WAIT, NTT1 } kind = NTT;
   bool column = false, fwd = false;
   int pro = 0, epi = 0, ewop = 0;
   bool aux = false;
   bool gather_own = false, gather_ext = false;
   int max_in = 0, max_out = 0;
   std::vector<fhe::Seg> segs;
+  std::vector<fhe::Seg> segs2;
   std::vector<fhe::BconvGroup> groups;
 };
 
@@ -48,6 +51,7 @@ struct Program {
 struct DevProgram {
   void *buf = nullptr;
   std::vector<fhe::SegList> lists;   // per stage (segment stages)
+  std::vector<fhe::SegList> lists2;  // per stage (NTT1: the second pass's segments)
   std::vector<fhe::BconvArgs> bargs; // per stage (BConv stages)
 };
 

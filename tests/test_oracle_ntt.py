@@ -111,3 +111,29 @@ def test_ntt_linear_and_x_monomial():
     bits = 12
     for i in range(0, N, 97):
         assert int(got[i]) == pow(psi, 2 * brv(i, bits) + 1, q)
+
+
+def test_twiddle_runs_factor_for_on_the_fly_generation():
+    """The on-the-fly twiddles of the block passes rest on two identities: for a run of
+    twiddle indices 2^s + t0 + k (t0 a multiple of 2^m, k < 2^m) the bits are disjoint, so
+    psi^brv(2^s + t0 + k) = psi^brv(2^s + t0) psi^brv(k); and the Shoup companion of w is
+    floor(w 2^32 / q) = w floor(2^32 / q) + floor(w (2^32 mod q) / q)."""
+    g = inputs.rng(41)
+    for N in (1 << 12, 1 << 16):
+        logn = N.bit_length() - 1
+        q = inputs.ntt_primes(N, 31, 2)[1]
+        psi = oracle.psi(q, N)
+
+        def brv(x):
+            return int(format(x, f"0{logn}b")[::-1], 2)
+
+        for _ in range(200):
+            m = int(g.integers(0, 4))
+            s = int(g.integers(m + 4, logn))
+            t0 = int(g.integers(0, 1 << (s - m))) << m
+            k = int(g.integers(0, 1 << m))
+            lhs = pow(psi, brv((1 << s) + t0 + k), q)
+            rhs = pow(psi, brv((1 << s) + t0), q) * pow(psi, brv(k), q) % q
+            assert lhs == rhs
+            w = int(g.integers(0, q))
+            assert (w << 32) // q == w * ((1 << 32) // q) + (w * ((1 << 32) % q)) // q
