@@ -132,7 +132,7 @@ FHE_API int fhe_ctx_set_fused(fhe_ctx *ctx, int fused);
 FHE_API int fhe_ctx_set_pipelining(fhe_ctx *ctx, int on);
 /* NTT kernel variants (flags; 0 = the two-pass kernels, the default):
  *   FHE_NTT_OTF: the block passes (the last eight stages, the paper's second
- *     NTT kernel, Section III-A) form most of their register twiddles on the fly
+ *     NTT kernel, Section III-C) form most of their register twiddles on the fly
  *     from one loaded twiddle and a staged 8-entry table instead of loading each;
  *   FHE_NTT_SINGLE_PASS: each 2^16-point transform of a stage program runs as
  *     one launch with a cluster of 16 CTAs per limb, the first pass's tiles

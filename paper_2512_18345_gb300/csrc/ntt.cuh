@@ -17,7 +17,7 @@
 //   Butterflies keep values lazily in [0, 2q) (q < 2^31).
 //
 // Variants (chosen per context, measured by the autotuner):
-//   * on-the-fly twiddles (Section III-A cites them for the second NTT kernel):
+//   * on-the-fly twiddles (Section III-C cites them for the second NTT kernel):
 //     the block pass's register twiddles of a run of 2^m consecutive indices are
 //     formed as w_0 * psi^brv(k) from one loaded twiddle and a staged 8-entry
 //     table instead of 2^m loads;
@@ -89,6 +89,11 @@ __device__ __forceinline__ int kmap(bool hi, int e, int tau) {
 // twiddles of its R stages, shared by every column; the block pass: the 240
 // twiddles of its first four stages for its 16 blocks, 16 2^sigma at 16 (2^sigma - 1))
 __host__ __device__ constexpr int ntt_twiddle_smem(bool column, int S) { return (column ? S : 248) * 8; }
+
+// Split cluster barrier (all threads of every CTA of the cluster): arrive releases this
+// thread's earlier shared-memory accesses to the cluster, wait acquires the others'.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 
 // Where a pass reads its round-0 elements and writes its results.
 enum : int { SRC_GLOBAL = 0, SRC_CLUSTER = 1 };
@@ -179,6 +184,7 @@ __device__ __forceinline__ void ntt_pass(const Seg &sg, const KsArgs &ks, int wi
   if constexpr (SRCM == SRC_CLUSTER) {
     static_assert(LOGN == 16, "the single-pass kernel splits a 2^16 limb into 16 tiles");
     cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+    cluster_wait();  // every CTA's first-pass tile is in its shared memory (its arrive ended pass 1)
 #pragma unroll
     for (int e = 0; e < 16; e++) {
       if (FWD) {  // block pass: element (r, col) = ((16 tile + c), 16 e + tau), owned by column tile e
@@ -189,7 +195,7 @@ __device__ __forceinline__ void ntt_pass(const Seg &sg, const KsArgs &ks, int wi
         x[e] = peer[e * 256 + tile * 16 + c];
       }
     }
-    cl.sync();  // every CTA has read what it needs from the others' transfer buffers
+    cluster_arrive();  // this CTA's reads of the others' buffers are done (waited for at the kernel's end)
   } else if (!COLUMN && !hi0 && PRO == PRO_PLAIN) {
     // inverse block pass: a thread's 16 elements are contiguous
     const uint4 *p = reinterpret_cast<const uint4 *>(src + G::gidx(tile, c, kmap<R>(false, 0, tau)));
@@ -289,6 +295,7 @@ __device__ __forceinline__ void ntt_pass(const Seg &sg, const KsArgs &ks, int wi
       if (COLUMN) xfer[k * 16 + c] = x[e];  // (r, col & 15) = (k, c)
       else xfer[c * 256 + k] = x[e];         // (r & 15, col) = (c, k)
     }
+    cluster_arrive();  // the tile is published; the second pass waits before reading the cluster
     return;
   }
   uint2 scale = make_uint2(0, 0);
@@ -394,9 +401,14 @@ __global__ void __cluster_dims__(16, 1, 1) __launch_bounds__(kNttThreads)
   const KsArgs &k2 = item_ks(second, s2);
   const int prime = s1.prime + w1;
   // forward: column pass then block pass; inverse: block pass then column pass
+  // (the passes pair a split cluster barrier: pass 1 arrives after publishing its tile and
+  // pass 2 waits just before reading the cluster, so pass 2's twiddle loads overlap the
+  // wait; pass 2 arrives after its reads and the CTA waits before exiting, so no CTA's
+  // shared memory goes away while another reads it)
   ntt_pass<LOGN, FWD, FWD, PRO, EPI_LAZY, OTF, SRC_GLOBAL, DST_LOCAL>(s1, k1, w1, prime, tb, tile, sm, tws, xfer);
-  cooperative_groups::this_cluster().sync();  // every tile of the first pass is in shared memory
+  __syncthreads();  // pass 1's last reads of the staged twiddles come before pass 2 restages them
   ntt_pass<LOGN, !FWD, FWD, PRO_PLAIN, EPI, OTF, SRC_CLUSTER, DST_GLOBAL>(s2, k2, w2, prime, tb, tile, sm, tws, xfer);
+  cluster_wait();
 }
 
 }  // namespace fhe
