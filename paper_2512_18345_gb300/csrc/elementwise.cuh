@@ -293,7 +293,6 @@ __global__ void __launch_bounds__(kIpThreads, 2) k_ip_bulk(const __grid_constant
   // the gathered own values of a unit are loaded one unit ahead (after the wait
   // that orders the unit's descriptor), so their latency overlaps a unit's work
   constexpr int E = kIpEpt;
-  static_assert(E == 4, "the sigma reads fetch aligned groups of four slots");
   auto gather = [&](const IpUnit &d, uint32_t (&v)[E]) {
     const uint32_t j = d.j0 + tid * E;
 #pragma unroll
