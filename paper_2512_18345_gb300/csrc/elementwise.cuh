@@ -221,7 +221,7 @@ struct IpUnit {            // one unit, as the consumers need it
 // automorphism): only the key chunks stream through the stages; every digit's values
 // are gathered with plain loads one unit ahead (the shared digits stay in L2).
 template <bool GOWN, bool GEXT>
-__global__ void __launch_bounds__(kIpThreads, 2) k_ip_bulk(const __grid_constant__ SegList sl, const PrimeC *pc,
+__global__ void __launch_bounds__(kIpThreads + 32, 2) k_ip_bulk(const __grid_constant__ SegList sl, const PrimeC *pc,
                                                            int logn, unsigned int *status, int beta_max, int stages) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int tid = threadIdx.x;
@@ -230,14 +230,17 @@ __global__ void __launch_bounds__(kIpThreads, 2) k_ip_bulk(const __grid_constant
   const int total = sl.total * chunks;
   const size_t stage_words = (size_t)3 * beta_max * kIpChunk;
   uint32_t *buf = reinterpret_cast<uint32_t *>(smem);
+  // per stage: `bar` completes when the stage's copies have landed, `dbar` when its
+  // descriptor is written, `ebar` when the consumers are done with it (then it is refilled)
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + (size_t)stages * stage_words * 4);
-  IpUnit *desc = reinterpret_cast<IpUnit *>(bar + stages);
+  uint64_t *dbar = bar + stages, *ebar = dbar + stages;
+  IpUnit *desc = reinterpret_cast<IpUnit *>(ebar + stages);
   __shared__ int s_ok;
 
   // keys are read exactly once: evict them first, so that ModUp outputs (and the digits shared
   // by hoisted rotations) stay in L2
   const uint64_t key_policy = l2_evict_first_policy();
-  // thread 0: describe unit u and stream its operands into stage st
+  // the producer: describe unit u and stream its operands into stage st
   auto issue = [&](int u, int st) {
     int within;
     const Seg &sg = seg_at(sl, seg_find(sl, u / chunks, within));
@@ -266,6 +269,7 @@ __global__ void __launch_bounds__(kIpThreads, 2) k_ip_bulk(const __grid_constant
     d.galois_add = ks.galois_add;
     d.pm = add ? ks.pmod[t] : make_uint2(0, 0);
     desc[st] = d;
+    mbar_arrive(&dbar[st]);  // the descriptor is readable (release)
     const size_t kstride = (size_t)2 * (ks.L + ks.K) * N, half = (size_t)(ks.L + ks.K) * N;
     const uint32_t copies = GEXT ? 2u * (uint32_t)ks.beta : 3u * (uint32_t)ks.beta - (d.gjd >= 0 ? 1u : 0u);
     mbar_arrive_expect_tx(&bar[st], copies * kIpChunk * 4u);
@@ -281,14 +285,30 @@ __global__ void __launch_bounds__(kIpThreads, 2) k_ip_bulk(const __grid_constant
       bulk_g2s_hint(dst + (size_t)(3 * jd + 2) * kIpChunk, kp + half, kIpChunk * 4u, &bar[st], key_policy);
     }
   };
+  // Warp specialisation: warps 0..7 reduce units, warp 8 (one lane) produces them.  The
+  // producer runs ahead of the consumers by up to `stages` units, so its dependent reads
+  // of the launch descriptors stay off the consumers' path.
   if (tid == 0) {
-    for (int st = 0; st < stages; st++) mbar_init(&bar[st], 1);
     for (int st = 0; st < stages; st++) {
-      const int u = blockIdx.x + st * gridDim.x;
-      if (u < total) issue(u, st);
+      mbar_init(&bar[st], 1);
+      mbar_init(&dbar[st], 1);
+      mbar_init(&ebar[st], 1);
     }
   }
   __syncthreads();
+  if (tid >= kIpThreads) {
+    if (tid != kIpThreads) return;
+    for (int k = 0;; k++) {
+      const int u = (int)blockIdx.x + k * (int)gridDim.x;
+      if (u >= total) break;
+      const int st = k % stages;
+      // the consumers released this stage's previous unit (bounded: if they gave up, so do we)
+      if (k >= stages && !mbar_wait_bounded(&ebar[st], (uint32_t)(k / stages - 1) & 1u)) break;
+      fence_proxy_async_smem();
+      issue(u, st);
+    }
+    return;
+  }
 
   // the gathered own values of a unit are loaded one unit ahead (after the wait
   // that orders the unit's descriptor), so their latency overlaps a unit's work
@@ -319,17 +339,23 @@ __global__ void __launch_bounds__(kIpThreads, 2) k_ip_bulk(const __grid_constant
 #pragma unroll
         for (int e = 0; e < E; e++) v[jd][e] = __ldg(d.esrc[jd] + galois_src(j + e, d.egal[jd], logn));
   };
+  // consumer-only barrier (named barrier 1, the 256 consumer threads)
+  auto consumers_sync = []() { asm volatile("bar.sync 1, %0;" ::"n"(kIpThreads) : "memory"); };
   uint32_t gnext[E] = {}, pnext0[E] = {}, pnext1[E] = {}, xnext[XD][E] = {};
-  if ((int)blockIdx.x < total) {
-    if (GOWN && desc[0].gjd >= 0) gather(desc[0], gnext);
-    if (GEXT) gather_all(desc[0], xnext);
-    if (desc[0].add0) pass(desc[0], pnext0, pnext1);
-  }
   bool ok = true;
+  if ((int)blockIdx.x < total) {
+    if (tid == 0) s_ok = mbar_wait_bounded(&dbar[0], 0u) ? 1 : 0;
+    consumers_sync();
+    ok = s_ok != 0;
+    if (ok) {
+      if (GOWN && desc[0].gjd >= 0) gather(desc[0], gnext);
+      if (GEXT) gather_all(desc[0], xnext);
+      if (desc[0].add0) pass(desc[0], pnext0, pnext1);
+    }
+  }
   int k = 0;
-  for (int u = blockIdx.x; u < total; u += gridDim.x, k++) {
+  for (int u = blockIdx.x; ok && u < total; u += gridDim.x, k++) {
     const int st = k % stages;
-    const IpUnit d = desc[st];
     uint32_t gv[E], pv0[E], pv1[E], xv[XD][E];
 #pragma unroll
     for (int e = 0; e < E; e++) gv[e] = gnext[e], pv0[e] = pnext0[e], pv1[e] = pnext1[e];
@@ -337,11 +363,17 @@ __global__ void __launch_bounds__(kIpThreads, 2) k_ip_bulk(const __grid_constant
     for (int jd = 0; jd < XD; jd++)
 #pragma unroll
       for (int e = 0; e < E; e++) xv[jd][e] = xnext[jd][e];
-    if (tid == 0) s_ok = mbar_wait_bounded(&bar[st], (uint32_t)(k / stages) & 1u) ? 1 : 0;
-    __syncthreads();
+    const bool has_next = u + (int)gridDim.x < total;
+    if (tid == 0) {
+      bool w = mbar_wait_bounded(&bar[st], (uint32_t)(k / stages) & 1u);
+      if (w && has_next) w = mbar_wait_bounded(&dbar[(k + 1) % stages], (uint32_t)((k + 1) / stages) & 1u);
+      s_ok = w ? 1 : 0;
+    }
+    consumers_sync();
     ok = s_ok != 0;
     if (!ok) break;
-    if (u + (int)gridDim.x < total) {  // descriptor of this CTA's next unit, written before this wait
+    const IpUnit d = desc[st];
+    if (has_next) {  // the next unit's descriptor (its readiness was waited for above)
       const IpUnit dn = desc[(k + 1) % stages];
       if (GOWN && dn.gjd >= 0) gather(dn, gnext);
       if (GEXT) gather_all(dn, xnext);
@@ -388,18 +420,13 @@ __global__ void __launch_bounds__(kIpThreads, 2) k_ip_bulk(const __grid_constant
     uint32_t *d0 = d.d0 + tid * E;
     st_words<E>(d0, r0);
     st_words<E>(d0 + d.d1_off, r1);
-    __syncthreads();  // every thread is done with stage st and its descriptor
-    if (tid == 0) {
-      const int u2 = u + stages * gridDim.x;
-      if (u2 < total) {
-        fence_proxy_async_smem();
-        issue(u2, st);
-      }
-    }
+    consumers_sync();  // every consumer is done with stage st and its descriptor
+    if (tid == 0) mbar_arrive(&ebar[st]);
   }
   if (!ok && tid == 0) {
-    // an expired wait: report it, then wait (bounded) for this CTA's copies still
-    // in flight so that none lands after the CTA has left the SM
+    // an expired wait: report it, then wait (bounded) for this CTA's copies that may still
+    // be in flight (the producer issues at most `stages` units beyond the last one
+    // released) so that none lands after the CTA has left the SM
     atomicOr(status, 2u);
     const int issued = (total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1;  // units of this CTA
     for (int k2 = k; k2 < min(issued, k + stages); k2++)

@@ -209,7 +209,7 @@ cudaError_t launch_ip(const DevTables &t, const SegList &sl, bool gather_own, bo
     // streaming kernel: as many stages as fit half an SM's shared memory; one or two CTAs per
     // SM (one leaves half of every SM to the transforms running beside it)
     const int stage_bytes = 3 * beta_max * kIpChunk * 4;
-    const int per_stage = stage_bytes + 8 + (int)sizeof(IpUnit);
+    const int per_stage = stage_bytes + 24 + (int)sizeof(IpUnit);  // data, three mbarriers, descriptor
     const int stages = std::min(8, (113 * 1024 - 256) / per_stage);
     const int smem = stages * per_stage;
     static bool configured[4] = {false, false, false, false};
@@ -231,10 +231,10 @@ cudaError_t launch_ip(const DevTables &t, const SegList &sl, bool gather_own, bo
     const int units = sl.total * ((1 << t.logn) / kIpChunk);
     const unsigned grid = (unsigned)std::min(units, std::max(1, std::min(2, t.ip_ctas_per_sm)) * sms);
     switch (variant) {
-      case 0: k_ip_bulk<false, false><<<grid, kIpThreads, smem, s>>>(sl, t.pc, t.logn, t.status, beta_max, stages); break;
-      case 1: k_ip_bulk<true, false><<<grid, kIpThreads, smem, s>>>(sl, t.pc, t.logn, t.status, beta_max, stages); break;
-      case 2: k_ip_bulk<false, true><<<grid, kIpThreads, smem, s>>>(sl, t.pc, t.logn, t.status, beta_max, stages); break;
-      default: k_ip_bulk<true, true><<<grid, kIpThreads, smem, s>>>(sl, t.pc, t.logn, t.status, beta_max, stages); break;
+      case 0: k_ip_bulk<false, false><<<grid, kIpThreads + 32, smem, s>>>(sl, t.pc, t.logn, t.status, beta_max, stages); break;
+      case 1: k_ip_bulk<true, false><<<grid, kIpThreads + 32, smem, s>>>(sl, t.pc, t.logn, t.status, beta_max, stages); break;
+      case 2: k_ip_bulk<false, true><<<grid, kIpThreads + 32, smem, s>>>(sl, t.pc, t.logn, t.status, beta_max, stages); break;
+      default: k_ip_bulk<true, true><<<grid, kIpThreads + 32, smem, s>>>(sl, t.pc, t.logn, t.status, beta_max, stages); break;
     }
     g_launches++;
     return cudaGetLastError();
