@@ -87,7 +87,8 @@ __device__ __forceinline__ int kmap(bool hi, int e, int tau) {
 
 // dynamic shared memory of a pass: its staged twiddles (the column pass: the S - 1
 // twiddles of its R stages, shared by every column; the block pass: the 240
-// twiddles of its first four stages for its 16 blocks, 16 2^sigma at 16 (2^sigma - 1))
+// twiddles of its first four stages for its 16 blocks, 16 2^sigma at 16 (2^sigma - 1),
+// then the 8 entries psi^brv(k), k < 8, of the on-the-fly variant)
 __host__ __device__ constexpr int ntt_twiddle_smem(bool column, int S) { return (column ? S : 248) * 8; }
 
 // Split cluster barrier (all threads of every CTA of the cluster): arrive releases this
