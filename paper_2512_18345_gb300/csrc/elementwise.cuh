@@ -161,16 +161,16 @@ __global__ void __launch_bounds__(kEwThreads) k_ip(const __grid_constant__ SegLi
 }
 
 // Stage 2 as a persistent streaming kernel (the ext limbs are read in order).
-// A unit is kIpChunk coefficients of one extended limb.  Thread 0 streams each
-// unit's operands -- per digit the ModUp value (ext, or the own limb when it is
-// not read through an automorphism) and both key halves, 4 KB each -- into a
-// ring of shared-memory stages with cp.async.bulk, completing on one mbarrier
-// per stage, and writes the unit's descriptor (output, prime, digit count) next
-// to the stage; the copies of the next stages stay in flight while the CTA
-// reduces the current one.  Thread 0 alone polls the barrier (bounded); the
-// other threads sleep at the CTA barrier.  The own digit of a rotation
-// (sigma_{galois_own} applied on the fly) is gathered with plain loads issued
-// before the wait.
+// A unit is kIpChunk coefficients of one extended limb.  A producer warp (one
+// lane) streams each unit's operands -- per digit the ModUp value (ext, or the
+// own limb when it is not read through an automorphism) and both key halves,
+// 4 KB each -- into a ring of shared-memory stages with cp.async.bulk,
+// completing on the stage's full mbarrier, after writing the unit's descriptor
+// (output, prime, digit count) next to the stage; it refills a stage as soon as
+// the consumers release it, up to `stages` units ahead.  Of the kIpThreads
+// consumers, thread 0 alone polls the barriers (bounded); the others sleep at a
+// named barrier.  The own digit of a rotation (sigma_{galois_own} applied on
+// the fly) is gathered with plain loads one unit ahead.
 constexpr int kIpChunk = 1024;  // coefficients per unit
 constexpr int kIpThreads = 256;
 constexpr int kIpEpt = kIpChunk / kIpThreads;  // coefficients per thread and unit (2 or 4)

@@ -62,13 +62,6 @@ static bool overlaps(const void *a, size_t abytes, const void *b, size_t bbytes)
   return x < y + bbytes && y < x + abytes;
 }
 
-[[maybe_unused]] static KsArgs ks_none() {
-  KsArgs ks;
-  memset(&ks, 0, sizeof ks);
-  ks.galois_own = ks.galois_ext = ks.galois_add = 1;
-  return ks;
-}
-
 // run a program of at most kMaxInlineItems items with by-value launch arguments
 static int run_items(fhe_ctx *c, const std::vector<Item> &items, cudaStream_t s) {
   Program P;

@@ -178,7 +178,6 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
       const int lo = j * A, hi = std::min((j + 1) * A, level);
       BconvGroup g;
       memset(&g, 0, sizeof g);
-    memset(&g, 0, sizeof g);
       g.in = S.Y + (size_t)lo * N;
       g.out = S.EXT + (size_t)j * n_ext * N;
       g.T = c->modup_T[(size_t)(level - 1) * c->dnum + j];
@@ -251,7 +250,6 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
       add(msc, y);
       BconvGroup g;
       memset(&g, 0, sizeof g);
-    memset(&g, 0, sizeof g);
       g.in = uc;
       g.out = r;
       g.T = c->d_mdT;

@@ -166,3 +166,23 @@ def test_rejections(fhe_lib):
     assert code(lambda: ctx.linear_transform_dh(ct, level, [0] * 33, [0], pt, [[0] * 33])) == binding.FHE_EINVAL
     assert code(lambda: ctx.linear_transform_dh(ct, level, [0], [0], pt, [[0]], out=ct)) == binding.FHE_EALIAS
     ctx.close()
+
+
+@pytest.mark.parametrize("level", [1, 2, 3])
+def test_low_levels(fhe_lib, level):
+    """One digit or a partial last digit (alpha = 2 on this ring): the extended basis is a few
+    q-limbs plus the special limbs."""
+    from paper_2512_18345_gb300 import binding
+    P = inputs.workload_params("cts_stc_N4096_L8")
+    OP = oracle.OracleParams.from_params(P)
+    plan = inputs.bsgs_plan(P.N // 2, 3, 4)
+    g = inputs.rng(1450 + level)
+    ctx = binding.Context.from_params(P)
+    keys = {}
+    for r in plan.rotations():
+        keys[r] = rand_key(P, g)
+        ctx.set_rot_key(r, dev(keys[r]))
+    ct, diags = uniform_level(P, plan, level, g)
+    got = host(ctx, ctx.linear_transform_dh(dev(ct), level, plan.baby, plan.giant, dev(diags), plan.idx))
+    assert np.array_equal(got, blt.lt_double_hoisted(OP, ct, level, plan.baby, plan.giant, diags, plan.idx, keys))
+    ctx.close()
