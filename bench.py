@@ -306,7 +306,7 @@ def bench_bootstrap_lt(binding, inputs, dev, timed, hbm_peak, only=None, runs=0)
     P = inputs.workload_params(name)
     g = inputs.rng(w["seed"])
     ctx = binding.Context.from_params(P, device=dev)
-    ctx.set_bconv(binding.FHE_BCONV_SCALAR)  # alpha = 12 exceeds the tensor-core bound
+    ctx.set_bconv(binding.FHE_BCONV_TC)  # the K = 64 shape for the 12-limb digits
     key = binding.to_device(rand_key_np(inputs, P, g), dev)
     tg = torch.Generator(device=f"cuda:{dev}")
     tg.manual_seed(w["seed"])
@@ -377,15 +377,14 @@ def bench_bootstrap_lt(binding, inputs, dev, timed, hbm_peak, only=None, runs=0)
 
 def bench_paper_shapes(binding, inputs, roofline, dev, timed, steps, l2_gbs, B=8):
     """The paper's key-switching shapes (alpha = K = 12; (l, beta) = (24, 2), (48, 4)):
-    B rotations with distinct keys per step, autotuned schedule, one CUDA graph,
-    CUDA-core conversion (alpha = 12 exceeds the tensor-core bound)."""
+    B rotations with distinct keys per step, autotuned schedule and conversion kernel
+    (CUDA cores or the tensor-core K = 64 shape), one CUDA graph."""
     import numpy as np
     res = {}
     for name in ("paper_ks_N65536_L24_a12", "paper_ks_N65536_L48_a12"):
         P = inputs.workload_params(name)
         g = inputs.rng(inputs.WORKLOADS[name]["seed"] + 500)
         ctx = binding.Context.from_params(P, device=dev)
-        ctx.set_bconv(binding.FHE_BCONV_SCALAR)
         items, used = [], set()
         while len(items) < B:
             r = inputs.rotation_index(g)
@@ -397,7 +396,7 @@ def bench_paper_shapes(binding, inputs, roofline, dev, timed, steps, l2_gbs, B=8
             ct = binding.to_device(np.stack([inputs.uniform_residues(g, P.q, P.N) for _ in range(2)]), dev)
             items.append(dict(op=binding.FHE_OP_ROTATE, level=P.L, rot=r, **{"in": ct},
                               out=binding.empty((2, P.L, P.N), dev)))
-        tune = ctx.autotune(P.L, B)
+        tune = ctx.autotune(P.L, B, binding.FHE_TUNE_BCONV)
         plan = ctx.batch_plan(items, binding.FHE_PLAN_GRAPH)
         for _ in range(3):
             plan.launch()
@@ -409,7 +408,8 @@ def bench_paper_shapes(binding, inputs, roofline, dev, timed, steps, l2_gbs, B=8
         res[f"l{P.L}_alpha{P.alpha}_beta{P.beta(P.L)}"] = {
             "value": 1.0 / t_ks, "unit": "key-switches/s", "us_per_ks": t_ks * 1e6, "items": B,
             "bytes_per_ks_model": bks, "l2_roofline_frac": (bks / (l2_gbs * 1e9)) / t_ks,
-            "groups": plan.groups, "autotune": tune, "bconv": "cuda cores"}
+            "groups": plan.groups, "autotune": tune,
+            "bconv": "tensor cores (K = 64)" if tune["bconv_mode"] == binding.FHE_BCONV_TC else "cuda cores"}
         plan.close()
         ctx.close()
     return res

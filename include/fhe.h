@@ -90,7 +90,7 @@ typedef struct {
 /* BConv implementation selector (fhe_ctx_set_bconv).  Both give identical bits. */
 #define FHE_BCONV_SCALAR 0 /* CUDA-core 64-bit multiply-accumulate, one final reduction */
 #define FHE_BCONV_TC 1     /* tensor cores: 8-bit digit split, f16 operands, exact fp32 accumulation;
-                              needs alpha <= 8 and K <= 8 (fhe_bconv: n_in <= 8) */
+                              needs alpha <= 12 and K <= 12 (fhe_bconv: n_in <= 12) */
 
 /*
  * Create a context for ring degree N (a power of two, 2^12..2^16), ciphertext
@@ -106,8 +106,10 @@ FHE_API int fhe_ctx_create(fhe_ctx **out, uint32_t N, const uint32_t *q, int L, 
 FHE_API int fhe_ctx_destroy(fhe_ctx *ctx);
 FHE_API int fhe_ctx_info(const fhe_ctx *ctx, fhe_info *out);
 /* Select the BConv implementation for later calls (FHE_BCONV_SCALAR / FHE_BCONV_TC).
- * FHE_EUNSUPPORTED for FHE_BCONV_TC when alpha > 8 or K > 8 (the exactness bound
- * of the tensor-core digit split holds for at most 8 inputs per conversion). */
+ * The tensor-core digit split is exact for at most 12 inputs per conversion: a
+ * K = 48 contraction when alpha and K are at most 8, a K = 64 one (signed offset
+ * pieces) when they are at most 12.  FHE_EUNSUPPORTED for FHE_BCONV_TC when alpha
+ * > 12 or K > 12. */
 FHE_API int fhe_ctx_set_bconv(fhe_ctx *ctx, int mode);
 /*
  * Synchronize the context's device and report device-side failures: returns
@@ -255,7 +257,7 @@ FHE_API int fhe_add(fhe_ctx *ctx, const uint32_t *a, const uint32_t *b, int npol
  *     in_idx) to out [n_out][N] (primes out_idx), Section II-B "BConv" with the
  *     table T[i][j] = (Qstar / q_j) mod p_i of Section III-C and the
  *     [(Qstar / q_j)^-1]_{q_j} pre-multiplication; n_in <= 16, n_out <= 64
- *     (n_in <= 8 under FHE_BCONV_TC, else FHE_EUNSUPPORTED).
+ *     (n_in <= 12 under FHE_BCONV_TC, else FHE_EUNSUPPORTED).
  */
 FHE_API int fhe_ntt(fhe_ctx *ctx, uint32_t *a, const int *prime_idx, int n, fhe_stream stream);
 FHE_API int fhe_intt(fhe_ctx *ctx, uint32_t *a, const int *prime_idx, int n, fhe_stream stream);

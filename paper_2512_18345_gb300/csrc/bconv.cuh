@@ -25,13 +25,17 @@ struct BconvGroup {
   const uint32_t *T;    // [n_out][n_in] device table
   const int2 *omap;     // [n_out] (limb offset from out, prime index)
   int n_in, n_out;
-  const uint16_t *Btc;  // tensor-core path: digit table, canonical layout, npad x kTcK f16
+  const uint16_t *Btc;  // tensor-core path: digit table, canonical layout, npad x K f16 (K = 48 or 64)
   int npad;             // tc_npad(n_out)
 };
 
 // tensor-core base conversion: 128 coefficients per MMA, K = 32 data slots
 // (4 bytes of at most 8 inputs) + 4 offset slots + 12 zero slots
+// tensor-core base conversion: M = 128 coefficients per MMA; the contraction width K is
+// 48 for at most 8 input limbs (unsigned offset slots) and 64 for 9..12 (signed offsets)
 constexpr int kTcM = 128, kTcK = 48, kTcMaxIn = 8;
+constexpr int kTcK12 = 64, kTcMaxIn12 = 12;
+__host__ __device__ constexpr int tc_k_for(int max_in) { return max_in <= kTcMaxIn ? kTcK : kTcK12; }
 __host__ __device__ constexpr int tc_npad(int n_out) { return (4 * n_out + 15) / 16 * 16; }
 
 constexpr int kMaxBconvGroups = 48;

@@ -22,7 +22,16 @@
 // The epilogue forms lo = S_0 + 2^8 S_1 and hi = S_2 + 2^8 S_3 (both < 2^30)
 // and reduces lo + 2^16 hi modulo p_o once: bit-identical to the CUDA-core path.
 //
-// A 128-coefficient tile of one group is one M = 128 MMA of three K = 16 steps;
+// Digits of 9..12 limbs (the paper's alpha = 12) use K = 64: 48 data slots and 8
+// offset slots whose B pieces may be negative (each in [-2048, 2048], summing to
+// 8192 - the row sum, which now reaches 48 * 255 = 12240).  The accumulator still
+// ends at 2^23 + S_b with S_b < 48 * 255^2 < 2^22; every partial sum lies between the
+// sum of the negative terms (> -2^22 * 1.0) and the sum of the positive ones
+// (< 1024 * 12240 + 2^22 < 2^24), so the fp32 accumulation stays exact in any order.
+// The epilogue's lo, hi < 2^30 + 2^22, so one conditional subtraction after adding
+// 2^16 hi mod p suffices for primes above 2^30 + 2^23.
+//
+// A 128-coefficient tile of one group is one M = 128 MMA of K / 16 steps;
 // persistent CTAs of 256 threads walk the tiles (see k_bconv_tc).  Operands sit
 // in shared memory in the canonical K-major layout without swizzle: 8 x 16-byte
 // core matrices, core matrices adjacent along K 128 bytes apart (leading byte
@@ -76,13 +85,18 @@ struct TcOut {  // per output prime of the current group, read by whole warps (b
 // input pairs into A, thread 0 issues the MMAs and commits to the mbarrier
 // (phase = tile parity), all wait (bounded), then each warp reads its lane
 // quarter for half of the outputs and writes the reduced results.
+template <int KT>
 __global__ void __launch_bounds__(kTcThreads, 4) k_bconv_tc(const __grid_constant__ BconvArgs a, const PrimeC *pc,
                                                          int logn, unsigned int *status, int npad_max,
                                                          int tiles_per_group) {
+  static_assert(KT == kTcK || KT == kTcK12, "K is 48 or 64");
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5;
-  constexpr uint32_t kRowBytes = kTcK * 2;           // one A / B row: 48 f16
-  constexpr uint32_t kSbo = (kTcK / 8) * 128u;       // 8-row group stride
+  constexpr uint32_t kRowBytes = KT * 2;             // one A / B row: K f16
+  constexpr uint32_t kSbo = (KT / 8) * 128u;         // 8-row group stride
+  constexpr int kDataChunks = KT == kTcK ? 4 : 6;    // 8-slot K chunks holding inputs (two each)
+  constexpr int kNch = kDataChunks / 2;              // data chunks built by each thread
+  constexpr uint32_t kBigPrime = KT == kTcK ? (1u << 30) : (1u << 30) + (1u << 23);
   uint8_t *sA = smem;
   uint8_t *sB = smem + kTcM * kRowBytes;
   TcOut *sO = reinterpret_cast<TcOut *>(sB + (size_t)npad_max * kRowBytes);
@@ -98,12 +112,16 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_bconv_tc(const __grid_constan
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) mbar_init(bar, 1);
-  // constant K chunks of A (written once): chunk 4 = the offset slots (1024) and
-  // four zero slots, chunk 5 = zero slots
+  // constant K chunks of A (written once): K = 48: chunk 4 = four offset slots (1024) and
+  // four zero slots, chunk 5 = zero slots; K = 64: chunk 6 = eight offset slots, chunk 7 = zero
   if (tid < kTcM) {
     uint8_t *row = sA + (tid >> 3) * kSbo + (tid & 7) * 16;
-    *reinterpret_cast<uint4 *>(row + 4 * 128) = make_uint4(0x64006400u, 0x64006400u, 0u, 0u);
-    *reinterpret_cast<uint4 *>(row + 5 * 128) = make_uint4(0u, 0u, 0u, 0u);
+    if (KT == kTcK)
+      *reinterpret_cast<uint4 *>(row + kDataChunks * 128) = make_uint4(0x64006400u, 0x64006400u, 0u, 0u);
+    else
+      *reinterpret_cast<uint4 *>(row + kDataChunks * 128) =
+          make_uint4(0x64006400u, 0x64006400u, 0x64006400u, 0x64006400u);
+    *reinterpret_cast<uint4 *>(row + (kDataChunks + 1) * 128) = make_uint4(0u, 0u, 0u, 0u);
   }
   tc_fence_before();
   __syncthreads();
@@ -119,18 +137,17 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_bconv_tc(const __grid_constan
   uint32_t phase = 0;
   bool ok = true;
   const int r = tid & (kTcM - 1);  // A row built by this thread
-  const int kc0 = tid >> 7;        // its K chunks: kc0 and kc0 + 2 (inputs 2 kc, 2 kc + 1)
+  const int kc0 = tid >> 7;        // its K chunks: kc0, kc0 + 2 (, kc0 + 4) (inputs 2 kc, 2 kc + 1)
+  uint32_t y[2 * kNch];
   auto load_inputs = [&](const BconvGroup *g, int nin, size_t m0) {
-    uint4 v;
-    uint32_t *w = reinterpret_cast<uint32_t *>(&v);
 #pragma unroll
-    for (int h = 0; h < 4; h++) {
+    for (int h = 0; h < 2 * kNch; h++) {
       const int j = 2 * (kc0 + 2 * (h >> 1)) + (h & 1);
-      w[h] = j < nin ? __ldg(g->in + (size_t)j * N + m0 + r) : 0u;
+      y[h] = j < nin ? __ldg(g->in + (size_t)j * N + m0 + r) : 0u;
     }
-    return v;
   };
-  uint4 y = make_uint4(0, 0, 0, 0);
+#pragma unroll
+  for (int h = 0; h < 2 * kNch; h++) y[h] = 0u;
   bool prefetched = false;  // y holds the current tile's inputs
   bool big_primes = true;   // the current group's output primes all exceed 2^30
   uint32_t *gout = nullptr; // the current group's output base
@@ -147,7 +164,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_bconv_tc(const __grid_constan
       uint4 *dst = reinterpret_cast<uint4 *>(sB);
       const int n16 = npad * (int)kRowBytes / 16;
       for (int i = tid; i < n16; i += kTcThreads) dst[i] = __ldg(src + i);
-      bool big = true;  // every output prime above 2^30: one conditional subtraction suffices
+      bool big = true;  // every output prime above kBigPrime: one conditional subtraction suffices
       for (int o = tid; o < n_out; o += kTcThreads) {
         const int2 m = gp->omap[o];
         const PrimeC p = pc[m.y];
@@ -157,7 +174,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_bconv_tc(const __grid_constan
         t.div32 = p.div32;
         t.off = (uint32_t)m.x << logn;
         sO[o] = t;
-        big = big && p.q > (1u << 30);
+        big = big && p.q > kBigPrime;
       }
       big_primes = __syncthreads_and(big ? 1 : 0) != 0;
       gout = gp->out;
@@ -167,11 +184,11 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_bconv_tc(const __grid_constan
     // The inputs were loaded during the previous tile (prefetch), except for the
     // first tile of a group.
     {
-      if (!prefetched) y = load_inputs(gp, n_in, n0);
+      if (!prefetched) load_inputs(gp, n_in, n0);
       uint8_t *row = sA + (r >> 3) * kSbo + (r & 7) * 16;
 #pragma unroll
-      for (int i = 0; i < 2; i++) {
-        const uint32_t y0 = i ? y.z : y.x, y1 = i ? y.w : y.y;
+      for (int i = 0; i < kNch; i++) {
+        const uint32_t y0 = y[2 * i], y1 = y[2 * i + 1];
         *reinterpret_cast<uint4 *>(row + (kc0 + 2 * i) * 128) =
             make_uint4(__byte_perm(y0, 0x64006400u, 0x7150), __byte_perm(y0, 0x64006400u, 0x7352),
                        __byte_perm(y1, 0x64006400u, 0x7150), __byte_perm(y1, 0x64006400u, 0x7352));
@@ -179,7 +196,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_bconv_tc(const __grid_constan
     }
     // prefetch the next tile's inputs when it belongs to the same group
     prefetched = tile + 1 < t1 && (tile + 1) / tiles_per_group == grp;
-    if (prefetched) y = load_inputs(gp, n_in, (size_t)((tile + 1) % tiles_per_group) * kTcM);
+    if (prefetched) load_inputs(gp, n_in, (size_t)((tile + 1) % tiles_per_group) * kTcM);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
     __syncthreads();
@@ -188,7 +205,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_bconv_tc(const __grid_constan
       const uint32_t aaddr = smem_addr(sA), baddr = smem_addr(sB);
       const uint32_t idesc = idesc_f16(kTcM, npad);
 #pragma unroll
-      for (int kk = 0; kk < kTcK / 16; kk++) {
+      for (int kk = 0; kk < KT / 16; kk++) {
         const uint64_t ad = smem_desc(aaddr + kk * 256u, 128u, kSbo);
         const uint64_t bd = smem_desc(baddr + kk * 256u, 128u, kSbo);
         const uint32_t acc = kk > 0 ? 1u : 0u;
@@ -228,10 +245,10 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_bconv_tc(const __grid_constan
         for (int i = 0; i < 8; i++) {
           if (i < cnt) {
             const TcOut t = sO[o0 + i];
-            // lo, hi < 2^30; the 0x4B000000 of each accumulator cancels modulo 2^32
+            // lo, hi < 2^30 + 2^22; the 0x4B000000 of each accumulator cancels modulo 2^32
             const uint32_t lo = rr[4 * i + 1] * 256u + rr[4 * i] - 0x4B000000u;
             const uint32_t hi = rr[4 * i + 3] * 256u + rr[4 * i + 2] - 0x4B000000u;
-            const uint32_t sum = lo + red2(shoup_lazy(hi, 65536u, t.w16s, t.q), t.q);  // < 2^30 + q
+            const uint32_t sum = lo + red2(shoup_lazy(hi, 65536u, t.w16s, t.q), t.q);  // < 2^30 + 2^22 + q
             const uint32_t v = big_primes ? red2(sum, t.q) : red2(shoup_lazy(sum, 1u, t.div32, t.q), t.q);
             gout[t.off + n] = v;
           }
@@ -252,20 +269,19 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_bconv_tc(const __grid_constan
 
 static int round16(int x) { return (x + 15) / 16 * 16; }
 
-cudaError_t launch_bconv_tc(const DevTables &t, const BconvArgs &a, int max_in, int max_out, cudaStream_t s) {
-  if (a.ngroups == 0) return cudaSuccess;
-  if (max_in > kTcMaxIn || max_out > 64) return cudaErrorInvalidValue;
+template <int KT>
+static cudaError_t bconv_tc_go(const DevTables &t, const BconvArgs &a, int max_out, cudaStream_t s) {
   const int npad = tc_npad(max_out);
   const int ncols = npad <= 32 ? 32 : npad <= 64 ? 64 : npad <= 128 ? 128 : 256;
   // operands, output constants, barrier; at least enough shared memory that no
   // more CTAs fit on an SM than its 512 tensor-memory columns hold
-  const int need = kTcM * kTcK * 2 + npad * kTcK * 2 + 64 * (int)sizeof(TcOut) + 64;
+  const int need = kTcM * KT * 2 + npad * KT * 2 + 64 * (int)sizeof(TcOut) + 64;
   const int per_sm = std::min(512 / ncols, 2048 / kTcThreads);
   int smem = std::max(need, 233472 / (per_sm + 1) + 1024);  // 228 KB of shared memory per SM
   if (smem > 232448) smem = 232448;
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_bconv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    cudaError_t e = cudaFuncSetAttribute(k_bconv_tc<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e != cudaSuccess) return e;
     configured = true;
   }
@@ -276,48 +292,63 @@ cudaError_t launch_bconv_tc(const DevTables &t, const BconvArgs &a, int max_in, 
   const int total = tiles_per_group * a.ngroups;
   const int grid = std::min(total, std::max(1, sms * per_sm));
   TraceScope ts(t, "bconv_tc", s);
-  k_bconv_tc<<<grid, kTcThreads, smem, s>>>(a, t.pc, t.logn, t.status, npad, tiles_per_group);
+  k_bconv_tc<KT><<<grid, kTcThreads, smem, s>>>(a, t.pc, t.logn, t.status, npad, tiles_per_group);
   note_launch();
   return cudaGetLastError();
 }
 
-// exact f16 bit pattern of an integer 0 <= v <= 2048
-static uint16_t f16_int(uint32_t v) {
+cudaError_t launch_bconv_tc(const DevTables &t, const BconvArgs &a, int max_in, int max_out, cudaStream_t s, int kt) {
+  if (a.ngroups == 0) return cudaSuccess;
+  if (max_out > 64) return cudaErrorInvalidValue;
+  if (kt == kTcK && max_in <= kTcMaxIn) return bconv_tc_go<kTcK>(t, a, max_out, s);
+  if (kt == kTcK12 && max_in <= kTcMaxIn12) return bconv_tc_go<kTcK12>(t, a, max_out, s);
+  return cudaErrorInvalidValue;
+}
+
+// exact f16 bit pattern of an integer -2048 <= v <= 2048
+static uint16_t f16_int(int v) {
   if (v == 0) return 0;
-  int e = 31 - __builtin_clz(v);
-  const uint32_t mant = e <= 10 ? (v << (10 - e)) & 0x3FFu : (v >> (e - 10)) & 0x3FFu;
-  return (uint16_t)(((uint32_t)(e + 15) << 10) | mant);
+  const uint16_t sign = v < 0 ? 0x8000u : 0u;
+  const uint32_t m = (uint32_t)(v < 0 ? -v : v);
+  const int e = 31 - __builtin_clz(m);
+  const uint32_t mant = e <= 10 ? (m << (10 - e)) & 0x3FFu : (m >> (e - 10)) & 0x3FFu;
+  return (uint16_t)(sign | ((uint32_t)(e + 15) << 10) | mant);
 }
 
 // Host side: the digit table of one conversion (inputs with primes q_in, outputs
 // with primes p_out, T[o][j] row-major) in the canonical layout of B
-// (tc_npad(n_out) x kTcK f16): row 4 o + b, column 4 j + a holds byte b of
-// (2^(8a) T[o][j]) mod p_o; columns 32..35 hold pieces (<= 2048) of
-// 8192 - (row sum of columns 0..31); all other entries are zero.
-std::vector<uint16_t> bconv_tc_table(const std::vector<uint32_t> &T, int n_in, const std::vector<uint32_t> &p_out) {
+// (tc_npad(n_out) x K f16): row 4 o + b, column 4 j + a holds byte b of
+// (2^(8a) T[o][j]) mod p_o; the offset columns (32..35 for K = 48, 48..51 for
+// K = 64) hold pieces of 8192 - (the row sum of the data columns): nonnegative and
+// <= 2048 for K = 48 (row sums <= 32 * 255), in [-2048, 2048] for K = 64; every
+// other entry is zero.
+std::vector<uint16_t> bconv_tc_table(const std::vector<uint32_t> &T, int n_in, const std::vector<uint32_t> &p_out,
+                                     int kt) {
   const int n_out = (int)p_out.size();
   const int npad = tc_npad(n_out);
-  std::vector<uint16_t> B((size_t)npad * kTcK, 0);
+  const int data = kt == kTcK ? 32 : 48;
+  std::vector<uint16_t> B((size_t)npad * kt, 0);
+  if (n_in > data / 4) return B;  // callers check n_in against the chosen K
   auto at = [&](int nn, int kk) -> uint16_t & {
-    return B[(size_t)(nn / 8) * (kTcK / 8) * 64 + (size_t)(kk / 8) * 64 + (nn % 8) * 8 + (kk % 8)];
+    return B[(size_t)(nn / 8) * (kt / 8) * 64 + (size_t)(kk / 8) * 64 + (nn % 8) * 8 + (kk % 8)];
   };
   for (int o = 0; o < n_out; o++) {
     const uint32_t p = p_out[o];
-    uint32_t rowsum[4] = {0, 0, 0, 0};
+    int rowsum[4] = {0, 0, 0, 0};
     for (int j = 0; j < n_in; j++)
       for (int a = 0; a < 4; a++) {
         const uint32_t ta = (uint32_t)(((unsigned __int128)T[(size_t)o * n_in + j] << (8 * a)) % p);
         for (int b = 0; b < 4; b++) {
-          const uint32_t byte = (ta >> (8 * b)) & 0xFFu;
+          const int byte = (int)((ta >> (8 * b)) & 0xFFu);
           at(4 * o + b, 4 * j + a) = f16_int(byte);
           rowsum[b] += byte;
         }
       }
     for (int b = 0; b < 4; b++) {
-      uint32_t rest = 8192u - rowsum[b];  // rowsum <= 32 * 255 = 8160
+      int rest = 8192 - rowsum[b];  // K = 48: >= 8192 - 8160; K = 64: >= 8192 - 12240
       for (int e = 0; e < 4; e++) {
-        const uint32_t piece = std::min(rest, 2048u);
-        at(4 * o + b, 32 + e) = f16_int(piece);
+        const int piece = std::max(-2048, std::min(rest, 2048));
+        at(4 * o + b, data + e) = f16_int(piece);
         rest -= piece;
       }
     }

@@ -117,6 +117,9 @@ static int build_tables(fhe_ctx *c) {
   const uint32_t N = c->N;
   const int NP = c->L + c->K;
   const std::vector<uint32_t> &pr = c->primes;
+  // the tensor-core BConv's contraction width for this digit size and special-prime count
+  const int wide = std::max(c->alpha, c->K);
+  c->tabs.tc_k = wide <= fhe::kTcMaxIn ? fhe::kTcK : wide <= fhe::kTcMaxIn12 ? fhe::kTcK12 : 0;
   // per-prime constants
   std::vector<PrimeC> pcs(NP);
   for (int i = 0; i < NP; i++) {
@@ -192,8 +195,9 @@ static int build_tables(fhe_ctx *c) {
       CUDA_OR_FAIL(upload(&c->modup_map[(size_t)(level - 1) * c->dnum + j], om));
       std::vector<uint32_t> pout;
       for (const int2 &m : om) pout.push_back(pr[m.y]);
-      if (hi - lo <= fhe::kTcMaxIn)  // tensor-core tables exist for digits of at most 8 limbs
-        CUDA_OR_FAIL(upload(&c->modup_Btc[(size_t)(level - 1) * c->dnum + j], fhe::bconv_tc_table(T, hi - lo, pout)));
+      if (c->tabs.tc_k)  // tensor-core tables (digits of at most 8 limbs: K = 48; at most 12: K = 64)
+        CUDA_OR_FAIL(upload(&c->modup_Btc[(size_t)(level - 1) * c->dnum + j],
+                            fhe::bconv_tc_table(T, hi - lo, pout, c->tabs.tc_k)));
     }
   }
   CUDA_OR_FAIL(upload(&c->d_mu_scale, mu_scale));
@@ -233,8 +237,9 @@ static int build_tables(fhe_ctx *c) {
   CUDA_OR_FAIL(upload(&c->d_pmod, pmod));
   CUDA_OR_FAIL(upload(&c->d_mdT, mdT));
   CUDA_OR_FAIL(upload(&c->d_mdmap, mdmap));
-  if (K <= fhe::kTcMaxIn)
-    CUDA_OR_FAIL(upload(&c->d_md_Btc, fhe::bconv_tc_table(mdT, K, std::vector<uint32_t>(pr.begin(), pr.begin() + L))));
+  if (c->tabs.tc_k)
+    CUDA_OR_FAIL(upload(&c->d_md_Btc, fhe::bconv_tc_table(mdT, K, std::vector<uint32_t>(pr.begin(), pr.begin() + L),
+                                                          c->tabs.tc_k)));
   CUDA_OR_FAIL(upload(&c->d_status, std::vector<unsigned int>(1, 0u)));
   c->tabs.status = c->d_status;
 
@@ -442,9 +447,9 @@ extern "C" int fhe_ctx_set_bconv(fhe_ctx *c, int mode) {
   if (mode != FHE_BCONV_SCALAR && mode != FHE_BCONV_TC) return fhe_fail(FHE_EINVAL, "fhe_ctx_set_bconv: mode %d", mode);
   if (mode == FHE_BCONV_TC && !fhe_tc_available())
     return fhe_fail(FHE_EUNSUPPORTED, "fhe_ctx_set_bconv: tensor-core base conversion not built");
-  if (mode == FHE_BCONV_TC && (c->alpha > fhe::kTcMaxIn || c->K > fhe::kTcMaxIn))
+  if (mode == FHE_BCONV_TC && !c->tabs.tc_k)
     return fhe_fail(FHE_EUNSUPPORTED, "fhe_ctx_set_bconv: tensor-core base conversion needs alpha <= %d and K <= %d",
-                    fhe::kTcMaxIn, fhe::kTcMaxIn);
+                    fhe::kTcMaxIn12, fhe::kTcMaxIn12);
   c->bconv_mode = mode;
   return FHE_OK;
 }

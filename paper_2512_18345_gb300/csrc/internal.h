@@ -37,6 +37,7 @@ struct DevTables {
   int ip_ctas_per_sm;      // resident CTAs per SM of the streaming inner product (1 or 2; autotuned)
   int ntt_otf;             // block passes form their register twiddles on the fly
   int ntt_single;          // 2^16-point transforms in one cluster launch instead of two passes
+  int tc_k;                // K of the context's tensor-core BConv tables (48 or 64; 0: none)
 };
 
 // bracket one launch with trace events when tracing is on
@@ -52,7 +53,9 @@ struct TraceScope {
 };
 void note_launch();
 // the byte-digit table of the tensor-core base conversion (host side)
-std::vector<uint16_t> bconv_tc_table(const std::vector<uint32_t> &T, int n_in, const std::vector<uint32_t> &p_out);
+// K = kt (48 for at most 8 inputs, 64 for at most 12)
+std::vector<uint16_t> bconv_tc_table(const std::vector<uint32_t> &T, int n_in, const std::vector<uint32_t> &p_out,
+                                     int kt);
 
 // One NTT pass over every limb of `sl` (column or block pass, forward or inverse).
 cudaError_t launch_ntt_pass(const DevTables &t, bool column, bool fwd, int pro, int epi, const SegList &sl,
@@ -69,7 +72,8 @@ cudaError_t launch_ntt_single(const DevTables &t, bool fwd, int pro, int epi, co
 // how many 16-CTA clusters of the single-pass NTT the current device holds at once (0: none)
 int ntt_single_pass_clusters();
 cudaError_t launch_bconv(const DevTables &t, const BconvArgs &a, int max_in, int max_out, cudaStream_t s);
-cudaError_t launch_bconv_tc(const DevTables &t, const BconvArgs &a, int max_in, int max_out, cudaStream_t s);
+// kt: the K of the groups' tables (48: max_in <= 8; 64: max_in <= 12)
+cudaError_t launch_bconv_tc(const DevTables &t, const BconvArgs &a, int max_in, int max_out, cudaStream_t s, int kt);
 cudaError_t launch_ew(const DevTables &t, int op, const SegList &sl, cudaStream_t s);
 // key inner product (both halves) for the ext limbs of sl; seg.dst = u_0[t0]
 // beta_max: the largest digit count among the segments' items (sizes the stages)

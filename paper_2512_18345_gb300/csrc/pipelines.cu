@@ -405,7 +405,7 @@ extern "C" int fhe_moddown(fhe_ctx *c, const uint32_t *u, int level, uint32_t *o
   g.Btc = c->d_md_Btc;
   g.npad = tc_npad(level);
   if (c->bconv_mode == FHE_BCONV_TC)
-    LAUNCH_OR_FAIL(launch_bconv_tc(c->tabs, ba, K, level, s));
+    LAUNCH_OR_FAIL(launch_bconv_tc(c->tabs, ba, K, level, s, c->tabs.tc_k));
   else
     LAUNCH_OR_FAIL(launch_bconv(c->tabs, ba, K, level, s));
   nr.add(mkseg(R, R, level, 0));
@@ -433,8 +433,10 @@ extern "C" int fhe_bconv(fhe_ctx *c, const uint32_t *in, const int *in_idx, int 
     if (out_idx[i] < 0 || out_idx[i] >= NP) return fhe_fail(FHE_EINVAL, "fhe_bconv: out prime index");
   const size_t N = c->N;
   if (overlaps(in, 4 * N * n_in, out, 4 * N * n_out)) return fhe_fail(FHE_EALIAS, "fhe_bconv: out overlaps in");
-  if (c->bconv_mode == FHE_BCONV_TC && n_in > kTcMaxIn)
-    return fhe_fail(FHE_EUNSUPPORTED, "fhe_bconv: tensor-core base conversion takes at most %d inputs", kTcMaxIn);
+  const bool tc = c->bconv_mode == FHE_BCONV_TC;
+  if (tc && n_in > kTcMaxIn12)
+    return fhe_fail(FHE_EUNSUPPORTED, "fhe_bconv: tensor-core base conversion takes at most %d inputs", kTcMaxIn12);
+  const int kt = tc_k_for(n_in);
   const std::vector<uint32_t> &pr = c->primes;
   // host tables: pre-factor (Qstar/q_j)^-1 mod q_j and T[o][j] = (Qstar/q_j) mod p_o
   std::vector<uint2> pre(n_in);
@@ -466,7 +468,7 @@ extern "C" int fhe_bconv(fhe_ctx *c, const uint32_t *in, const int *in_idx, int 
   uint16_t *dB = nullptr;
   std::vector<uint32_t> pout;
   for (int o = 0; o < n_out; o++) pout.push_back(pr[out_idx[o]]);
-  const std::vector<uint16_t> Btc = bconv_tc_table(T, n_in, pout);
+  const std::vector<uint16_t> Btc = tc ? bconv_tc_table(T, n_in, pout, kt) : std::vector<uint16_t>(8, 0);
   auto cleanup = [&]() {
     cudaFree(dT);
     cudaFree(dM);
@@ -508,8 +510,7 @@ extern "C" int fhe_bconv(fhe_ctx *c, const uint32_t *in, const int *in_idx, int 
   g.Btc = dB;
   g.npad = tc_npad(n_out);
   if (rc == FHE_OK) {
-    cudaError_t e = c->bconv_mode == FHE_BCONV_TC ? launch_bconv_tc(c->tabs, ba, n_in, n_out, s)
-                                                  : launch_bconv(c->tabs, ba, n_in, n_out, s);
+    cudaError_t e = tc ? launch_bconv_tc(c->tabs, ba, n_in, n_out, s, kt) : launch_bconv(c->tabs, ba, n_in, n_out, s);
     if (e != cudaSuccess) rc = fhe_fail(FHE_ECUDA, "fhe_bconv: %s", cudaGetErrorString(e));
   }
   // the temporary tables are released once the stream has consumed them

@@ -328,7 +328,7 @@ static cudaError_t launch_stage(fhe_ctx *c, const Stage &st, const SegList &sl, 
     case Stage::EW: return launch_ew(c->tabs, st.ewop, sl, q);
     case Stage::IP: return launch_ip(c->tabs, sl, st.gather_own, st.gather_ext, c->dnum, q);
     case Stage::BCONV:
-      return c->bconv_mode == FHE_BCONV_TC ? launch_bconv_tc(c->tabs, ba, st.max_in, st.max_out, q)
+      return c->bconv_mode == FHE_BCONV_TC ? launch_bconv_tc(c->tabs, ba, st.max_in, st.max_out, q, c->tabs.tc_k)
                                            : launch_bconv(c->tabs, ba, st.max_in, st.max_out, q);
     case Stage::FORK: {
       cudaError_t e = cudaEventRecord(ev_fork, s);

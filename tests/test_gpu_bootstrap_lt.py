@@ -118,12 +118,13 @@ def test_chain_small_ring_bit_exact_and_decodes(fhe_lib):
     ctx.close()
 
 
-@pytest.mark.parametrize("kind,which,level_key", [("cts", 0, "cts_level"), ("stc", 1, "stc_level")])
-def test_level_parity_bootstrapping_shape(fhe_lib, kind, which, level_key):
+@pytest.mark.parametrize("kind,which,level_key,tc", [("cts", 0, "cts_level", False), ("stc", 1, "stc_level", False),
+                                                     ("cts", 1, "cts_level", True)])
+def test_level_parity_bootstrapping_shape(fhe_lib, kind, which, level_key, tc):
     """N = 2^16, L = 48, K = 12, dnum = 4: the first CoeffToSlot level at l = 48 (32 diagonals,
-    15 rotating baby steps and one rotating giant step) and the middle SlotToCoeff level at
-    l = 33 (63 diagonals, 15 + 3); CUDA-core BConv (the tensor-core kernel takes at most 8
-    input limbs)."""
+    15 rotating baby steps and one rotating giant step), the middle SlotToCoeff level at
+    l = 33 (63 diagonals, 15 + 3) with the CUDA-core BConv, and the second CoeffToSlot level
+    with the tensor-core BConv (its K = 64 shape for the 12-limb digits)."""
     from paper_2512_18345_gb300 import binding
     name = "cts_stc_N65536_L48_a12"
     P = inputs.workload_params(name)
@@ -131,8 +132,9 @@ def test_level_parity_bootstrapping_shape(fhe_lib, kind, which, level_key):
     W = inputs.WORKLOADS[name]
     plan = inputs.transform_plans(P.N, W["levels"], kind)[which]
     level = W[level_key] - (which if kind == "cts" else 0)
-    g = inputs.rng(1300 + which)
+    g = inputs.rng(1300 + which + (50 if tc else 0))
     ctx = binding.Context.from_params(P)
+    ctx.set_bconv(binding.FHE_BCONV_TC if tc else binding.FHE_BCONV_SCALAR)
     keys = {}
     for r in plan.rotations():
         keys[r] = rand_key(P, g)

@@ -1,7 +1,7 @@
 """The paper's own key-switching shapes (Table "ks-param"): (l, alpha, beta) =
-(24, 12, 2) and (48, 12, 4) with K = alpha = 12 at N = 2^16, 31-bit primes.
-alpha = 12 exceeds the tensor-core conversion's exactness bound (8 inputs), so
-these run the CUDA-core conversion; every residue equals the oracle's."""
+(24, 12, 2) and (48, 12, 4) with K = alpha = 12 at N = 2^16, 31-bit primes, with
+the CUDA-core conversion and with the tensor-core conversion (its K = 64 shape
+for digits of 9..12 limbs); every residue equals the oracle's."""
 import numpy as np
 import pytest
 
@@ -18,15 +18,14 @@ def rand_key(P, g):
 
 
 @pytest.mark.parametrize("name", SHAPES)
-def test_paper_shape_keyswitch_rotate_and_batch(fhe_lib, name):
+@pytest.mark.parametrize("tc", [False, True])
+def test_paper_shape_keyswitch_rotate_and_batch(fhe_lib, name, tc):
     from paper_2512_18345_gb300 import binding
     P = inputs.workload_params(name)
     OP = oracle.OracleParams.from_params(P)
     ctx = binding.Context.from_params(P)
-    with pytest.raises(binding.FheError) as err:  # alpha = 12 > 8
-        ctx.set_bconv(binding.FHE_BCONV_TC)
-    assert err.value.code == binding.FHE_EUNSUPPORTED
-    g = inputs.rng(inputs.WORKLOADS[name]["seed"])
+    ctx.set_bconv(binding.FHE_BCONV_TC if tc else binding.FHE_BCONV_SCALAR)
+    g = inputs.rng(inputs.WORKLOADS[name]["seed"] + (7 if tc else 0))
     key = rand_key(P, g)
     ctx.set_relin_key(binding.to_device(key))
     d = inputs.uniform_residues(g, P.q, P.N)
@@ -53,4 +52,15 @@ def test_paper_shape_keyswitch_rotate_and_batch(fhe_lib, name):
         ctx.sync()
         assert np.array_equal(binding.to_numpy(it["out"]), binding.to_numpy(single))
     plan.close()
+    ctx.close()
+
+
+def test_tensor_core_limits(fhe_lib):
+    """The tensor-core conversion takes digits and special-prime counts of at most 12 limbs."""
+    from paper_2512_18345_gb300 import binding
+    P = inputs.make_params(1 << 12, 13, 13, 1, bits=30)  # alpha = K = 13
+    ctx = binding.Context.from_params(P)
+    with pytest.raises(binding.FheError) as err:
+        ctx.set_bconv(binding.FHE_BCONV_TC)
+    assert err.value.code == binding.FHE_EUNSUPPORTED
     ctx.close()

@@ -46,7 +46,8 @@ def rand_key(P, g):
     return np.stack([np.stack([inputs.uniform_residues(g, P.primes, P.N) for _ in range(2)]) for _ in range(P.dnum)])
 
 
-@pytest.mark.parametrize("n_in,n_out", [(1, 5), (3, 29), (8, 24), (4, 16), (2, 30)])
+@pytest.mark.parametrize("n_in,n_out", [(1, 5), (3, 29), (8, 24), (4, 16), (2, 30), (9, 20), (12, 24), (11, 21),
+                                         (12, 1)])
 def test_bconv_tc_parity(tc, n_in, n_out):
     P, OP, ctx = tc
     g = inputs.rng(300 + n_in)
@@ -60,17 +61,18 @@ def test_bconv_tc_parity(tc, n_in, n_out):
 
 
 @pytest.mark.parametrize("fill", ["max", "zero", "ones"])
-def test_bconv_tc_extremes(tc, fill):
+@pytest.mark.parametrize("n_in", [8, 12])
+def test_bconv_tc_extremes(tc, fill, n_in):
     P, OP, ctx = tc
-    in_idx, out_idx = list(range(24, 32)), list(range(24))
+    in_idx, out_idx = list(range(32 - n_in, 32)), list(range(24))
     pin = [P.primes[i] for i in in_idx]
     pout = [P.primes[i] for i in out_idx]
     if fill == "max":
         x = np.array([[q - 1] * P.N for q in pin], np.uint32)
     elif fill == "zero":
-        x = np.zeros((8, P.N), np.uint32)
+        x = np.zeros((n_in, P.N), np.uint32)
     else:
-        x = np.ones((8, P.N), np.uint32)
+        x = np.ones((n_in, P.N), np.uint32)
     got = host(ctx, ctx.bconv(dev(x), in_idx, out_idx))
     assert np.array_equal(got, oracle.bconv(x, pin, pout))
 

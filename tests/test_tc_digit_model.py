@@ -8,13 +8,17 @@ of 8192 - row sum) make every fp32 accumulator exactly 2^23 + S_b.  This
 model checks, in exact integers, every step the exactness argument relies on:
 the f16 bit patterns, the nonnegativity of all terms, the 2^24 bound on every
 partial sum, the accumulator's bit pattern, and the epilogue's reduction,
-against the plain definition of the sum, for random and worst-case inputs."""
+against the plain definition of the sum, for random and worst-case inputs.
+Digits of 9..12 limbs use a K = 64 shape whose offset pieces may be negative;
+`conversion12` checks that every partial sum still stays inside (-2^24, 2^24)."""
 import struct
 
 import numpy as np
 import pytest
 
 K_DATA, K_TOTAL = 32, 48
+# digits of 9..12 limbs: K = 64, 48 data slots, 8 offset slots with signed B pieces
+K_DATA12, K_TOTAL12 = 48, 64
 
 
 def byte_perm(x: int, y: int, s: int) -> int:
@@ -27,12 +31,14 @@ def f16_value(h: int) -> float:
 
 
 def f16_int(v: int) -> int:
-    """f16 bit pattern of an integer 0 <= v <= 2048 (the table builder's rule)."""
+    """f16 bit pattern of an integer -2048 <= v <= 2048 (the table builder's rule)."""
     if v == 0:
         return 0
+    sign = 0x8000 if v < 0 else 0
+    v = abs(v)
     e = v.bit_length() - 1
     mant = ((v << (10 - e)) & 0x3FF) if e <= 10 else ((v >> (e - 10)) & 0x3FF)
-    return ((e + 15) << 10) | mant
+    return sign | ((e + 15) << 10) | mant
 
 
 def f32_bits(x: int) -> int:
@@ -87,8 +93,56 @@ def conversion(y, T, p):
     return red2(s, p) if p > 2 ** 30 else red2(shoup_lazy(s, 1, (1 << 32) // p, p), p)
 
 
+def conversion12(y, T, p):
+    """The K = 64 shape (up to 12 inputs): the offset pieces may be negative, so the exactness
+    argument is that every partial sum, in any order, lies between the sum of the negative
+    terms and the sum of the positive ones, both inside (-2^24, 2^24)."""
+    n_in = len(y)
+    assert n_in <= 12
+    A = [0.0] * K_TOTAL12
+    for j in range(12):
+        yj = y[j] if j < n_in else 0
+        w0, w1 = byte_perm(yj, 0x64006400, 0x7150), byte_perm(yj, 0x64006400, 0x7352)
+        for idx, h in enumerate((w0 & 0xFFFF, w0 >> 16, w1 & 0xFFFF, w1 >> 16)):
+            A[4 * j + idx] = f16_value(h)
+    for e in range(8):
+        A[K_DATA12 + e] = 1024.0
+    acc = []
+    for b in range(4):
+        B = [0.0] * K_TOTAL12
+        for j in range(n_in):
+            for a in range(4):
+                ta = (T[j] << (8 * a)) % p
+                B[4 * j + a] = f16_value(f16_int((ta >> (8 * b)) & 0xFF))
+        rest = 8192 - int(sum(B[:K_DATA12]))
+        for e in range(4):
+            piece = max(-2048, min(rest, 2048))
+            B[K_DATA12 + e] = f16_value(f16_int(piece))
+            rest -= piece
+        assert rest == 0
+        terms = [int(x) * int(z) for x, z in zip(A, B)]
+        neg = sum(t for t in terms if t < 0)
+        pos = sum(t for t in terms if t > 0)
+        assert -2 ** 24 < neg and pos < 2 ** 24     # every partial sum is an exact fp32 integer
+        total = sum(terms)
+        assert 2 ** 23 <= total < 2 ** 24
+        acc.append(f32_bits(total))
+    s_b = [u - 0x4B000000 for u in acc]
+    assert all(0 <= s < 2 ** 22 for s in s_b)
+    lo = (acc[1] * 256 + acc[0] - 0x4B000000) & 0xFFFFFFFF
+    hi = (acc[3] * 256 + acc[2] - 0x4B000000) & 0xFFFFFFFF
+    assert lo < 2 ** 30 + 2 ** 22 and hi < 2 ** 30 + 2 ** 22
+    w16s = (65536 << 32) // p
+    s = lo + red2(shoup_lazy(hi, 65536, w16s, p), p)
+    assert s < 2 ** 32
+    big = p > 2 ** 30 + 2 ** 23
+    if big:
+        assert s < 2 * p                             # one conditional subtraction suffices
+    return red2(s, p) if big else red2(shoup_lazy(s, 1, (1 << 32) // p, p), p)
+
+
 def test_f16_patterns():
-    for v in range(0, 2049):
+    for v in range(-2048, 2049):
         assert f16_value(f16_int(v)) == v
     for b in range(256):
         assert f16_value(0x6400 | b) == 1024 + b
@@ -114,3 +168,40 @@ def test_random_and_extreme_conversions(p):
         else:
             y = [int(v) for v in rng.integers(0, p, n_in)]
         assert conversion(y, T, p) == sum(a * b for a, b in zip(y, T)) % p
+
+
+@pytest.mark.parametrize("p", PRIMES)
+def test_wide_digit_conversions(p):
+    """9..12 inputs (K = 64): random, all-(p - 1) tables and inputs above every residue."""
+    rng = np.random.default_rng(p + 12)
+    for trial in range(60):
+        n_in = int(rng.integers(9, 13)) if trial % 5 else int(rng.integers(1, 9))
+        if trial % 3 == 0:
+            T = [p - 1] * n_in
+        else:
+            T = [int(t) for t in rng.integers(0, p, n_in)]
+        if trial % 4 == 0:
+            y = [2 ** 31 - 1] * n_in
+        else:
+            y = [int(v) for v in rng.integers(0, p, n_in)]
+        assert conversion12(y, T, p) == sum(a * b for a, b in zip(y, T)) % p
+
+
+def test_wide_digit_worst_row_sums():
+    """Row sums at both extremes: every table byte 255 (rest = 8192 - 12240 < 0) and every byte 0
+    (rest = 8192): the offset pieces stay within [-2048, 2048] and the sums stay exact."""
+    p = PRIMES[0]
+    # T whose shifted residues have all bytes 0xFF is not constructible for every a, so check the
+    # offset split and the bound on synthetic byte rows directly
+    for row in ([255] * 48, [0] * 48, [255] * 24 + [0] * 24):
+        rest = 8192 - sum(row)
+        pieces = []
+        for _ in range(4):
+            piece = max(-2048, min(rest, 2048))
+            pieces.append(piece)
+            rest -= piece
+        assert rest == 0 and all(-2048 <= x <= 2048 for x in pieces)
+        A = [1024 + 255] * 48 + [1024] * 4
+        terms = [a * b for a, b in zip(A, row + pieces)]
+        assert sum(t for t in terms if t > 0) < 2 ** 24 and sum(t for t in terms if t < 0) > -2 ** 24
+    assert conversion12([p - 1] * 12, [p - 1] * 12, p) == (12 * (p - 1) * (p - 1)) % p
