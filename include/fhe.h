@@ -125,6 +125,12 @@ FHE_API int fhe_ctx_sync(fhe_ctx *ctx);
  * (and clears it).  No fault, trap or unbounded wait is involved.
  */
 FHE_API int fhe_selftest_wait_timeout(fhe_ctx *ctx, fhe_stream stream);
+/* Cap the device memory the context may still grow into (workspace slots, the
+ * linear transforms' scratch, switching-key copies), in bytes; 0 (the default)
+ * removes the cap.  A call that would grow past it returns FHE_ENOMEM before
+ * allocating or launching anything, and the context stays usable (memory already
+ * held is kept).  Also the host-side way to inject allocation failures in tests. */
+FHE_API int fhe_ctx_set_memory_limit(fhe_ctx *ctx, size_t bytes);
 /* Fuse stage epilogues (1, default) or run the plain per-kernel pipeline (0).  Same bits. */
 FHE_API int fhe_ctx_set_fused(fhe_ctx *ctx, int fused);
 /* Complementary pipelining (Section IV-B) in the fused pipeline: with `on`

@@ -34,7 +34,7 @@ EXPORTS = (
     "fhe_rotate_hoisted", "fhe_linear_transform", "fhe_linear_transform_dh", "fhe_pmult", "fhe_add", "fhe_ntt", "fhe_intt", "fhe_modup", "fhe_moddown",
     "fhe_bconv", "fhe_batch_plan", "fhe_batch_launch", "fhe_plan_destroy", "fhe_plan_kernel_count",
     "fhe_plan_groups", "fhe_ctx_set_batch",
-    "fhe_trace_enable", "fhe_trace_read", "fhe_probe_bandwidth", "fhe_autotune", "fhe_autotune_cached", "fhe_ctx_set_pipelining", "fhe_ctx_set_ntt", "fhe_selftest_wait_timeout", "fhe_bconv_noalloc", "fhe_last_error",
+    "fhe_trace_enable", "fhe_trace_read", "fhe_probe_bandwidth", "fhe_autotune", "fhe_autotune_cached", "fhe_ctx_set_pipelining", "fhe_ctx_set_ntt", "fhe_ctx_set_memory_limit", "fhe_selftest_wait_timeout", "fhe_bconv_noalloc", "fhe_last_error",
 )
 
 
@@ -124,6 +124,7 @@ def lib() -> ctypes.CDLL:
         "fhe_selftest_wait_timeout": [vp, vp],
         "fhe_ctx_set_pipelining": [vp, ctypes.c_int],
         "fhe_ctx_set_ntt": [vp, ctypes.c_int],
+        "fhe_ctx_set_memory_limit": [vp, ctypes.c_size_t],
         "fhe_autotune": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(TuneResult), vp],
         "fhe_autotune_cached": [vp, ctypes.c_char_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                 ctypes.POINTER(TuneResult), vp],
@@ -284,6 +285,10 @@ class Context:
         else:
             check(lib().fhe_autotune(self.h, level, n_items, flags, ctypes.byref(r), _stream(stream)))
         return {f: getattr(r, f) for f, _ in TuneResult._fields_}
+
+    def set_memory_limit(self, nbytes: int) -> None:
+        """Cap the device memory the context may still grow into (0: no cap)."""
+        check(lib().fhe_ctx_set_memory_limit(self.h, int(nbytes)))
 
     def set_ntt(self, flags: int) -> None:
         """NTT kernel variants: 0, FHE_NTT_OTF, FHE_NTT_SINGLE_PASS or both."""

@@ -284,6 +284,13 @@ int ensure_lanes(fhe_ctx *c, int n) {
   return FHE_OK;
 }
 
+int fhe_ctx::reserve(size_t bytes, const char *what) {
+  if (mem_limit && grown_bytes + bytes > mem_limit)
+    return fhe_fail(FHE_ENOMEM, "%s: %zu more bytes exceed the context's memory limit (%zu of %zu in use)", what,
+                    bytes, grown_bytes, mem_limit);
+  return FHE_OK;
+}
+
 int ensure_slots(fhe_ctx *c, int n) {
   const size_t N = c->N;
   const int L = c->L, K = c->K, B = c->beta(L);
@@ -291,7 +298,10 @@ int ensure_slots(fhe_ctx *c, int n) {
   c->slot_bytes = limbs * N * sizeof(uint32_t);
   while ((int)c->slots.size() < n) {
     fhe_ctx::Slot s;
+    const int rc = c->reserve(c->slot_bytes, "workspace slot");
+    if (rc != FHE_OK) return rc;
     CUDA_OR_FAIL(cudaMalloc(&s.base, c->slot_bytes));
+    c->grown_bytes += c->slot_bytes;
     uint32_t *p = s.base;
     auto take = [&](size_t l) {
       uint32_t *r = p;
@@ -521,6 +531,12 @@ extern "C" int fhe_ctx_set_ntt(fhe_ctx *c, int flags) {
   return FHE_OK;
 }
 
+extern "C" int fhe_ctx_set_memory_limit(fhe_ctx *c, size_t bytes) {
+  if (!c) return fhe_fail(FHE_EINVAL, "fhe_ctx_set_memory_limit: null");
+  c->mem_limit = bytes;
+  return FHE_OK;
+}
+
 extern "C" int fhe_ctx_set_fused(fhe_ctx *c, int fused) {
   if (!c) return fhe_fail(FHE_EINVAL, "fhe_ctx_set_fused: null");
   c->fused = fused ? 1 : 0;
@@ -537,7 +553,12 @@ uint32_t fhe_galois_elt(int32_t rot, uint32_t N) {
 
 static int set_key(fhe_ctx *c, uint32_t **slot, const uint32_t *key, cudaStream_t s) {
   const size_t bytes = (size_t)c->dnum * 2 * (c->L + c->K) * c->N * sizeof(uint32_t);
-  if (!*slot) CUDA_OR_FAIL(cudaMalloc(slot, bytes));
+  if (!*slot) {
+    const int rc = c->reserve(bytes, "switching key");
+    if (rc != FHE_OK) return rc;
+    CUDA_OR_FAIL(cudaMalloc(slot, bytes));
+    c->grown_bytes += bytes;
+  }
   c->order_stream(s);
   CUDA_OR_FAIL(cudaMemcpyAsync(*slot, key, bytes, cudaMemcpyDefault, s));
   return FHE_OK;

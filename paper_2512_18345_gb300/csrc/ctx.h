@@ -62,6 +62,10 @@ struct fhe_ctx {
   uint32_t *lt_scratch = nullptr;  // linear transform: baby / giant rotations and inner sums
   size_t lt_words = 0;
   size_t ws_bytes = 0;
+  // growable device memory (workspace slots, transform scratch, key copies) and its cap
+  // (0: none); growth past the cap fails with FHE_ENOMEM before any allocation
+  size_t grown_bytes = 0, mem_limit = 0;
+  int reserve(size_t bytes, const char *what);
 
   // cross-stream ordering of calls on this context
   cudaStream_t last_stream = nullptr;

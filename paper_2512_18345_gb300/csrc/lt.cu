@@ -35,10 +35,11 @@ __device__ __forceinline__ int limb_prime(int i, int level, int L) { return i < 
 
 // out_g[c][i][n] = sum_b diag[didx[g][b]][i][n] babies[b][c][i][n] mod (prime of limb i); one
 // thread per V consecutive coefficients of one limb (vector loads) and group of kGsub giant
-// steps (blockIdx.y; the groups re-read the baby values); two baby steps' loads are issued
-// before their multiply-accumulates, and the accumulators are reduced after every second
-// baby step (a reduced value plus two 62-bit products stays below 2^64).
+// steps (blockIdx.y; the groups re-read the baby values); kDiagBatch baby steps' loads are
+// issued before their multiply-accumulates, and the accumulators are reduced after each
+// such batch.
 constexpr int kGsub = 4;
+constexpr int kDiagBatch = 2;  // baby steps whose loads are issued together
 template <int V>
 struct VecU32;
 template <>
@@ -87,17 +88,20 @@ __global__ void __launch_bounds__(256) k_diagmac(const __grid_constant__ DiagArg
   for (int g = 0; g < kGsub; g++)
 #pragma unroll
     for (int e = 0; e < V; e++) acc[0][g][e] = acc[1][g][e] = 0;
-  for (int b = 0; b < a.nb; b += 2) {
-    const bool two = b + 1 < a.nb;
-    uint32_t x[2][2][V], d[2][kGsub][V];
+  // kDiagBatch baby steps' loads in flight before their multiply-accumulates; a reduced
+  // accumulator plus three 62-bit products stays below 2^64, so kDiagBatch <= 3
+  static_assert(kDiagBatch >= 1 && kDiagBatch <= 3, "at most three products between reductions");
+  for (int b = 0; b < a.nb; b += kDiagBatch) {
+    uint32_t x[kDiagBatch][2][V], d[kDiagBatch][kGsub][V];
 #pragma unroll
-    for (int h = 0; h < 2; h++) {
-      const int bb = two ? b + h : b;
+    for (int h = 0; h < kDiagBatch; h++) {
+      const bool live = b + h < a.nb;
+      const int bb = live ? b + h : b;
       Vec::load(a.babies[bb] + (size_t)i * N + n, x[h][0]);
       Vec::load(a.babies[bb] + poly + (size_t)i * N + n, x[h][1]);
 #pragma unroll
       for (int g = 0; g < kGsub; g++) {
-        const int k = g < ng ? a.didx[(g0 + g) * a.nb + bb] : -1;
+        const int k = (live && g < ng) ? a.didx[(g0 + g) * a.nb + bb] : -1;
         if (k >= 0) {
           Vec::load(dbase + (size_t)k * poly, d[h][g]);
         } else {
@@ -107,8 +111,7 @@ __global__ void __launch_bounds__(256) k_diagmac(const __grid_constant__ DiagArg
       }
     }
 #pragma unroll
-    for (int h = 0; h < 2; h++) {
-      if (h == 1 && !two) break;
+    for (int h = 0; h < kDiagBatch; h++)
 #pragma unroll
       for (int g = 0; g < kGsub; g++)
 #pragma unroll
@@ -116,7 +119,6 @@ __global__ void __launch_bounds__(256) k_diagmac(const __grid_constant__ DiagArg
           acc[0][g][e] += (uint64_t)d[h][g][e] * x[h][0][e];
           acc[1][g][e] += (uint64_t)d[h][g][e] * x[h][1][e];
         }
-    }
 #pragma unroll
     for (int g = 0; g < kGsub; g++)
 #pragma unroll
@@ -225,12 +227,18 @@ static bool ranges_overlap(const void *a, size_t abytes, const void *b, size_t b
 
 static int ensure_lt_scratch(fhe_ctx *c, size_t words) {
   if (c->lt_words >= words) return FHE_OK;
+  const size_t old_bytes = c->lt_words * sizeof(uint32_t);
+  // the old buffer is released first, so only the difference counts against the limit
+  const int rc = c->reserve(words * sizeof(uint32_t) - old_bytes, "linear-transform scratch");
+  if (rc != FHE_OK) return rc;
   if (c->lt_scratch) cudaFree(c->lt_scratch);
+  c->grown_bytes -= old_bytes;
   c->lt_scratch = nullptr;
   c->lt_words = 0;
   if (cudaMalloc(&c->lt_scratch, words * sizeof(uint32_t)) != cudaSuccess)
     return fhe_fail(FHE_ENOMEM, "fhe_linear_transform: %zu bytes of scratch", words * 4);
   c->lt_words = words;
+  c->grown_bytes += words * sizeof(uint32_t);
   return FHE_OK;
 }
 

@@ -5,7 +5,10 @@ buffers.
   nothing arrives on) is reported by the next fhe_ctx_sync as FHE_ETIMEOUT,
   the status is cleared, and the context keeps computing bit-exact results.
 * Every output buffer sits between canary words; rotations, HMult, rescale,
-  batched plans and the base conversion leave the canaries untouched."""
+  batched plans and the base conversion leave the canaries untouched.
+* An allocation failure injected on the host (the context's memory limit) is
+  reported as FHE_ENOMEM before anything is launched, and the context keeps
+  working once the limit is lifted."""
 import numpy as np
 import pytest
 
@@ -101,3 +104,50 @@ def test_outputs_stay_within_their_buffers(small, bconv):
     assert np.array_equal(binding.to_numpy(o4), binding.to_numpy(o1))
     plan.close()
     ctx.set_bconv(binding.FHE_BCONV_SCALAR)
+
+
+def test_memory_limit_injects_enomem_and_recovers(fhe_lib):
+    from paper_2512_18345_gb300 import binding
+    P = inputs.workload_params("hmult_relin_rescale_N4096_L4")
+    OP = oracle.OracleParams.from_params(P)
+    ctx = binding.Context.from_params(P)
+    g = inputs.rng(2100)
+    key = rand_key(P, g)
+
+    def code(fn):
+        with pytest.raises(binding.FheError) as e:
+            fn()
+        return e.value.code
+
+    ctx.set_memory_limit(1)  # nothing may grow: the key copy is refused
+    assert code(lambda: ctx.set_relin_key(dev(key))) == binding.FHE_ENOMEM
+    ctx.set_memory_limit(0)
+    ctx.set_relin_key(dev(key))
+    # no room beyond what is held (the key and the context's first workspace slot): a single
+    # key switch runs in that slot, a batch of three items needs two more and is refused
+    held = ctx.info()["key_bytes"] + ctx.info()["workspace_bytes"]
+    ctx.set_memory_limit(held + 1)
+    ds = [inputs.uniform_residues(g, P.q, P.N) for _ in range(3)]
+    got = ctx.keyswitch(dev(ds[0]), P.L)
+    ctx.sync()
+    assert np.array_equal(binding.to_numpy(got), oracle.keyswitch(OP, ds[0], P.L, key))
+    items = [dict(op=binding.FHE_OP_KS, level=P.L, rot=binding.FHE_RELIN_KEY, **{"in": dev(d)},
+                  out=binding.empty((2, P.L, P.N))) for d in ds]
+    assert code(lambda: ctx.batch_plan(items, binding.FHE_PLAN_GRAPH)) == binding.FHE_ENOMEM
+    ctx.sync()  # nothing was launched: no device-side failure either
+    ctx.set_memory_limit(0)
+    plan = ctx.batch_plan(items, binding.FHE_PLAN_GRAPH)
+    plan.launch()
+    ctx.sync()
+    for it, d in zip(items, ds):
+        assert np.array_equal(binding.to_numpy(it["out"]), oracle.keyswitch(OP, d, P.L, key))
+    plan.close()
+    # the linear transforms' scratch counts too
+    ctx.set_memory_limit(ctx.info()["key_bytes"] + ctx.info()["workspace_bytes"] + 1)
+    ct = dev(np.stack([inputs.uniform_residues(g, P.q, P.N) for _ in range(2)]))
+    pt = dev(inputs.uniform_residues(g, tuple(P.q) + tuple(P.p), P.N)[None])
+    assert code(lambda: ctx.linear_transform_dh(ct, P.L, [0], [0], pt, [[0]])) == binding.FHE_ENOMEM
+    ctx.set_memory_limit(0)
+    ctx.linear_transform_dh(ct, P.L, [0], [0], pt, [[0]])
+    ctx.sync()
+    ctx.close()
