@@ -801,6 +801,37 @@ def main():
             stream.wait_event(ev_back[0])
             stream.wait_event(ev_back[1])
 
+    # the host link's own rate for these copies (100 MB each way per step): the e2e ceiling
+    def link_gbs(copy_fn, reps=5):
+        copy_fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            copy_fn()
+        torch.cuda.synchronize()
+        return reps * bytes_io / (time.perf_counter() - t0) / 1e9
+
+    bytes_io = B * 2 * level * P.N * 4
+
+    def h2d():
+        for hi, di in zip(h_in, cts1):
+            di.copy_(hi, non_blocking=True)
+
+    def d2h():
+        for ho, do in zip(h_out, outs1):
+            ho.copy_(do, non_blocking=True)
+
+    link = {"h2d_gbs": link_gbs(h2d), "d2h_gbs": link_gbs(d2h)}
+
+    def both():
+        with torch.cuda.stream(s_in):
+            h2d()
+        with torch.cuda.stream(s_out):
+            d2h()
+
+    link["concurrent_gbs_each_way"] = link_gbs(both)
+    link["copy_bound_ks_per_s"] = B / (bytes_io / (link["concurrent_gbs_each_way"] * 1e9))
+
     e2e_steps, e2e_warm = max(4, min(args.steps, 50)), 4
     join_at = {e2e_warm, e2e_warm + e2e_steps}
     for _ in range(e2e_warm):
@@ -811,7 +842,6 @@ def main():
     e2e_ok = all(torch.equal(ho, do.cpu()) and torch.equal(ho, d1.cpu()) for ho, do, d1 in zip(h_out, outs, outs1))
     plan1.close()
     e2e_val = job_throughput(B * e2e_steps, ws, ms_e2e)
-    bytes_io = B * 2 * level * P.N * 4
 
     # --- the fourth and fifth workloads (reported beside the headline)
     extra = {}
@@ -842,7 +872,7 @@ def main():
             "clocks": clk,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io,
                     "pipelined": "two device buffer sets; a step's copies overlap its neighbours' key switches",
-                    "outputs_match": e2e_ok},
+                    "outputs_match": e2e_ok, "host_link": link},
             "roofline": roof,
             "cpu_baseline": cpu,
             "l2_roofline": {"bytes_per_ks": bks, "l2_gbs_measured": l2_gbs, "frac": l2_frac, "l2_probe": l2,
