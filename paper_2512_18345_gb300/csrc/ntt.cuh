@@ -350,13 +350,13 @@ __device__ __forceinline__ void ntt_pass(const Seg &sg, const KsArgs &ks, int wi
 }
 
 // Resident CTAs per SM asked of the register allocator for each pass (the occupancy the
-// passes were measured at: 8 for the forward column passes, 6 for the inverse column pass
-// and ModUp's forward block pass, 5 or 4 for the other block passes).
+// passes were measured best at: 8 for the forward column passes, 6 for the inverse column
+// pass, 5 or 4 for the block passes; 6 for ModUp's forward block pass cost a register
+// spill and 1.5 % of its time).
 template <bool COLUMN, bool FWD, int PRO, int EPI, bool OTF>
 constexpr int ntt_min_blocks() {
   if (COLUMN) return FWD ? 8 : 6;
   if (!FWD) return 5;
-  if (EPI == EPI_PLAIN) return OTF ? 5 : 6;
   return EPI == EPI_RESCALE ? 4 : 5;
 }
 
