@@ -7,7 +7,12 @@
 // diagonal multiply-accumulate reads every baby rotation once and every
 // diagonal once (the diagonals stream from HBM: G B l limbs); the G - 1 giant
 // rotations are ordinary rotations, run as batched stage programs; one pass sums
-// the giant-step outputs.
+// the giant-step outputs (fhe_linear_transform).
+//
+// fhe_linear_transform_dh is the double-hoisted form used by the CoeffToSlot /
+// SlotToCoeff levels of bootstrapping: sparse diagonals chosen per (giant, baby)
+// pair, baby rotations kept in the extended basis Q_l u P, ModDown hoisted over
+// both step kinds (see the function's comment below).
 #include <algorithm>
 #include <cstring>
 #include <vector>
