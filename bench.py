@@ -51,10 +51,10 @@ def parse():
     ap.add_argument("--sweep", action="store_true",
                     help="kernel-utilisation sweep (NTT over 10..250 limbs, BConv over output counts, key-switch "
                          "batch sizes) as one JSON line instead of the benchmark line")
-    ap.add_argument("--profile-run", choices=["scalar", "tc", "cts"], default=None,
+    ap.add_argument("--profile-run", choices=["scalar", "tc", "cts", "lt"], default=None,
                     help="only launch the batched stage programs (one lane, no graph) warmup + steps times, "
                          "in a fixed launch order for profilers ('cts': the CoeffToSlot chain at N = 2^16, "
-                         "L = 48 instead); prints no JSON line")
+                         "L = 48 instead; 'lt': the level-24 BSGS transform); prints no JSON line")
     return ap.parse_args()
 
 
@@ -256,8 +256,10 @@ def bench_batch64(binding, inputs, roofline, dev, timed, steps, bconv_mode):
     return res
 
 
-def bench_lt(binding, inputs, dev, timed, bconv_mode):
-    """Fifth workload: BSGS linear transform at N = 2^16, level 24, 16 baby x 8 giant steps."""
+def bench_lt(binding, inputs, dev, timed, bconv_mode, runs=0):
+    """Fifth workload: BSGS linear transform at N = 2^16, level 24, 16 baby x 8 giant steps.
+    With `runs`, the transform runs that many times untimed (a profiler's target) and nothing
+    is returned."""
     import numpy as np
     name = "bsgs_lt_N65536_L24"
     w = inputs.WORKLOADS[name]
@@ -273,6 +275,13 @@ def bench_lt(binding, inputs, dev, timed, bconv_mode):
     for d in range(baby * giant):
         diags[d].copy_(binding.to_device(inputs.uniform_residues(g, P.q, P.N), dev))
     out = binding.empty((2, level, P.N), dev)
+    if runs:
+        for _ in range(runs):
+            ctx.linear_transform(ct, level, diags, baby, giant, out=out)
+        ctx.sync()
+        ctx.close()
+        print(f"profile run: {runs} BSGS transforms at N={P.N}, level {level}, {baby} x {giant} steps")
+        return None
     for _ in range(2):
         ctx.linear_transform(ct, level, diags, baby, giant, out=out)
     k = 5
@@ -598,6 +607,9 @@ def main():
     torch.cuda.set_device(dev)
     if args.profile_run == "cts":  # the CoeffToSlot chain alone, for a profiler
         bench_bootstrap_lt(binding, inputs, dev, None, 0.0, only="cts", runs=max(3, args.warmup) + args.steps)
+        return
+    if args.profile_run == "lt":  # the level-24 BSGS transform alone, for a profiler
+        bench_lt(binding, inputs, dev, None, binding.FHE_BCONV_TC, runs=max(3, args.warmup) + args.steps)
         return
     P = inputs.workload_params(WORKLOAD)
     level, B = P.L, args.batch

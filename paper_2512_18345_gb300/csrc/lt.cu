@@ -34,116 +34,206 @@ struct DiagArgs {
   uint32_t *out;                     // [giant][2][nlimb][N]
   int nb, giant, nlimb, level, L;    // limb i < level is modulo q_i, limb i >= level modulo p_{i - level}
   int16_t didx[kMaxGiant * kMaxBaby];  // [giant][nb]: index into diags, -1 where the pair has no diagonal
+  uint32_t gmask[kMaxGiant];           // bit b of gmask[g]: didx[g][b] >= 0
 };
+
+static void diag_masks(DiagArgs &da) {
+  for (int g = 0; g < da.giant; g++) {
+    da.gmask[g] = 0;
+    for (int b = 0; b < da.nb; b++)
+      if (da.didx[g * da.nb + b] >= 0) da.gmask[g] |= 1u << b;
+  }
+}
 
 __device__ __forceinline__ int limb_prime(int i, int level, int L) { return i < level ? i : L + (i - level); }
 
-// out_g[c][i][n] = sum_b diag[didx[g][b]][i][n] babies[b][c][i][n] mod (prime of limb i); one
-// thread per V consecutive coefficients of one limb (vector loads) and group of kGsub giant
-// steps (blockIdx.y; the groups re-read the baby values); kDiagBatch baby steps' loads are
-// issued before their multiply-accumulates, and the accumulators are reduced after each
-// such batch.
+// out_g[c][i][n] = sum_b diag[didx[g][b]][i][n] babies[b][c][i][n] mod (prime of limb i).
+// A unit is kDiagChunk coefficients of one limb for one group of kGsub giant steps; the
+// units of one chunk's groups are adjacent, so the later groups find the baby rows in L2.
+// Per (unit, baby step with a diagonal in the group) a producer warp (one lane) copies the
+// baby rotation's two rows and the group's diagonal rows (4 KB each) into a ring of
+// shared-memory stages with cp.async.bulk, completing on the stage's full mbarrier, and
+// refills a stage as soon as every consumer thread has released it.  The consumers wait on
+// the full barriers themselves (bounded; a warp gives up as a whole) and multiply-accumulate
+// from shared memory into 64-bit accumulators; every third step folds them (fold34), and the
+// end of a unit reduces them.
 constexpr int kGsub = 4;
-constexpr int kDiagBatch = 2;  // baby steps whose loads are issued together
-template <int V>
-struct VecU32;
-template <>
-struct VecU32<1> {
-  static __device__ __forceinline__ void load(const uint32_t *p, uint32_t *v) { v[0] = __ldg(p); }
-  static __device__ __forceinline__ void store(uint32_t *p, const uint32_t *v) { p[0] = v[0]; }
-};
-template <>
-struct VecU32<2> {
-  static __device__ __forceinline__ void load(const uint32_t *p, uint32_t *v) {
-    const uint2 w = __ldg(reinterpret_cast<const uint2 *>(p));
-    v[0] = w.x;
-    v[1] = w.y;
-  }
-  static __device__ __forceinline__ void store(uint32_t *p, const uint32_t *v) {
-    *reinterpret_cast<uint2 *>(p) = make_uint2(v[0], v[1]);
-  }
-};
-template <>
-struct VecU32<4> {
-  static __device__ __forceinline__ void load(const uint32_t *p, uint32_t *v) {
-    const uint4 w = __ldg(reinterpret_cast<const uint4 *>(p));
-    v[0] = w.x;
-    v[1] = w.y;
-    v[2] = w.z;
-    v[3] = w.w;
-  }
-  static __device__ __forceinline__ void store(uint32_t *p, const uint32_t *v) {
-    *reinterpret_cast<uint4 *>(p) = make_uint4(v[0], v[1], v[2], v[3]);
-  }
-};
+constexpr int kDiagChunk = 1024, kDiagThreads = 256, kDiagEpt = kDiagChunk / kDiagThreads;
+constexpr int kDiagRows = 2 + kGsub;  // stage rows: baby c0, baby c1, one diagonal per giant step
+static_assert(kDiagEpt == 4, "diagonal kernel: one 16-byte access per row and thread");
 
-template <int V>
-__global__ void __launch_bounds__(256) k_diagmac(const __grid_constant__ DiagArgs a, const PrimeC *pc, int logn) {
-  using Vec = VecU32<V>;
-  const size_t N = (size_t)1 << logn;
-  const int per_limb = (int)(N / (256 * V));
-  const int i = blockIdx.x / per_limb;
-  const size_t n = ((size_t)(blockIdx.x % per_limb) * 256 + threadIdx.x) * V;
-  const int g0 = blockIdx.y * kGsub, ng = min(kGsub, a.giant - g0);
-  const PrimeC P = pc[limb_prime(i, a.level, a.L)];
-  const size_t poly = (size_t)a.nlimb * N;
-  const uint32_t *dbase = a.diags + (size_t)i * N + n;
-  uint64_t acc[2][kGsub][V];
+// shared-memory stages of the diagonal kernel: as many as fit beside a second CTA, at most 4
+constexpr int kDiagStageBytes = kDiagRows * kDiagChunk * 4 + 16;  // rows, two mbarriers
+constexpr int kDiagStages = (113 * 1024 - 256) / kDiagStageBytes < 4 ? (113 * 1024 - 256) / kDiagStageBytes : 4;
+
+// a = hi 2^34 + lo  ->  hi r34 + lo with r34 = 2^34 mod q: the same residue, below 2^61 + 2^34
+// for any 64-bit a (hi < 2^30, r34 < 2^31), so three more products below 2^62 still fit
+__device__ __forceinline__ uint64_t fold34(uint64_t a, uint32_t r34) {
+  return (uint64_t)(uint32_t)(a >> 34) * r34 + (a & ((1ull << 34) - 1));
+}
+
+__global__ void __maxnreg__(112) k_diag_bulk(const __grid_constant__ DiagArgs a, const PrimeC *pc,
+                                                                   int logn, unsigned int *status) {
+  constexpr int stages = kDiagStages;
+  extern __shared__ __align__(128) uint8_t smem[];
+  constexpr int E = kDiagEpt;
+  const int tid = threadIdx.x;
+  const size_t N = (size_t)1 << logn, poly = (size_t)a.nlimb * N;
+  const int chunks = (int)(N / kDiagChunk), groups = (a.giant + kGsub - 1) / kGsub;
+  const int total = a.nlimb * chunks * groups;
+  const size_t stage_words = (size_t)kDiagRows * kDiagChunk;
+  uint32_t *buf = reinterpret_cast<uint32_t *>(smem);
+  // per stage: `bar` completes when the stage's copies have landed, `ebar` when every
+  // consumer thread is done with it
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + (size_t)stages * stage_words * 4);
+  uint64_t *ebar = bar + stages;
+  if (tid == 0)
+    for (int st = 0; st < stages; st++) {
+      mbar_init(&bar[st], 1);
+      mbar_init(&ebar[st], kDiagThreads);
+    }
+  __syncthreads();
+  // the baby steps of group grp that meet a diagonal
+  auto group_mask = [&](int grp, uint32_t (&gm)[kGsub]) {
+    uint32_t any = 0;
 #pragma unroll
-  for (int g = 0; g < kGsub; g++)
+    for (int g = 0; g < kGsub; g++) {
+      gm[g] = grp * kGsub + g < a.giant ? a.gmask[grp * kGsub + g] : 0u;
+      any |= gm[g];
+    }
+    return any;
+  };
+
+  if (tid >= kDiagThreads) {  // the producer
+    if (tid != kDiagThreads) return;
+    const uint64_t once = l2_evict_first_policy();  // diagonals are read exactly once
+    int k = 0;
+    for (int u = blockIdx.x; u < total; u += gridDim.x) {
+      const int grp = u % groups, ch = (u / groups) % chunks, i = u / (groups * chunks);
+      const size_t off = (size_t)i * N + (size_t)ch * kDiagChunk;
+      uint32_t gm[kGsub];
+      for (uint32_t live = group_mask(grp, gm); live; live &= live - 1) {
+        const int b = __ffs(live) - 1;
+        const int st = k % stages;
+        // the consumers released this stage's previous step (bounded: if they gave up, so do we)
+        if (k >= stages && !mbar_wait_bounded(&ebar[st], (uint32_t)(k / stages - 1) & 1u)) return;
+        fence_proxy_async_smem();
+        uint32_t rows = 2;
 #pragma unroll
-    for (int e = 0; e < V; e++) acc[0][g][e] = acc[1][g][e] = 0;
-  // kDiagBatch baby steps' loads in flight before their multiply-accumulates; a reduced
-  // accumulator plus three 62-bit products stays below 2^64, so kDiagBatch <= 3
-  static_assert(kDiagBatch >= 1 && kDiagBatch <= 3, "at most three products between reductions");
-  for (int b = 0; b < a.nb; b += kDiagBatch) {
-    uint32_t x[kDiagBatch][2][V], d[kDiagBatch][kGsub][V];
+        for (int g = 0; g < kGsub; g++) rows += (gm[g] >> b) & 1u;
+        mbar_arrive_expect_tx(&bar[st], rows * kDiagChunk * 4u);
+        uint32_t *dst = buf + (size_t)st * stage_words;
+        bulk_g2s(dst, a.babies[b] + off, kDiagChunk * 4u, &bar[st]);
+        bulk_g2s(dst + kDiagChunk, a.babies[b] + poly + off, kDiagChunk * 4u, &bar[st]);
 #pragma unroll
-    for (int h = 0; h < kDiagBatch; h++) {
-      const bool live = b + h < a.nb;
-      const int bb = live ? b + h : b;
-      Vec::load(a.babies[bb] + (size_t)i * N + n, x[h][0]);
-      Vec::load(a.babies[bb] + poly + (size_t)i * N + n, x[h][1]);
-#pragma unroll
-      for (int g = 0; g < kGsub; g++) {
-        const int k = (live && g < ng) ? a.didx[(g0 + g) * a.nb + bb] : -1;
-        if (k >= 0) {
-          Vec::load(dbase + (size_t)k * poly, d[h][g]);
-        } else {
-#pragma unroll
-          for (int e = 0; e < V; e++) d[h][g][e] = 0u;
-        }
+        for (int g = 0; g < kGsub; g++)
+          if ((gm[g] >> b) & 1u)
+            bulk_g2s_hint(dst + (size_t)(2 + g) * kDiagChunk,
+                          a.diags + (size_t)a.didx[(grp * kGsub + g) * a.nb + b] * poly + off, kDiagChunk * 4u,
+                          &bar[st], once);
+        k++;
       }
     }
-#pragma unroll
-    for (int h = 0; h < kDiagBatch; h++)
-#pragma unroll
-      for (int g = 0; g < kGsub; g++)
-#pragma unroll
-        for (int e = 0; e < V; e++) {
-          acc[0][g][e] += (uint64_t)d[h][g][e] * x[h][0][e];
-          acc[1][g][e] += (uint64_t)d[h][g][e] * x[h][1][e];
-        }
+    return;
+  }
+
+  const int lane = tid & 31;
+  bool ok = true;
+  int k = 0;
+  for (int u = blockIdx.x; ok && u < total; u += gridDim.x) {
+    const int grp = u % groups, ch = (u / groups) % chunks, i = u / (groups * chunks);
+    const PrimeC P = pc[limb_prime(i, a.level, a.L)];
+    uint32_t r34 = P.r32 << 2;  // 2^34 mod q from 2^32 mod q (< q): at most three subtractions
+    r34 = red2(r34, P.q);
+    r34 = red2(r34, P.q);
+    r34 = red2(r34, P.q);
+    uint32_t gm[kGsub];
+    uint32_t live = group_mask(grp, gm);
+    uint64_t acc[2][kGsub][E];
 #pragma unroll
     for (int g = 0; g < kGsub; g++)
 #pragma unroll
-      for (int e = 0; e < V; e++) {
-        acc[0][g][e] = reduce_u64(acc[0][g][e], P);
-        acc[1][g][e] = reduce_u64(acc[1][g][e], P);
+      for (int e = 0; e < E; e++) acc[0][g][e] = acc[1][g][e] = 0;
+    int since = 0;  // products added to each accumulator since the last fold
+    for (; live; live &= live - 1) {
+      const int b = __ffs(live) - 1;
+      const int st = k % stages;
+      if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bar[st], (uint32_t)(k / stages) & 1u))) {
+        ok = false;
+        break;
       }
+      const uint32_t *src = buf + (size_t)st * stage_words + tid * E;
+      uint32_t x0[E], x1[E];
+      ld_words<E>(src, x0);
+      ld_words<E>(src + kDiagChunk, x1);
+#pragma unroll
+      for (int g = 0; g < kGsub; g++)
+        if ((gm[g] >> b) & 1u) {
+          uint32_t d[E];
+          ld_words<E>(src + (size_t)(2 + g) * kDiagChunk, d);
+#pragma unroll
+          for (int e = 0; e < E; e++) {
+            acc[0][g][e] += (uint64_t)d[e] * x0[e];
+            acc[1][g][e] += (uint64_t)d[e] * x1[e];
+          }
+        }
+      mbar_arrive(&ebar[st]);  // this thread is done with stage st
+      k++;
+      if (++since == 3) {
+        since = 0;
+#pragma unroll
+        for (int g = 0; g < kGsub; g++)
+#pragma unroll
+          for (int e = 0; e < E; e++) {
+            acc[0][g][e] = fold34(acc[0][g][e], r34);
+            acc[1][g][e] = fold34(acc[1][g][e], r34);
+          }
+      }
+    }
+    if (!ok) break;
+    const int g0 = grp * kGsub, ng = min(kGsub, a.giant - g0);
+    const size_t o = (size_t)i * N + (size_t)ch * kDiagChunk + tid * E;
+#pragma unroll
+    for (int g = 0; g < kGsub; g++)
+      if (g < ng)
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+          uint32_t r[E];
+#pragma unroll
+          for (int e = 0; e < E; e++) r[e] = reduce_u64(acc[c][g][e], P);
+          st_words<E>(a.out + ((size_t)(g0 + g) * 2 + c) * poly + o, r);
+        }
   }
-#pragma unroll
-  for (int g = 0; g < kGsub; g++)
-    if (g < ng)
-#pragma unroll
-      for (int c = 0; c < 2; c++) {
-        uint32_t o[V];
-#pragma unroll
-        for (int e = 0; e < V; e++) o[e] = (uint32_t)acc[c][g][e];
-        Vec::store(a.out + ((size_t)(g0 + g) * 2 + c) * poly + (size_t)i * N + n, o);
-      }
+  if (!ok && lane == 0) {
+    // an expired wait: report it, then wait (bounded) for this CTA's copies that may still be
+    // in flight (the producer runs at most `stages` steps beyond the last one released)
+    atomicOr(status, 4u);
+    int issued = 0;  // steps of this CTA
+    for (int u = blockIdx.x; u < total; u += gridDim.x) {
+      uint32_t gm[kGsub];
+      issued += __popc(group_mask(u % groups, gm));
+    }
+    for (int k2 = k; k2 < min(issued, k + stages); k2++)
+      mbar_wait_bounded(&bar[k2 % stages], (uint32_t)(k2 / stages) & 1u);
+  }
 }
-constexpr int kDiagVec = 2;  // coefficients per thread of the diagonal kernel
+
+
+static cudaError_t launch_diag(fhe_ctx *c, const DiagArgs &da, cudaStream_t s) {
+  static bool configured = false;
+  if (!configured) {
+    const cudaError_t e = cudaFuncSetAttribute(k_diag_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, 113 * 1024);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  const int units = da.nlimb * (int)(c->N / kDiagChunk) * ((da.giant + kGsub - 1) / kGsub);
+  const unsigned grid = (unsigned)std::min(units, 2 * std::max(1, sms));
+  k_diag_bulk<<<grid, kDiagThreads + 32, kDiagStages * kDiagStageBytes, s>>>(da, c->d_pc, c->logn, c->tabs.status);
+  note_launch();
+  return cudaGetLastError();
+}
 
 // The identity baby step of a double-hoisted transform, in the extended basis:
 // out[c] = P ct[c] on the q-limbs and 0 on the special limbs (ModDown of it returns ct exactly).
@@ -288,12 +378,10 @@ extern "C" int fhe_linear_transform(fhe_ctx *c, const uint32_t *ct, int level, c
   da.level = level;
   da.L = c->L;
   for (int k = 0; k < baby * giant; k++) da.didx[k] = (int16_t)k;
+  diag_masks(da);
   {
     TraceScope ts(c->tabs, "diag_mac", s);
-    const dim3 grid((unsigned)(level * (N / (256 * kDiagVec))), (unsigned)((giant + kGsub - 1) / kGsub));
-    k_diagmac<kDiagVec><<<grid, 256, 0, s>>>(da, c->d_pc, c->logn);
-    note_launch();
-    if (cudaGetLastError() != cudaSuccess) return fhe_fail(FHE_ECUDA, "fhe_linear_transform: diagonal kernel");
+    if (launch_diag(c, da, s) != cudaSuccess) return fhe_fail(FHE_ECUDA, "fhe_linear_transform: diagonal kernel");
   }
   // giant rotations, as many per batched stage program as the launch arguments hold
   std::vector<Item> its;
@@ -340,7 +428,7 @@ extern "C" int fhe_linear_transform(fhe_ctx *c, const uint32_t *ct, int level, c
 // (1) one ModUp of c1; every baby rotation's inner product stays in the
 //     extended basis Q_l u P, with P sigma_b(c0) folded onto its q-limbs
 //     (IT_IPX); a baby step without rotation is P ct (k_lift);
-// (2) the inner sums are formed in the extended basis (k_diagmac over l + K limbs);
+// (2) the inner sums are formed in the extended basis (k_diag_bulk over l + K limbs);
 // (3) per rotating giant step, the c1 half of its inner sum goes down to Q_l
 //     (IT_MDX), is decomposed again (IT_MODUP) and key-switched with sigma_g on the
 //     extended digits (IT_IPX), again without ModDown;
@@ -431,12 +519,10 @@ extern "C" int fhe_linear_transform_dh(fhe_ctx *c, const uint32_t *ct, int level
   da.level = level;
   da.L = c->L;
   for (int k = 0; k < n_baby * n_giant; k++) da.didx[k] = (int16_t)idx[k];
+  diag_masks(da);
   {
     TraceScope ts(c->tabs, "diag_mac", s);
-    const dim3 grid((unsigned)(n_ext * (N / (256 * kDiagVec))), (unsigned)((n_giant + kGsub - 1) / kGsub));
-    k_diagmac<kDiagVec><<<grid, 256, 0, s>>>(da, c->d_pc, c->logn);
-    note_launch();
-    if (cudaGetLastError() != cudaSuccess) return fhe_fail(FHE_ECUDA, "%s: diagonal kernel", fn);
+    if (launch_diag(c, da, s) != cudaSuccess) return fhe_fail(FHE_ECUDA, "%s: diagonal kernel", fn);
   }
 
   // (3) rotating giant steps: ModDown of the c1 halves, then ModUp + extended-basis key switch
