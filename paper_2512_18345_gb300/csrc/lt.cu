@@ -62,9 +62,12 @@ constexpr int kDiagChunk = 1024, kDiagThreads = 256, kDiagEpt = kDiagChunk / kDi
 constexpr int kDiagRows = 2 + kGsub;  // stage rows: baby c0, baby c1, one diagonal per giant step
 static_assert(kDiagEpt == 4, "diagonal kernel: one 16-byte access per row and thread");
 
-// shared-memory stages of the diagonal kernel: as many as fit beside a second CTA, at most 4
+// One CTA per SM (the 8 consumer warps' accumulators take about 100 registers a thread, and
+// a second CTA would put 5 warps on one SM sub-partition: more than its register file holds),
+// so the ring takes most of the shared memory: 8 stages, 192 KB in flight per SM.
 constexpr int kDiagStageBytes = kDiagRows * kDiagChunk * 4 + 16;  // rows, two mbarriers
-constexpr int kDiagStages = (113 * 1024 - 256) / kDiagStageBytes < 4 ? (113 * 1024 - 256) / kDiagStageBytes : 4;
+constexpr int kDiagStages = 8;
+static_assert(kDiagStages * kDiagStageBytes <= 227 * 1024, "diagonal kernel: stages exceed shared memory");
 
 // a = hi 2^34 + lo  ->  hi r34 + lo with r34 = 2^34 mod q: the same residue, below 2^61 + 2^34
 // for any 64-bit a (hi < 2^30, r34 < 2^31), so three more products below 2^62 still fit
@@ -72,7 +75,7 @@ __device__ __forceinline__ uint64_t fold34(uint64_t a, uint32_t r34) {
   return (uint64_t)(uint32_t)(a >> 34) * r34 + (a & ((1ull << 34) - 1));
 }
 
-__global__ void __maxnreg__(112) k_diag_bulk(const __grid_constant__ DiagArgs a, const PrimeC *pc,
+__global__ void __launch_bounds__(kDiagThreads + 32, 1) k_diag_bulk(const __grid_constant__ DiagArgs a, const PrimeC *pc,
                                                                    int logn, unsigned int *status) {
   constexpr int stages = kDiagStages;
   extern __shared__ __align__(128) uint8_t smem[];
@@ -222,14 +225,15 @@ __global__ void __maxnreg__(112) k_diag_bulk(const __grid_constant__ DiagArgs a,
 static cudaError_t launch_diag(fhe_ctx *c, const DiagArgs &da, cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
-    const cudaError_t e = cudaFuncSetAttribute(k_diag_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, 113 * 1024);
+    const cudaError_t e = cudaFuncSetAttribute(k_diag_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               kDiagStages * kDiagStageBytes);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
   const int units = da.nlimb * (int)(c->N / kDiagChunk) * ((da.giant + kGsub - 1) / kGsub);
-  const unsigned grid = (unsigned)std::min(units, 2 * std::max(1, sms));
+  const unsigned grid = (unsigned)std::min(units, std::max(1, sms));  // persistent: one CTA per SM
   k_diag_bulk<<<grid, kDiagThreads + 32, kDiagStages * kDiagStageBytes, s>>>(da, c->d_pc, c->logn, c->tabs.status);
   note_launch();
   return cudaGetLastError();
