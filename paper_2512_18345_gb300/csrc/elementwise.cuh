@@ -228,7 +228,9 @@ __global__ void __launch_bounds__(kIpThreads + 32, 2) k_ip_bulk(const __grid_con
   const size_t N = (size_t)1 << logn;
   const int chunks = (int)(N / kIpChunk);
   const int total = sl.total * chunks;
-  const size_t stage_words = (size_t)3 * beta_max * kIpChunk;
+  // stage rows per digit: the ModUp value (unless gathered) and both key halves
+  constexpr int RPD = GEXT ? 2 : 3, KR = GEXT ? 0 : 1;  // rows per digit, first key row
+  const size_t stage_words = (size_t)RPD * beta_max * kIpChunk;
   uint32_t *buf = reinterpret_cast<uint32_t *>(smem);
   // per stage: `bar` completes when the stage's copies have landed, `dbar` when its
   // descriptor is written, `ebar` when the consumers are done with it (then it is refilled)
@@ -278,11 +280,11 @@ __global__ void __launch_bounds__(kIpThreads + 32, 2) k_ip_bulk(const __grid_con
       if (!GEXT && jd != d.gjd) {
         const bool own = t < ks.level && t >= jd * ks.alpha && t < (jd + 1) * ks.alpha;
         const uint32_t *e = own ? ks.own + (size_t)t * N : ks.ext + ((size_t)jd * ks.n_ext + t) * N;
-        bulk_g2s(dst + (size_t)(3 * jd) * kIpChunk, e + c0, kIpChunk * 4u, &bar[st]);
+        bulk_g2s(dst + (size_t)(RPD * jd) * kIpChunk, e + c0, kIpChunk * 4u, &bar[st]);
       }
       const uint32_t *kp = ks.key + jd * kstride + (size_t)row * N + c0;
-      bulk_g2s_hint(dst + (size_t)(3 * jd + 1) * kIpChunk, kp, kIpChunk * 4u, &bar[st], key_policy);
-      bulk_g2s_hint(dst + (size_t)(3 * jd + 2) * kIpChunk, kp + half, kIpChunk * 4u, &bar[st], key_policy);
+      bulk_g2s_hint(dst + (size_t)(RPD * jd + KR) * kIpChunk, kp, kIpChunk * 4u, &bar[st], key_policy);
+      bulk_g2s_hint(dst + (size_t)(RPD * jd + KR + 1) * kIpChunk, kp + half, kIpChunk * 4u, &bar[st], key_policy);
     }
   };
   // Warp specialisation: warps 0..7 reduce units, warp 8 (one lane) produces them.  The
@@ -392,10 +394,10 @@ __global__ void __launch_bounds__(kIpThreads + 32, 2) k_ip_bulk(const __grid_con
 #pragma unroll
           for (int e = 0; e < E; e++) ev[e] = gv[e];
         } else {
-          ld_words<E>(src + (size_t)(3 * jd) * kIpChunk, ev);
+          ld_words<E>(src + (size_t)(RPD * jd) * kIpChunk, ev);
         }
-        ld_words<E>(src + (size_t)(3 * jd + 1) * kIpChunk, k0);
-        ld_words<E>(src + (size_t)(3 * jd + 2) * kIpChunk, k1);
+        ld_words<E>(src + (size_t)(RPD * jd + KR) * kIpChunk, k0);
+        ld_words<E>(src + (size_t)(RPD * jd + KR + 1) * kIpChunk, k1);
 #pragma unroll
         for (int i = 0; i < E; i++) {
           a0[i] += (uint64_t)ev[i] * k0[i];

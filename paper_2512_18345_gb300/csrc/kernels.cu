@@ -206,12 +206,15 @@ cudaError_t launch_ip(const DevTables &t, const SegList &sl, bool gather_own, bo
   TraceScope ts(t, "inner_product", s);
   const bool go = gather_own, ge = gather_ext;
   if (beta_max >= 1 && beta_max <= 4 && (1 << t.logn) % kIpChunk == 0) {
-    // streaming kernel: two stages per CTA (with the producer warp refilling a stage as soon
-    // as it is released, a third stage bought nothing and took shared memory from the
-    // transforms running beside it on other lanes); one or two CTAs per SM
-    const int stage_bytes = 3 * beta_max * kIpChunk * 4;
+    // streaming kernel, one or two CTAs per SM.  Two stages per CTA where each stage holds
+    // the ModUp values and the keys (with the producer warp refilling a stage as soon as it
+    // is released, a third stage bought nothing and took shared memory from the transforms
+    // running beside it on other lanes); with the digits gathered through the automorphism
+    // (hoisted rotations) a stage holds the keys alone, and up to four stages fill the same
+    // shared memory.
+    const int stage_bytes = (ge ? 2 : 3) * beta_max * kIpChunk * 4;
     const int per_stage = stage_bytes + 24 + (int)sizeof(IpUnit);  // data, three mbarriers, descriptor
-    const int stages = std::min(2, (113 * 1024 - 256) / per_stage);
+    const int stages = std::min(ge ? 4 : 2, (113 * 1024 - 256) / per_stage);
     const int smem = stages * per_stage;
     static bool configured[4] = {false, false, false, false};
     const int variant = (go ? 1 : 0) + (ge ? 2 : 0);
