@@ -167,10 +167,11 @@ __global__ void __launch_bounds__(kEwThreads) k_ip(const __grid_constant__ SegLi
 // 4 KB each -- into a ring of shared-memory stages with cp.async.bulk,
 // completing on the stage's full mbarrier, after writing the unit's descriptor
 // (output, prime, digit count) next to the stage; it refills a stage as soon as
-// the consumers release it, up to `stages` units ahead.  Of the kIpThreads
-// consumers, thread 0 alone polls the barriers (bounded); the others sleep at a
-// named barrier.  The own digit of a rotation (sigma_{galois_own} applied on
-// the fly) is gathered with plain loads one unit ahead.
+// the consumers release it, up to `stages` units ahead.  Every one of the
+// kIpThreads consumers waits on the barriers itself (bounded; a warp gives up
+// as a whole) and releases a stage by its own arrival.  The own digit of a
+// rotation (sigma_{galois_own} applied on the fly) is gathered with plain
+// loads one unit ahead.
 constexpr int kIpChunk = 1024;  // coefficients per unit
 constexpr int kIpThreads = 256;
 constexpr int kIpEpt = kIpChunk / kIpThreads;  // coefficients per thread and unit (2 or 4)
@@ -237,7 +238,6 @@ __global__ void __launch_bounds__(kIpThreads + 32, 2) k_ip_bulk(const __grid_con
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + (size_t)stages * stage_words * 4);
   uint64_t *dbar = bar + stages, *ebar = dbar + stages;
   IpUnit *desc = reinterpret_cast<IpUnit *>(ebar + stages);
-  __shared__ int s_ok;
 
   // keys are read exactly once: evict them first, so that ModUp outputs (and the digits shared
   // by hoisted rotations) stay in L2
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(kIpThreads + 32, 2) k_ip_bulk(const __grid_con
     for (int st = 0; st < stages; st++) {
       mbar_init(&bar[st], 1);
       mbar_init(&dbar[st], 1);
-      mbar_init(&ebar[st], 1);
+      mbar_init(&ebar[st], kIpThreads);
     }
   }
   __syncthreads();
@@ -341,14 +341,11 @@ __global__ void __launch_bounds__(kIpThreads + 32, 2) k_ip_bulk(const __grid_con
 #pragma unroll
         for (int e = 0; e < E; e++) v[jd][e] = __ldg(d.esrc[jd] + galois_src(j + e, d.egal[jd], logn));
   };
-  // consumer-only barrier (named barrier 1, the 256 consumer threads)
-  auto consumers_sync = []() { asm volatile("bar.sync 1, %0;" ::"n"(kIpThreads) : "memory"); };
+  // every consumer thread waits on the barriers itself (bounded; a warp gives up as a whole)
   uint32_t gnext[E] = {}, pnext0[E] = {}, pnext1[E] = {}, xnext[XD][E] = {};
   bool ok = true;
   if ((int)blockIdx.x < total) {
-    if (tid == 0) s_ok = mbar_wait_bounded(&dbar[0], 0u) ? 1 : 0;
-    consumers_sync();
-    ok = s_ok != 0;
+    ok = __all_sync(0xffffffffu, mbar_wait_bounded(&dbar[0], 0u));
     if (ok) {
       if (GOWN && desc[0].gjd >= 0) gather(desc[0], gnext);
       if (GEXT) gather_all(desc[0], xnext);
@@ -366,13 +363,9 @@ __global__ void __launch_bounds__(kIpThreads + 32, 2) k_ip_bulk(const __grid_con
 #pragma unroll
       for (int e = 0; e < E; e++) xv[jd][e] = xnext[jd][e];
     const bool has_next = u + (int)gridDim.x < total;
-    if (tid == 0) {
-      bool w = mbar_wait_bounded(&bar[st], (uint32_t)(k / stages) & 1u);
-      if (w && has_next) w = mbar_wait_bounded(&dbar[(k + 1) % stages], (uint32_t)((k + 1) / stages) & 1u);
-      s_ok = w ? 1 : 0;
-    }
-    consumers_sync();
-    ok = s_ok != 0;
+    bool w = mbar_wait_bounded(&bar[st], (uint32_t)(k / stages) & 1u);
+    if (w && has_next) w = mbar_wait_bounded(&dbar[(k + 1) % stages], (uint32_t)((k + 1) / stages) & 1u);
+    ok = __all_sync(0xffffffffu, w);
     if (!ok) break;
     const IpUnit d = desc[st];
     if (has_next) {  // the next unit's descriptor (its readiness was waited for above)
@@ -422,10 +415,9 @@ __global__ void __launch_bounds__(kIpThreads + 32, 2) k_ip_bulk(const __grid_con
     uint32_t *d0 = d.d0 + tid * E;
     st_words<E>(d0, r0);
     st_words<E>(d0 + d.d1_off, r1);
-    consumers_sync();  // every consumer is done with stage st and its descriptor
-    if (tid == 0) mbar_arrive(&ebar[st]);
+    mbar_arrive(&ebar[st]);  // this thread is done with stage st and its descriptor
   }
-  if (!ok && tid == 0) {
+  if (!ok && (tid & 31) == 0) {
     // an expired wait: report it, then wait (bounded) for this CTA's copies that may still
     // be in flight (the producer issues at most `stages` units beyond the last one
     // released) so that none lands after the CTA has left the SM
