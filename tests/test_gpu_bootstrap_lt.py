@@ -146,6 +146,39 @@ def test_level_parity_bootstrapping_shape(fhe_lib, kind, which, level_key, tc):
     ctx.close()
 
 
+def test_diagonal_pass_sparse_pairs(fhe_lib):
+    """The diagonal pass's per-group bookkeeping: 32 baby steps (the top bit of the baby-step
+    masks), five giant steps (a second group holding one), a giant step without any diagonal,
+    baby steps that meet no diagonal in the first group but do in the second, one baby step
+    that meets none at all, and diagonals shared by several pairs."""
+    from paper_2512_18345_gb300 import binding
+    P = inputs.workload_params("cts_stc_N4096_L8")
+    OP = oracle.OracleParams.from_params(P)
+    g = inputs.rng(1470)
+    level = 5
+    baby = list(range(32))
+    giant = [0, 32, 64, 96, 128]
+    n_diag = 40
+    live = g.random((len(giant), len(baby))) < 0.4
+    live[1, :] = False          # giant step 1: no diagonal
+    live[:4, [5, 17]] = False   # first group: baby steps 5 and 17 unused ...
+    live[4, [5, 17, 31]] = True  # ... the second group uses them and the top mask bit
+    live[2, 31] = True
+    live[:, 9] = False          # baby step 9: no diagonal anywhere
+    idx = np.where(live, g.integers(0, n_diag, size=live.shape), -1).tolist()
+    ctx = binding.Context.from_params(P)
+    keys = {}
+    for r in sorted(set(baby[1:]) | set(giant[1:])):
+        keys[r] = rand_key(P, g)
+        ctx.set_rot_key(r, dev(keys[r]))
+    ct = np.stack([inputs.uniform_residues(g, P.q[:level], P.N) for _ in range(2)])
+    xp = tuple(P.q[:level]) + tuple(P.p)
+    diags = np.stack([inputs.uniform_residues(g, xp, P.N) for _ in range(n_diag)])
+    got = host(ctx, ctx.linear_transform_dh(dev(ct), level, baby, giant, dev(diags), idx))
+    assert np.array_equal(got, blt.lt_double_hoisted(OP, ct, level, baby, giant, diags, idx, keys))
+    ctx.close()
+
+
 def test_rejections(fhe_lib):
     from paper_2512_18345_gb300 import binding
     P = inputs.workload_params("cts_stc_N4096_L8")
