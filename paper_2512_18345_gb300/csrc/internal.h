@@ -33,7 +33,9 @@ struct DevTables {
   const PrimeC *pc;
   int logn;
   Tracer *tracer;          // null: no tracing
-  unsigned int *status;    // device word: bit 0 set when a bounded device-side wait expired
+  unsigned int *status;    // device word, nonzero once a bounded device-side wait expired: bit 0
+                           // tensor-core BConv, bit 1 inner product, bit 2 diagonal pass,
+                           // bit 7 the wait self-test
   int ip_ctas_per_sm;      // resident CTAs per SM of the streaming inner product (1 or 2; autotuned)
   int ntt_otf;             // block passes form their register twiddles on the fly
   int ntt_single;          // 2^16-point transforms in one cluster launch instead of two passes
