@@ -707,6 +707,20 @@ def main():
     value = job_throughput(B * args.steps, ws, ms)
     graph_kernels = plan.kernel_count
 
+    # --- per-step distribution (after the timed region): CUDA events on the launching
+    # stream around each of a run of back-to-back graph launches
+    dist_steps = max(10, min(args.steps, 100))
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(dist_steps + 1)]
+    evs[0].record(stream)
+    for i in range(dist_steps):
+        plan.launch()
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    step_ms = np.array([evs[i].elapsed_time(evs[i + 1]) for i in range(dist_steps)])
+    per_step = {"steps": dist_steps, "median_ms": float(np.median(step_ms)),
+                "p10_ms": float(np.percentile(step_ms, 10)), "p90_ms": float(np.percentile(step_ms, 90)),
+                "median_ks_per_s": B * ws / (float(np.median(step_ms)) / 1e3)}
+
     # --- comparison paths on the same inputs (fewer steps)
     cmp_steps = max(3, min(args.steps, 50))
 
@@ -726,6 +740,18 @@ def main():
     ctx.set_bconv(binding.FHE_BCONV_TC)
     plain_ks = B * cmp_steps * ws / (ms_plain / 1e3)
     fused_ks = B * cmp_steps * ws / (ms_fused / 1e3)
+
+    # --- warm L2 (labelled; not the headline): the 8 rotations of a step share one
+    # ciphertext and one rotation key, so after the first item the key (50 MB) and the input
+    # are read from L2; outputs and the ModUp working set are as in the headline
+    items_w = [dict(op=binding.FHE_OP_ROTATE, level=level, rot=rots[0], **{"in": cts[0]}, out=o) for o in outs]
+    plan_w = ctx.batch_plan(items_w, binding.FHE_PLAN_GRAPH)
+    for _ in range(3):
+        plan_w.launch()
+    ms_warm = timed(plan_w.launch, cmp_steps)
+    warm_l2 = {"value": B * cmp_steps * ws / (ms_warm / 1e3), "unit": UNIT, "steps": cmp_steps,
+               "inputs": "one ciphertext and one rotation key shared by the step's 8 rotations"}
+    plan_w.close()
 
     # --- per-kernel times (CUDA events around each launch on its stream): the same batched
     # stage programs as the headline, launched directly on one lane (no concurrent lane
@@ -892,6 +918,7 @@ def main():
             "paths": {"graph_batched_tc_bconv": value, "graph_batched_scalar_bconv": graph_scalar_ks,
                       "direct_batched_tc_bconv": batched_direct_ks, "direct_fused_single_scalar": fused_ks,
                       "plain_per_kernel_single_scalar": plain_ks},
+            "per_step": per_step, "warm_l2": warm_l2,
             "batch_groups": head_groups, "lanes": tune["lanes"] if tune else (args.lanes or 2),
             "autotune": tune, "traced_groups_one_lane": groups,
             "other_workloads": extra,
