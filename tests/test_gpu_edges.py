@@ -1,5 +1,6 @@
 """Edge cases of the boundary and the method: every level of a ring (partial
-digits included) on both BConv kernels, extreme and negative rotation indices,
+digits included) on both BConv kernels, keys of maximal residues, extreme and
+negative rotation indices,
 rescale down to one limb, and the host-side rejection of misaligned, aliased
 or empty requests (no kernel runs for those)."""
 import numpy as np
@@ -47,6 +48,41 @@ def test_keyswitch_every_level(small, bconv):
         d = inputs.uniform_residues(g, P.q[:level], P.N)
         assert np.array_equal(host(ctx, ctx.keyswitch(dev(d), level)), oracle.keyswitch(OP, d, level, key)), level
     ctx.set_bconv(binding.FHE_BCONV_SCALAR)
+
+
+@pytest.mark.parametrize("name", ["hmult_relin_rescale_N4096_L4", "hrotate_N65536_L24_tc", "paper_ks_N65536_L48_a12"])
+@pytest.mark.parametrize("fill", ["max", "uniform"])
+def test_maximal_keys(fhe_lib, name, fill):
+    """Every key residue q - 1, so each inner-product product is as large as the ModUp value
+    it meets allows (up to four digits' products before a reduction at L = 48); with
+    fill = "max" the rotated ciphertext is q - 1 everywhere as well (the pass-through term
+    P sigma(c0) then at its largest).  Key switch, rotation and hoisted rotations, against
+    the oracle."""
+    from paper_2512_18345_gb300 import binding
+    P = inputs.workload_params(name)
+    OP = oracle.OracleParams.from_params(P)
+    ctx = binding.Context.from_params(P)
+    g = inputs.rng(930 + len(name) + (1 if fill == "max" else 0))
+    key = np.stack([np.stack([np.array([[p - 1] * P.N for p in P.primes], np.uint32)] * 2)] * P.dnum)
+    level = P.L
+
+    def poly():
+        if fill == "max":
+            return np.array([[q - 1] * P.N for q in P.q[:level]], np.uint32)
+        return inputs.uniform_residues(g, P.q[:level], P.N)
+
+    ctx.set_relin_key(dev(key))
+    d = poly()
+    assert np.array_equal(host(ctx, ctx.keyswitch(dev(d), level)), oracle.keyswitch(OP, d, level, key))
+    rot = 3
+    ctx.set_rot_key(rot, dev(key))
+    ct = np.stack([poly(), poly()])
+    assert np.array_equal(host(ctx, ctx.rotate(dev(ct), level, rot)), oracle.rotate(OP, ct, level, rot, key))
+    ctx.set_rot_key(5, dev(key))
+    outs = ctx.rotate_hoisted(dev(ct), level, [rot, 5])
+    for o, w in zip(outs, oracle.rotate_hoisted(OP, ct, level, [rot, 5], [key, key])):
+        assert np.array_equal(host(ctx, o), w)
+    ctx.close()
 
 
 @pytest.mark.parametrize("rot", [1, -1, -5, 2047, 2049, 4095])
