@@ -267,8 +267,6 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_bconv_tc(const __grid_constan
   }
 }
 
-static int round16(int x) { return (x + 15) / 16 * 16; }
-
 template <int KT>
 static cudaError_t bconv_tc_go(const DevTables &t, const BconvArgs &a, int max_out, cudaStream_t s) {
   const int npad = tc_npad(max_out);
