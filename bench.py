@@ -413,11 +413,13 @@ def bench_paper_shapes(binding, inputs, roofline, dev, timed, steps, l2_gbs, B=8
         ms = timed(plan.launch, k)
         ctx.sync()
         t_ks = ms / 1e3 / (k * B)
+        pipe = comp_pipe_on_off(binding, ctx, items, timed, k, B)
+        ctx.set_pipelining(bool(tune["comp_pipe"]))
         bks = roofline.ks_bytes(P.N, P.L, P.K, P.alpha)
         res[f"l{P.L}_alpha{P.alpha}_beta{P.beta(P.L)}"] = {
             "value": 1.0 / t_ks, "unit": "key-switches/s", "us_per_ks": t_ks * 1e6, "items": B,
             "bytes_per_ks_model": bks, "l2_roofline_frac": (bks / (l2_gbs * 1e9)) / t_ks,
-            "groups": plan.groups, "autotune": tune,
+            "groups": plan.groups, "autotune": tune, "comp_pipe_ks_per_s": pipe,
             "bconv": "tensor cores (K = 64)" if tune["bconv_mode"] == binding.FHE_BCONV_TC else "cuda cores"}
         plan.close()
         ctx.close()
@@ -433,7 +435,7 @@ def run_sweep(args, dev):
     import numpy as np
     import torch
     from paper_2512_18345_gb300 import binding, inputs
-    out = {"ntt": [], "bconv": [], "batch": []}
+    out = {"ntt": [], "bconv": [], "batch": [], "int_peaks": measure_alu_peaks(binding, dev)}
     alu = ALU_PEAK["bfly"]
 
     def traced(ctx, fn, reps):
@@ -534,16 +536,22 @@ def kernel_model(name, P, level, G):
         "ntt_blk+combine": (7 * level * W, 2 * level * bf_blk, "bfly"),
         "bconv": ((level + conv + 2 * K + 2 * level) * W, macs, "mac"),
         "bconv_tc": ((level + conv + 2 * K + 2 * level) * W, macs, "mac"),
-        "inner_product": ((level + K) * (3 * beta + 2) * W, 2 * beta * (level + K) * P.N, "mac"),
+        # per extended limb: beta decomposed limbs, 2 beta key limbs, two u limbs; plus the
+        # pass-through limb (sigma(c0)) each q-limb reads for the u += P sigma(c0) fold
+        "inner_product": (((level + K) * (3 * beta + 2) + level) * W, 2 * beta * (level + K) * P.N, "mac"),
     }
     b, o, unit = m.get(name, (0, 0, "bfly"))
     return b * G, o * G, unit
 
 
-# ALU peaks from the probe's per-SM unit counts at the maximum SM clock (152 SMs, 2.07 GHz):
-# a Shoup radix-2 butterfly takes >= 4 IMAD-pipe issue cycles (IMAD.HI is half rate) ->
-# 16 per clock per SM; a 32x32->64-bit multiply-accumulate (IMAD.WIDE) ~23 per clock per SM.
+# ALU peaks: measured on the device by the library's integer-pipe probe (fhe_probe_int) --
+# register-only chains of the NTT's forward Shoup butterfly and of the 64-bit
+# multiply-accumulate, at four CTAs per SM -- and filled in by main(); the fallback below is
+# the earlier derivation (16 butterflies and 23 multiply-accumulates per clock per SM,
+# 152 SMs, 2.07 GHz), used only when the probe fails.
 ALU_PEAK = {"bfly": 16 * 152 * 2.07e9, "mac": 23 * 152 * 2.07e9}
+ALU_PEAK_SOURCE = ["derived from probe unit counts x 152 SMs x 2.07 GHz"]
+NTT_KERNELS = ("intt_blk+gather", "intt_col+scale", "ntt_col", "ntt_blk", "intt_blk", "ntt_blk+combine")
 
 
 def measured_traffic_per_item(name):
@@ -583,9 +591,63 @@ def kernel_roofline(name, launches_per_group, launch_ms, P, level, G, hbm_peak):
               "frac_hbm": f_hbm, "frac_alu": f_alu}
     if f_alu >= f_hbm:
         return {"bound": "alu", "achieved": ach_ops / 1e12, "peak": ALU_PEAK[unit] / 1e12, "unit": f"T{unit}/s",
-                "frac": f_alu, "peak_source": "derived from probe unit counts x 152 SMs x 2.07 GHz", **common}
+                "frac": f_alu, "peak_source": ALU_PEAK_SOURCE[0], **common}
     return {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": f_hbm,
             "peak_source": "measured (hbm_gbs)", **common}
+
+
+def measure_alu_peaks(binding, dev):
+    """Set ALU_PEAK from the library's integer-pipe probe on this device; on failure keep
+    the derived fallback and report why."""
+    try:
+        ipk = binding.probe_int(dev)
+        ALU_PEAK["bfly"], ALU_PEAK["mac"] = ipk["butterflies_per_s"], ipk["mac64_per_s"]
+        ALU_PEAK_SOURCE[0] = (f"measured (fhe_probe_int register-only chains at {ipk['clock_mhz']:.0f} MHz: "
+                              f"{ipk['butterflies_per_s'] / 1e12:.2f} T butterflies/s, "
+                              f"{ipk['mac64_per_s'] / 1e12:.2f} T 64-bit MAC/s)")
+        return ipk
+    except Exception as ex:
+        return {"failed": str(ex)}
+
+
+def kernel_rates(stats, P, level, G, groups_traced, hbm_peak):
+    """Per traced kernel: its algorithmic rate over its summed event time and the fraction of
+    the peak that bounds it; and the NTT family's aggregate butterfly rate (all forward and
+    inverse passes of the key switch: their butterflies over their summed time)."""
+    rows, ntt_ops, ntt_ms = {}, 0.0, 0.0
+    for name, (n, t_ms) in stats.items():
+        nbytes, ops, unit = kernel_model(name, P, level, G)
+        if not t_ms or not (nbytes or ops):
+            continue
+        secs = t_ms / 1e3
+        ach = ops * groups_traced / secs
+        rows[name] = {"alu_rate": ach, "alu_unit": f"{unit}/s", "frac_alu": ach / ALU_PEAK[unit],
+                      "gbs": nbytes * groups_traced / secs / 1e9,
+                      "frac_hbm": nbytes * groups_traced / secs / 1e9 / hbm_peak}
+        if name in NTT_KERNELS:
+            ntt_ops += ops * groups_traced
+            ntt_ms += t_ms
+    fam = None
+    if ntt_ms:
+        rate = ntt_ops / (ntt_ms / 1e3)
+        fam = {"butterflies_per_s": rate, "frac_alu": rate / ALU_PEAK["bfly"], "share_ms": ntt_ms,
+               "peak": ALU_PEAK["bfly"], "peak_source": ALU_PEAK_SOURCE[0]}
+    return rows, fam
+
+
+def comp_pipe_on_off(binding, ctx, items, timed, steps, B):
+    """Complementary pipelining (Section IV-B) on and off under the context's current
+    schedule: key switches per second of the graph-captured plan each way."""
+    res = {}
+    for on in (True, False):
+        ctx.set_pipelining(on)
+        pl = ctx.batch_plan(items, binding.FHE_PLAN_GRAPH)
+        for _ in range(3):
+            pl.launch()
+        ms = timed(pl.launch, steps)
+        res["on" if on else "off"] = B * steps / (ms / 1e3)
+        pl.close()
+    return res
 
 
 def main():
@@ -753,6 +815,10 @@ def main():
                "inputs": "one ciphertext and one rotation key shared by the step's 8 rotations"}
     plan_w.close()
 
+    # --- complementary pipelining (Section IV-B) on and off under the tuned schedule
+    pipe_head = comp_pipe_on_off(binding, ctx, items, timed, cmp_steps, B)
+    ctx.set_pipelining(bool(tune["comp_pipe"]) if tune else True)
+
     # --- per-kernel times (CUDA events around each launch on its stream): the same batched
     # stage programs as the headline, launched directly on one lane (no concurrent lane
     # inflates a kernel's event interval)
@@ -784,6 +850,7 @@ def main():
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     l2 = binding.probe_bandwidth(dev, 64 << 20, 50)
     l2_gbs = l2["copy"]
+    ipk = measure_alu_peaks(binding, dev)
 
     # algorithmic bytes of the headline step and its L2-roofline fraction (paper's definition)
     bks = roofline.ks_bytes(P.N, level, P.K, P.alpha)
@@ -794,6 +861,7 @@ def main():
     roof = kernel_roofline(top_name, top_n / (cmp_steps * ngroups), per_launch_ms, P, level, B / ngroups,
                            hbm_peak)
     roof["share"] = top_ms / total_ms if total_ms else None
+    krates, ntt_family = kernel_rates(stats, P, level, B / ngroups, cmp_steps * ngroups, hbm_peak)
 
     # --- e2e: every step copies its inputs from pinned host memory and its results back,
     # inside the timed region, through the same public API.  Steps alternate between two
@@ -913,6 +981,11 @@ def main():
                     "outputs_match": e2e_ok, "host_link": link},
             "roofline": roof,
             "cpu_baseline": cpu,
+            # the metric's comparison: plain per-kernel path against batched + tensor-core BConv
+            "plain_per_kernel_single_scalar": plain_ks, "graph_batched_scalar_bconv": graph_scalar_ks,
+            "graph_batched_tc_bconv": value, "batched_tc_over_plain": value / plain_ks,
+            "tc_over_scalar_bconv": value / graph_scalar_ks, "l2_roofline_frac": l2_frac,
+            "ntt_family": ntt_family, "int_peaks": ipk,
             "l2_roofline": {"bytes_per_ks": bks, "l2_gbs_measured": l2_gbs, "frac": l2_frac, "l2_probe": l2,
                             "definition": "B_KS(l) / measured L2 read+write bandwidth / time per key switch"},
             "paths": {"graph_batched_tc_bconv": value, "graph_batched_scalar_bconv": graph_scalar_ks,
@@ -922,8 +995,19 @@ def main():
             "batch_groups": head_groups, "lanes": tune["lanes"] if tune else (args.lanes or 2),
             "autotune": tune, "traced_groups_one_lane": groups,
             "other_workloads": extra,
-            "kernels": {k: {"launches": v[0], "ms": v[1], "share": v[1] / total_ms} for k, v in
-                        sorted(stats.items(), key=lambda kv: -kv[1][1])},
+            "kernels": {k: dict({"launches": v[0], "ms": v[1], "share": v[1] / total_ms}, **krates.get(k, {}))
+                        for k, v in sorted(stats.items(), key=lambda kv: -kv[1][1])},
+        }
+        # last (the end of the line survives truncated logs): the headline comparisons
+        line["summary"] = {
+            "ks_per_s": {"graph_batched_tc_bconv": value, "graph_batched_scalar_bconv": graph_scalar_ks,
+                         "plain_per_kernel_single_scalar": plain_ks, "e2e": e2e_val},
+            "batched_tc_over_plain": value / plain_ks, "tc_over_scalar_bconv": value / graph_scalar_ks,
+            "l2_roofline_frac": l2_frac, "inner_product_hbm_frac": roof.get("frac_hbm"),
+            "ntt_family_alu_frac": ntt_family["frac_alu"] if ntt_family else None,
+            "comp_pipe_ks_per_s": {"headline": pipe_head,
+                                   "l48_alpha12_beta4": extra.get("paper_shapes", {}).get(
+                                       "l48_alpha12_beta4", {}).get("comp_pipe_ks_per_s")},
         }
         print(json.dumps(line), flush=True)
     plan.close()

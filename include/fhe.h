@@ -263,7 +263,13 @@ FHE_API int fhe_add(fhe_ctx *ctx, const uint32_t *a, const uint32_t *b, int npol
  *     in_idx) to out [n_out][N] (primes out_idx), Section II-B "BConv" with the
  *     table T[i][j] = (Qstar / q_j) mod p_i of Section III-C and the
  *     [(Qstar / q_j)^-1]_{q_j} pre-multiplication; n_in <= 16, n_out <= 64
- *     (n_in <= 12 under FHE_BCONV_TC, else FHE_EUNSUPPORTED).
+ *     (n_in <= 12 under FHE_BCONV_TC, else FHE_EUNSUPPORTED).  The context
+ *     keeps the tables of each (in_idx, out_idx, kernel) combination: the
+ *     first call with a combination allocates them (a few KB) and copies them
+ *     on `stream`, and the context's first fhe_bconv call allocates its
+ *     [16][N]-word pre-multiplied input; a call with a known combination
+ *     allocates nothing and does not synchronize.  At most 64 combinations are
+ *     kept: a new one beyond that waits for `stream` and releases them.
  */
 FHE_API int fhe_ntt(fhe_ctx *ctx, uint32_t *a, const int *prime_idx, int n, fhe_stream stream);
 FHE_API int fhe_intt(fhe_ctx *ctx, uint32_t *a, const int *prime_idx, int n, fhe_stream stream);
@@ -379,30 +385,49 @@ FHE_API int fhe_trace_enable(fhe_ctx *ctx, int on);
  */
 FHE_API int fhe_probe_bandwidth(int device, size_t bytes, int reps, double *read_gbs, double *write_gbs,
                                 double *copy_gbs);
+/*
+ * Integer-pipe probe: register-only chains on `device` (four 256-thread CTAs
+ * per SM, one wave; allocates and frees a few KB).  Rates are whole-GPU units
+ * per second; clock_mhz is the SM clock the chains ran at (cycle counter over
+ * event time).  butterflies_per_s is the forward Shoup butterfly exactly as
+ * the NTT passes compute it (31-bit prime, values lazily in [0, 2q)): the
+ * ALU denominator of the transforms' roofline fractions; mac64_per_s the
+ * 32 x 32 -> 64-bit multiply-accumulate of the base conversion.
+ */
+typedef struct {
+  double clock_mhz;
+  double butterflies_per_s;
+  double mac64_per_s;
+  double imad_per_s, imad_hi_per_s, add_min_per_s;
+  int sms;
+} fhe_int_peaks;
+FHE_API int fhe_probe_int(int device, fhe_int_peaks *out);
 FHE_API int fhe_trace_read(fhe_ctx *ctx, fhe_kernel_stat *out, int max, int *n);
 
 /*
- * Allocation-free base conversion.  The paper has no counterpart: this is an
- * interface addition for callers that cannot allocate device memory -- code
- * recording a CUDA stream capture (cudaMalloc and stream synchronization are
- * not allowed while a capture is open), latency-critical loops that must avoid
- * cudaMalloc's implicit device synchronization, and processes whose framework
- * has already reserved all device memory for its own pool.
+ * Allocation-free base conversion.  The paper has no counterpart: this entry
+ * point is an addition to the interface for callers that cannot allocate
+ * device memory once they are running -- a process whose framework has
+ * already reserved all free device memory for its own pool (any further
+ * cudaMalloc fails), or a real-time loop that must not take cudaMalloc's
+ * implicit device-wide synchronization or its unbounded latency.
  *
- * Computes exactly what fhe_bconv computes (same bits) but allocates nothing:
- * its scratch -- the pre-multiplied input, at most
- * FHE_BCONV_NOALLOC_MAX_IN x FHE_BCONV_NOALLOC_MAX_N words, and the conversion
- * tables -- is one fixed device array of about 2 MB that every GPU loading
- * this library holds until the process exits.  Larger n_in, n_out or N are
- * rejected with FHE_EINVAL (use fhe_bconv).  The context must already exist.
+ * Computes exactly what fhe_bconv computes (same bits, CUDA-core kernel) but
+ * allocates nothing: its scratch -- the pre-multiplied input, at most
+ * FHE_BCONV_NOALLOC_MAX_IN x FHE_BCONV_NOALLOC_MAX_N words, and the
+ * conversion tables -- is one fixed device array of about 2 MB that every GPU
+ * loading this library holds until the process exits.  Larger n_in, n_out or
+ * N are rejected with FHE_EINVAL (use fhe_bconv).  The context must already
+ * exist.  The tables travel to the GPU as kernel arguments, not as copies
+ * from host memory.
  *
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * All calls share the array and it keeps the last call's contents; every word
- * a call reads it writes first, so nothing has to be cleared.  Calls on one
- * context are ordered by the library, but calls whose GPU work overlaps --
- * unordered streams of different contexts on the same device -- race on the
- * shared array.
+ * The first call on a device, with that device current, looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls share the array and it keeps the last call's
+ * contents; every word a call reads it writes first, so nothing has to be
+ * cleared.  Calls on one context are ordered by the library, but calls whose
+ * GPU work overlaps -- unordered streams of different contexts on the same
+ * device -- race on the shared array.
  */
 #define FHE_BCONV_NOALLOC_MAX_IN 8
 #define FHE_BCONV_NOALLOC_MAX_OUT 64

@@ -34,7 +34,7 @@ EXPORTS = (
     "fhe_rotate_hoisted", "fhe_linear_transform", "fhe_linear_transform_dh", "fhe_pmult", "fhe_add", "fhe_ntt", "fhe_intt", "fhe_modup", "fhe_moddown",
     "fhe_bconv", "fhe_batch_plan", "fhe_batch_launch", "fhe_plan_destroy", "fhe_plan_kernel_count",
     "fhe_plan_groups", "fhe_ctx_set_batch",
-    "fhe_trace_enable", "fhe_trace_read", "fhe_probe_bandwidth", "fhe_autotune", "fhe_autotune_cached", "fhe_ctx_set_pipelining", "fhe_ctx_set_ntt", "fhe_ctx_set_memory_limit", "fhe_selftest_wait_timeout", "fhe_bconv_noalloc", "fhe_last_error",
+    "fhe_trace_enable", "fhe_trace_read", "fhe_probe_bandwidth", "fhe_probe_int", "fhe_autotune", "fhe_autotune_cached", "fhe_ctx_set_pipelining", "fhe_ctx_set_ntt", "fhe_ctx_set_memory_limit", "fhe_selftest_wait_timeout", "fhe_bconv_noalloc", "fhe_last_error",
 )
 
 
@@ -54,6 +54,12 @@ class FheInfo(ctypes.Structure):
 
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int), ("total_ms", ctypes.c_double)]
+
+
+class IntPeaks(ctypes.Structure):
+    _fields_ = [("clock_mhz", ctypes.c_double), ("butterflies_per_s", ctypes.c_double),
+                ("mac64_per_s", ctypes.c_double), ("imad_per_s", ctypes.c_double),
+                ("imad_hi_per_s", ctypes.c_double), ("add_min_per_s", ctypes.c_double), ("sms", ctypes.c_int)]
 
 
 class TuneResult(ctypes.Structure):
@@ -131,6 +137,7 @@ def lib() -> ctypes.CDLL:
         "fhe_trace_enable": [vp, ctypes.c_int],
         "fhe_probe_bandwidth": [ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+        "fhe_probe_int": [ctypes.c_int, ctypes.POINTER(IntPeaks)],
         "fhe_trace_read": [vp, ctypes.POINTER(KernelStat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
         "fhe_bconv_noalloc": [vp, vp, ip, ctypes.c_int, vp, ip, ctypes.c_int, vp],
         "fhe_last_error": [],
@@ -187,6 +194,14 @@ def probe_bandwidth(device: int = 0, nbytes: int = 64 << 20, reps: int = 50) -> 
     r, w, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     check(lib().fhe_probe_bandwidth(device, nbytes, reps, ctypes.byref(r), ctypes.byref(w), ctypes.byref(c)))
     return {"read": r.value, "write": w.value, "copy": c.value, "bytes": nbytes}
+
+
+def probe_int(device: int = 0) -> dict:
+    """Integer-pipe rates (units per second over the GPU) of register-only chains: the NTT's
+    forward butterfly, the 64-bit multiply-accumulate, IMAD, IMAD.HI and add+min."""
+    r = IntPeaks()
+    check(lib().fhe_probe_int(device, ctypes.byref(r)))
+    return {f: getattr(r, f) for f, _ in IntPeaks._fields_}
 
 
 class Plan:

@@ -1,15 +1,16 @@
 // Allocation-free base conversion: fhe_bconv_noalloc.
 //
-// fhe_bconv allocates device memory on every call (its pre-multiplied copy of
-// the input and its conversion tables) and synchronizes the stream to free it.
-// Some callers cannot do that: code that is recording a CUDA stream capture
-// (cudaMalloc and stream synchronization are not allowed while a capture is
-// open), latency-critical loops that must not hit cudaMalloc's implicit device
-// synchronization, and processes whose framework has already reserved all
-// device memory for its own pool.  This variant computes exactly the same
-// conversion with no allocation: its scratch (the pre-multiplied input and the
-// tables) lives in one fixed, file-scope device array that every GPU loading
-// the library keeps until the process exits.
+// fhe_bconv keeps its tables and its pre-multiplied input in device memory
+// that the context allocates on first use.  Some callers cannot allocate once
+// they are running: a process whose framework has reserved all free device
+// memory for its own pool (cudaMalloc then fails), or a real-time loop that
+// must not take cudaMalloc's implicit device-wide synchronization.  This
+// variant computes exactly the same conversion with no allocation: its
+// scratch (the pre-multiplied input and the tables) lives in one fixed,
+// file-scope device array that every GPU loading the library keeps until the
+// process exits.  The tables reach the GPU as the argument of a small kernel
+// that writes them into the array, so no host memory is read after the call
+// returns.
 #include <cstring>
 #include <mutex>
 
@@ -35,6 +36,28 @@ constexpr int kMaxDevices = 64;
 // The shared scratch.  In host code this name is only a stand-in for the
 // device symbol: the device address is obtained with cudaGetSymbolAddress.
 static __device__ __align__(256) uint32_t g_bconv_scratch[kWords];
+
+// The conversion tables of one call, passed by value to the kernel that stores them.
+struct NoallocTables {
+  uint32_t T[kMaxOut * kMaxIn];  // T[o][j] = (Qstar/q_j) mod p_o
+  int2 om[kMaxOut];              // (output row, prime index)
+  uint2 pre[kMaxIn];             // ((Qstar/q_j)^-1 mod q_j, Shoup companion)
+  int n_in, n_out;
+};
+
+// Writes a call's tables into the shared scratch (device code names the array directly).
+__global__ void k_noalloc_tables(const __grid_constant__ NoallocTables t) {
+  const int nT = t.n_out * t.n_in;
+  for (int i = threadIdx.x; i < nT; i += blockDim.x) g_bconv_scratch[kOffT + i] = t.T[i];
+  for (int i = threadIdx.x; i < t.n_out; i += blockDim.x) {
+    g_bconv_scratch[kOffMap + 2 * i] = (uint32_t)t.om[i].x;
+    g_bconv_scratch[kOffMap + 2 * i + 1] = (uint32_t)t.om[i].y;
+  }
+  for (int i = threadIdx.x; i < t.n_in; i += blockDim.x) {
+    g_bconv_scratch[kOffPre + 2 * i] = t.pre[i].x;
+    g_bconv_scratch[kOffPre + 2 * i + 1] = t.pre[i].y;
+  }
+}
 
 static uint32_t *g_scratch_addr[kMaxDevices];
 static cudaError_t g_scratch_err[kMaxDevices];
@@ -71,11 +94,15 @@ extern "C" int fhe_bconv_noalloc(fhe_ctx *c, const uint32_t *in, const int *in_i
   const char *ib = (const char *)in, *ob = (const char *)out;
   if (ib < ob + 4 * N * n_out && ob < ib + 4 * N * n_in) return fhe_fail(FHE_EALIAS, "fhe_bconv_noalloc: out overlaps in");
 
-  // tables on the host stack: pre-factor (Qstar/q_j)^-1 mod q_j, T[o][j] = (Qstar/q_j) mod p_o
+  // the tables: pre-factor (Qstar/q_j)^-1 mod q_j, T[o][j] = (Qstar/q_j) mod p_o
   const std::vector<uint32_t> &pr = c->primes;
-  uint32_t T[kMaxOut * kMaxIn];
-  int2 om[kMaxOut];
-  uint2 pre[kMaxIn];
+  NoallocTables tabs;
+  memset(&tabs, 0, sizeof tabs);
+  tabs.n_in = n_in;
+  tabs.n_out = n_out;
+  uint32_t *T = tabs.T;
+  int2 *om = tabs.om;
+  uint2 *pre = tabs.pre;
   for (int j = 0; j < n_in; j++) {
     const uint32_t q = pr[in_idx[j]];
     uint32_t prod = 1;
@@ -106,10 +133,10 @@ extern "C" int fhe_bconv_noalloc(fhe_ctx *c, const uint32_t *in, const int *in_i
   cudaStream_t s = (cudaStream_t)stream;
   c->order_stream(s);
   // every scratch word the kernels read is written first by this call: nothing needs clearing
-  if (cudaMemcpyAsync(dT, T, sizeof(uint32_t) * n_out * n_in, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(dM, om, sizeof(int2) * n_out, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(dPre, pre, sizeof(uint2) * n_in, cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return fhe_fail(FHE_ECUDA, "fhe_bconv_noalloc: table copy");
+  k_noalloc_tables<<<1, 256, 0, s>>>(tabs);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fhe_fail(FHE_ECUDA, "fhe_bconv_noalloc: tables: %s", cudaGetErrorString(e));
   SegList sl;
   memset(&sl, 0, sizeof sl);
   for (int j = 0; j < n_in; j++) {
@@ -124,7 +151,7 @@ extern "C" int fhe_bconv_noalloc(fhe_ctx *c, const uint32_t *in, const int *in_i
     x.galois = 1;
     sl.total += 1;
   }
-  cudaError_t e = launch_ew(c->tabs, EW_SCALE, sl, s);
+  e = launch_ew(c->tabs, EW_SCALE, sl, s);
   if (e != cudaSuccess) return fhe_fail(FHE_ECUDA, "fhe_bconv_noalloc: scale: %s", cudaGetErrorString(e));
   BconvArgs ba;
   memset(&ba, 0, sizeof ba);

@@ -277,12 +277,10 @@ static cudaError_t bconv_tc_go(const DevTables &t, const BconvArgs &a, int max_o
   const int per_sm = std::min(512 / ncols, 2048 / kTcThreads);
   int smem = std::max(need, 233472 / (per_sm + 1) + 1024);  // 228 KB of shared memory per SM
   if (smem > 232448) smem = 232448;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_bconv_tc<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static PerDeviceOnce configured;
+  const cudaError_t ce = configured.run(
+      [] { return cudaFuncSetAttribute(k_bconv_tc<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448); });
+  if (ce != cudaSuccess) return ce;
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -18,7 +18,8 @@ struct PrimeC {
   uint32_t r32, r32s;   // 2^32 mod q and its Shoup companion floor(r32 2^32 / q)
   uint32_t div32;       // floor(2^32 / q) = Shoup companion of 1
   uint32_t r64, r64s;   // 2^64 mod q and companion
-  uint32_t pad0, pad1;
+  uint32_t r34;         // 2^34 mod q (the diagonal pass's fold constant)
+  uint32_t pad1;
 };
 
 // ---------------------------------------------------------------- arithmetic

@@ -131,6 +131,7 @@ static int build_tables(fhe_ctx *c) {
     p.div32 = (uint32_t)((1ull << 32) / q);
     p.r64 = h_mul(p.r32, p.r32, q);
     p.r64s = h_shoup(p.r64, q);
+    p.r34 = (uint32_t)((1ull << 34) % q);
     pcs[i] = p;
     c->psi[i] = h_psi(q, N);
   }
@@ -348,7 +349,8 @@ fhe_ctx::~fhe_ctx() {
   cudaFree(lt_scratch);
   cudaFree(relin_key);
   for (auto &kv : rot_keys) cudaFree(kv.second);
-  for (auto p : scratch_tabs) cudaFree(p);
+  for (auto &kv : bconv_prep) cudaFree(kv.second.block);
+  cudaFree(bconv_y);
   if (order_ev) cudaEventDestroy(order_ev);
   for (size_t i = 0; i < lanes.size(); i++) {
     if (i > 0) {

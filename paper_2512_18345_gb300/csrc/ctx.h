@@ -36,7 +36,17 @@ struct fhe_ctx {
   uint2 *d_pmod = nullptr;                             // [L] Shoup pairs of P mod q_i                        // tensor-core table of the ModDown conversion
   unsigned int *d_status = nullptr;                    // device status word (expired waits)
   uint2 *d_rs_qinv = nullptr;                          // [L][L]
-  std::vector<void *> scratch_tabs;                    // tables built for fhe_bconv calls
+  // fhe_bconv: the tables of each (input primes, output primes, kernel) combination, built and
+  // uploaded by the first call that uses it and reused by later calls (one device block each)
+  struct BconvPrep {
+    void *block = nullptr;
+    uint32_t *T = nullptr;
+    int2 *om = nullptr;
+    uint2 *pre = nullptr;
+    uint16_t *Btc = nullptr;
+  };
+  std::map<std::vector<int>, BconvPrep> bconv_prep;
+  uint32_t *bconv_y = nullptr;  // [16][N] fhe_bconv's pre-multiplied input
   size_t table_bytes = 0;
   fhe::DevTables tabs{};
   fhe::Tracer tracer;

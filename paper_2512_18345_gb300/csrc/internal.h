@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <vector>
 
@@ -10,6 +11,27 @@
 #include "ntt.cuh"
 
 namespace fhe {
+
+// A set-up step that applies to one device only (a kernel's function attributes:
+// cudaFuncSetAttribute acts on the current device), run once per device.  Safe to
+// call from several host threads: two may both run the step, which is idempotent.
+class PerDeviceOnce {
+ public:
+  template <class F>
+  cudaError_t run(F &&step) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = dev < 64 ? 1ull << dev : 0;  // devices beyond 64 repeat the step
+    if (bit && (done_.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = step();
+    if (e == cudaSuccess && bit) done_.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+  }
+
+ private:
+  std::atomic<uint64_t> done_{0};
+};
 
 // Optional per-launch timing: each kernel launch is bracketed by two CUDA events
 // on its stream and recorded under the kernel's name.

@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
+#include <string>
 
 #include "bconv.cuh"
 #include "elementwise.cuh"
@@ -37,14 +38,13 @@ template <int LOGN, bool COLUMN, bool FWD, int PRO, int EPI, bool OTF>
 static const char *ntt_name() {
   static const char *pro[] = {"", "+gather", "+reduce"};
   static const char *epi[] = {"", "", "+scale", "+combine", "+rescale"};
-  static char buf[64];
-  static bool init = false;
-  if (!init) {
+  static const std::string name = [] {  // initialised once, thread-safe
+    char buf[64];
     snprintf(buf, sizeof buf, "%s_%s%s%s%s", FWD ? "ntt" : "intt", COLUMN ? "col" : "blk", pro[PRO], epi[EPI],
              OTF ? "+otf" : "");
-    init = true;
-  }
-  return buf;
+    return std::string(buf);
+  }();
+  return name.c_str();
 }
 
 template <int LOGN, bool COLUMN, bool FWD, int PRO, int EPI, bool OTF>
@@ -53,13 +53,12 @@ static cudaError_t ntt_go(const DevTables &t, const SegList &sl, cudaStream_t s)
   const unsigned grid = (unsigned)(sl.total * G::TILES);
   if (grid == 0) return cudaSuccess;
   constexpr int smem = ntt_twiddle_smem(COLUMN, G::S);
-  static bool configured = false;  // opt in to > 48 KB of shared memory once per instantiation
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_ntt<LOGN, COLUMN, FWD, PRO, EPI, OTF>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static PerDeviceOnce configured;  // opt in to > 48 KB of shared memory once per instantiation and device
+  cudaError_t e = configured.run([] {
+    return cudaFuncSetAttribute(k_ntt<LOGN, COLUMN, FWD, PRO, EPI, OTF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem);
+  });
+  if (e != cudaSuccess) return e;
   TraceScope ts(t, ntt_name<LOGN, COLUMN, FWD, PRO, EPI, OTF>(), s);
   k_ntt<LOGN, COLUMN, FWD, PRO, EPI, OTF><<<grid, kNttThreads, smem, s>>>(sl, t.ntt);
   g_launches++;
@@ -105,12 +104,10 @@ static cudaError_t ntt1_go(const DevTables &t, const SegList &first, const SegLi
   const unsigned grid = (unsigned)(first.total * 16);
   if (grid == 0) return cudaSuccess;
   constexpr int smem = ntt_twiddle_smem(true, 256);  // the larger of the two passes' tables
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_ntt1<FWD, PRO, EPI, OTF>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static PerDeviceOnce configured;
+  cudaError_t e = configured.run(
+      [] { return cudaFuncSetAttribute(k_ntt1<FWD, PRO, EPI, OTF>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1); });
+  if (e != cudaSuccess) return e;
   static const char *name = FWD ? (OTF ? "ntt1+otf" : "ntt1") : (OTF ? "intt1+otf" : "intt1");
   TraceScope ts(t, name, s);
   k_ntt1<FWD, PRO, EPI, OTF><<<grid, kNttThreads, smem, s>>>(first, second, t.ntt);
@@ -216,19 +213,18 @@ cudaError_t launch_ip(const DevTables &t, const SegList &sl, bool gather_own, bo
     const int per_stage = stage_bytes + 24 + (int)sizeof(IpUnit);  // data, three mbarriers, descriptor
     const int stages = std::min(ge ? 4 : 2, (113 * 1024 - 256) / per_stage);
     const int smem = stages * per_stage;
-    static bool configured[4] = {false, false, false, false};
+    static PerDeviceOnce configured[4];
     const int variant = (go ? 1 : 0) + (ge ? 2 : 0);
-    if (!configured[variant]) {
-      cudaError_t e = cudaSuccess;
+    const cudaError_t e = configured[variant].run([variant] {
+      constexpr int kMax = 113 * 1024;
       switch (variant) {
-        case 0: e = cudaFuncSetAttribute(k_ip_bulk<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 113 * 1024); break;
-        case 1: e = cudaFuncSetAttribute(k_ip_bulk<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 113 * 1024); break;
-        case 2: e = cudaFuncSetAttribute(k_ip_bulk<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 113 * 1024); break;
-        default: e = cudaFuncSetAttribute(k_ip_bulk<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 113 * 1024); break;
+        case 0: return cudaFuncSetAttribute(k_ip_bulk<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMax);
+        case 1: return cudaFuncSetAttribute(k_ip_bulk<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMax);
+        case 2: return cudaFuncSetAttribute(k_ip_bulk<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMax);
+        default: return cudaFuncSetAttribute(k_ip_bulk<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMax);
       }
-      if (e != cudaSuccess) return e;
-      configured[variant] = true;
-    }
+    });
+    if (e != cudaSuccess) return e;
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

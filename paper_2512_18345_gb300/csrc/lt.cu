@@ -146,10 +146,7 @@ __global__ void __launch_bounds__(kDiagThreads + 32, 1) k_diag_bulk(const __grid
   for (int u = blockIdx.x; ok && u < total; u += gridDim.x) {
     const int grp = u % groups, ch = (u / groups) % chunks, i = u / (groups * chunks);
     const PrimeC P = pc[limb_prime(i, a.level, a.L)];
-    uint32_t r34 = P.r32 << 2;  // 2^34 mod q from 2^32 mod q (< q): at most three subtractions
-    r34 = red2(r34, P.q);
-    r34 = red2(r34, P.q);
-    r34 = red2(r34, P.q);
+    const uint32_t r34 = P.r34;
     uint32_t gm[kGsub];
     uint32_t live = group_mask(grp, gm);
     uint64_t acc[2][kGsub][E];
@@ -223,13 +220,12 @@ __global__ void __launch_bounds__(kDiagThreads + 32, 1) k_diag_bulk(const __grid
 
 
 static cudaError_t launch_diag(fhe_ctx *c, const DiagArgs &da, cudaStream_t s) {
-  static bool configured = false;
-  if (!configured) {
-    const cudaError_t e = cudaFuncSetAttribute(k_diag_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               kDiagStages * kDiagStageBytes);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static PerDeviceOnce configured;
+  const cudaError_t e = configured.run([] {
+    return cudaFuncSetAttribute(k_diag_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kDiagStages * kDiagStageBytes);
+  });
+  if (e != cudaSuccess) return e;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
   const int units = da.nlimb * (int)(c->N / kDiagChunk) * ((da.giant + kGsub - 1) / kGsub);

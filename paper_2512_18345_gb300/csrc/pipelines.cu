@@ -419,6 +419,97 @@ extern "C" int fhe_moddown(fhe_ctx *c, const uint32_t *u, int level, uint32_t *o
   return FHE_OK;
 }
 
+// The tables of one fhe_bconv combination (input primes, output primes, kernel): the
+// pre-factors (Qstar/q_j)^-1 mod q_j, T[o][j] = (Qstar/q_j) mod p_o, the output map and, for
+// the tensor-core kernel, its byte-digit table.  The first call with a combination builds them,
+// allocates one device block and copies them with cudaMemcpyAsync on `s` (from pageable host
+// memory, so that first call may wait while the runtime stages it); later calls find them in
+// the context and allocate, copy and wait for nothing.
+// The context also keeps the pre-multiplied input ([16][N] words, allocated once).  Calls on a
+// context are ordered on the GPU (order_stream), so one copy of each serves every call.  A
+// context keeps at most kMaxBconvPrep combinations; a new one beyond that waits for the
+// context's earlier work and releases the cached tables first.
+static constexpr size_t kMaxBconvPrep = 64;
+
+static int bconv_prepare(fhe_ctx *c, const int *in_idx, int n_in, const int *out_idx, int n_out, bool tc, int kt,
+                         cudaStream_t s, fhe_ctx::BconvPrep *out) {
+  const size_t N = c->N;
+  if (!c->bconv_y) {
+    const size_t bytes = 16 * N * sizeof(uint32_t);
+    const int rc = c->reserve(bytes, "fhe_bconv scratch");
+    if (rc != FHE_OK) return rc;
+    if (cudaMalloc(&c->bconv_y, bytes) != cudaSuccess) return fhe_fail(FHE_ENOMEM, "fhe_bconv: scratch");
+    c->grown_bytes += bytes;
+  }
+  std::vector<int> key;
+  key.reserve(n_in + n_out + 3);
+  key.push_back(tc ? kt : 0);
+  key.push_back(n_in);
+  key.insert(key.end(), in_idx, in_idx + n_in);
+  key.insert(key.end(), out_idx, out_idx + n_out);
+  auto it = c->bconv_prep.find(key);
+  c->order_stream(s);
+  if (it != c->bconv_prep.end()) {
+    *out = it->second;
+    return FHE_OK;
+  }
+  if (c->bconv_prep.size() >= kMaxBconvPrep) {
+    // the cached tables may still be read by enqueued work: wait for it before freeing them
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fhe_fail(FHE_ECUDA, "fhe_bconv: sync before releasing tables");
+    for (auto &kv : c->bconv_prep) cudaFree(kv.second.block);
+    c->bconv_prep.clear();
+  }
+  const std::vector<uint32_t> &pr = c->primes;
+  std::vector<uint2> pre(n_in);
+  for (int j = 0; j < n_in; j++) {
+    const uint32_t q = pr[in_idx[j]];
+    uint32_t prod = 1;
+    for (int k = 0; k < n_in; k++)
+      if (k != j) prod = h_mulmod_pub(prod, pr[in_idx[k]] % q, q);
+    const uint32_t w = h_invmod_pub(prod, q);
+    pre[j] = make_uint2(w, (uint32_t)(((uint64_t)w << 32) / q));
+  }
+  std::vector<uint32_t> T((size_t)n_out * n_in);
+  std::vector<int2> om(n_out);
+  std::vector<uint32_t> pout(n_out);
+  for (int o = 0; o < n_out; o++) {
+    const uint32_t p = pr[out_idx[o]];
+    for (int j = 0; j < n_in; j++) {
+      uint32_t prod = 1;
+      for (int k = 0; k < n_in; k++)
+        if (k != j) prod = h_mulmod_pub(prod, pr[in_idx[k]] % p, p);
+      T[(size_t)o * n_in + j] = prod;
+    }
+    om[o] = make_int2(o, out_idx[o]);
+    pout[o] = p;
+  }
+  const std::vector<uint16_t> Btc = tc ? bconv_tc_table(T, n_in, pout, kt) : std::vector<uint16_t>(8, 0);
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t oT = 0, oM = up(4 * T.size()), oP = oM + up(8 * om.size()), oB = oP + up(8 * pre.size());
+  const size_t bytes = oB + up(2 * Btc.size());
+  const int rc = c->reserve(bytes, "fhe_bconv tables");
+  if (rc != FHE_OK) return rc;
+  fhe_ctx::BconvPrep p;
+  if (cudaMalloc(&p.block, bytes) != cudaSuccess) return fhe_fail(FHE_ENOMEM, "fhe_bconv: tables");
+  c->grown_bytes += bytes;
+  char *b = static_cast<char *>(p.block);
+  p.T = reinterpret_cast<uint32_t *>(b + oT);
+  p.om = reinterpret_cast<int2 *>(b + oM);
+  p.pre = reinterpret_cast<uint2 *>(b + oP);
+  p.Btc = reinterpret_cast<uint16_t *>(b + oB);
+  if (cudaMemcpyAsync(p.T, T.data(), 4 * T.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(p.om, om.data(), 8 * om.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(p.pre, pre.data(), 8 * pre.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(p.Btc, Btc.data(), 2 * Btc.size(), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    cudaFree(p.block);
+    c->grown_bytes -= bytes;
+    return fhe_fail(FHE_ECUDA, "fhe_bconv: table copy");
+  }
+  c->bconv_prep.emplace(std::move(key), p);
+  *out = p;
+  return FHE_OK;
+}
+
 extern "C" int fhe_bconv(fhe_ctx *c, const uint32_t *in, const int *in_idx, int n_in, uint32_t *out,
                          const int *out_idx, int n_out, fhe_stream stream) {
   if (!c) return fhe_fail(FHE_EINVAL, "fhe_bconv: null ctx");
@@ -437,84 +528,34 @@ extern "C" int fhe_bconv(fhe_ctx *c, const uint32_t *in, const int *in_idx, int 
   if (tc && n_in > kTcMaxIn12)
     return fhe_fail(FHE_EUNSUPPORTED, "fhe_bconv: tensor-core base conversion takes at most %d inputs", kTcMaxIn12);
   const int kt = tc_k_for(n_in);
-  const std::vector<uint32_t> &pr = c->primes;
-  // host tables: pre-factor (Qstar/q_j)^-1 mod q_j and T[o][j] = (Qstar/q_j) mod p_o
-  std::vector<uint2> pre(n_in);
-  for (int j = 0; j < n_in; j++) {
-    const uint32_t q = pr[in_idx[j]];
-    uint32_t prod = 1;
-    for (int k = 0; k < n_in; k++)
-      if (k != j) prod = h_mulmod_pub(prod, pr[in_idx[k]] % q, q);
-    pre[j] = make_uint2(h_invmod_pub(prod, q), (uint32_t)(((uint64_t)h_invmod_pub(prod, q) << 32) / q));
-  }
-  std::vector<uint32_t> T((size_t)n_out * n_in);
-  std::vector<int2> om(n_out);
-  for (int o = 0; o < n_out; o++) {
-    const uint32_t p = pr[out_idx[o]];
-    for (int j = 0; j < n_in; j++) {
-      uint32_t prod = 1;
-      for (int k = 0; k < n_in; k++)
-        if (k != j) prod = h_mulmod_pub(prod, pr[in_idx[k]] % p, p);
-      T[(size_t)o * n_in + j] = prod;
-    }
-    om[o] = make_int2(o, out_idx[o]);
-  }
   cudaSetDevice(c->device);
   cudaStream_t s = (cudaStream_t)stream;
-  c->order_stream(s);
-  uint32_t *dT = nullptr, *y = nullptr;
-  int2 *dM = nullptr;
-  uint2 *dPre = nullptr;
-  uint16_t *dB = nullptr;
-  std::vector<uint32_t> pout;
-  for (int o = 0; o < n_out; o++) pout.push_back(pr[out_idx[o]]);
-  const std::vector<uint16_t> Btc = tc ? bconv_tc_table(T, n_in, pout, kt) : std::vector<uint16_t>(8, 0);
-  auto cleanup = [&]() {
-    cudaFree(dT);
-    cudaFree(dM);
-    cudaFree(dPre);
-    cudaFree(y);
-    cudaFree(dB);
-  };
-  if (cudaMalloc(&dT, 4 * T.size()) != cudaSuccess || cudaMalloc(&dM, 8 * om.size()) != cudaSuccess ||
-      cudaMalloc(&dPre, 8 * pre.size()) != cudaSuccess || cudaMalloc(&y, 4 * N * n_in) != cudaSuccess ||
-      cudaMalloc(&dB, 2 * Btc.size()) != cudaSuccess) {
-    cleanup();
-    return fhe_fail(FHE_ENOMEM, "fhe_bconv: temporary tables");
-  }
-  cudaMemcpy(dB, Btc.data(), 2 * Btc.size(), cudaMemcpyHostToDevice);
-  cudaMemcpy(dT, T.data(), 4 * T.size(), cudaMemcpyHostToDevice);
-  cudaMemcpy(dM, om.data(), 8 * om.size(), cudaMemcpyHostToDevice);
-  cudaMemcpy(dPre, pre.data(), 8 * pre.size(), cudaMemcpyHostToDevice);
+  fhe_ctx::BconvPrep prep;
+  const int rc0 = bconv_prepare(c, in_idx, n_in, out_idx, n_out, tc, kt, s, &prep);
+  if (rc0 != FHE_OK) return rc0;
   // pre-multiply limb by limb (each limb its own prime: one segment per limb)
-  int rc = FHE_OK;
-  for (int j0 = 0; j0 < n_in && rc == FHE_OK; j0 += kMaxSeg) {
+  uint32_t *y = c->bconv_y;
+  for (int j0 = 0; j0 < n_in; j0 += kMaxSeg) {
     SegBuilder sb;
     for (int j = j0; j < std::min(n_in, j0 + kMaxSeg); j++) {
       Seg x = mkseg(in + (size_t)j * N, y + (size_t)j * N, 1, in_idx[j]);
-      x.scale = dPre + j;
+      x.scale = prep.pre + j;
       sb.add(x);
     }
-    if (launch_ew(c->tabs, EW_SCALE, sb.l, s) != cudaSuccess)
-      rc = fhe_fail(FHE_ECUDA, "fhe_bconv: scale");
+    if (launch_ew(c->tabs, EW_SCALE, sb.l, s) != cudaSuccess) return fhe_fail(FHE_ECUDA, "fhe_bconv: scale");
   }
   BconvArgs ba;
   memset(&ba, 0, sizeof ba);
   BconvGroup &g = ba.g[ba.ngroups++];
   g.in = y;
   g.out = out;
-  g.T = dT;
-  g.omap = dM;
+  g.T = prep.T;
+  g.omap = prep.om;
   g.n_in = n_in;
   g.n_out = n_out;
-  g.Btc = dB;
+  g.Btc = prep.Btc;
   g.npad = tc_npad(n_out);
-  if (rc == FHE_OK) {
-    cudaError_t e = tc ? launch_bconv_tc(c->tabs, ba, n_in, n_out, s, kt) : launch_bconv(c->tabs, ba, n_in, n_out, s);
-    if (e != cudaSuccess) rc = fhe_fail(FHE_ECUDA, "fhe_bconv: %s", cudaGetErrorString(e));
-  }
-  // the temporary tables are released once the stream has consumed them
-  if (cudaStreamSynchronize(s) != cudaSuccess && rc == FHE_OK) rc = fhe_fail(FHE_ECUDA, "fhe_bconv: sync");
-  cleanup();
-  return rc;
+  const cudaError_t e = tc ? launch_bconv_tc(c->tabs, ba, n_in, n_out, s, kt) : launch_bconv(c->tabs, ba, n_in, n_out, s);
+  if (e != cudaSuccess) return fhe_fail(FHE_ECUDA, "fhe_bconv: %s", cudaGetErrorString(e));
+  return FHE_OK;
 }

@@ -113,6 +113,37 @@ def test_bconv_extremes(c2, fill):
     assert np.array_equal(got, oracle.bconv(x, pin, pout))
 
 
+def test_bconv_table_cache(c1):
+    """fhe_bconv keeps the tables of each (inputs, outputs, kernel) combination in the context:
+    repeated and interleaved combinations, both kernels, and more combinations than the context
+    keeps (it waits and releases them) all stay bit-exact, queued back to back without a sync."""
+    from paper_2512_18345_gb300 import binding
+    P, OP, ctx = c1
+    g = inputs.rng(15)
+    nP = len(P.primes)
+    import itertools
+    combos = []
+    for n_in in (1, 2, 3):
+        for ins in itertools.permutations(range(nP), n_in):
+            if n_in == 3 and list(ins) != sorted(ins):
+                continue
+            combos.append((list(ins), [i for i in range(nP) if i not in ins]))
+    # 56 index combinations, each with the CUDA-core kernel and every other one with the
+    # tensor-core kernel too: 84 table sets, more than the 64 a context keeps; then the first
+    # ones again
+    runs = [(c, binding.FHE_BCONV_SCALAR) for c in combos] + [(c, binding.FHE_BCONV_TC) for c in combos[::2]]
+    runs += runs[:5]
+    pending = []
+    for (in_idx, out_idx), mode in runs:
+        ctx.set_bconv(mode)
+        x = inputs.uniform_residues(g, [P.primes[i] for i in in_idx], P.N)
+        pending.append((x, in_idx, out_idx, ctx.bconv(dev(x), in_idx, out_idx)))
+    ctx.set_bconv(binding.FHE_BCONV_SCALAR)
+    for x, in_idx, out_idx, out in pending:
+        want = oracle.bconv(x, [P.primes[i] for i in in_idx], [P.primes[i] for i in out_idx])
+        assert np.array_equal(host(out), want), (in_idx, out_idx)
+
+
 # ------------------------------------------------------------------ stages
 
 @pytest.mark.parametrize("cfg,level", [("c1", 4), ("c1", 3), ("c1", 1), ("c2", 24), ("c2", 17), ("c2", 9)])

@@ -1,10 +1,11 @@
 """The allocation-free base conversion (fhe_bconv_noalloc) against the
 allocating one (fhe_bconv), called through the C ABI.
 
-fhe_bconv_noalloc exists for callers that cannot allocate device memory
-(stream capture in progress, latency-critical loops, a framework pool holding
-all memory).  Its scratch is one fixed device array shared by every call, so
-the test makes two different calls in a row: the second must not see the
+fhe_bconv_noalloc exists for callers that cannot allocate device memory once
+they run: a process whose framework pool already holds all free device memory,
+or a real-time loop that must not take cudaMalloc's device-wide
+synchronization.  Its scratch is one fixed device array shared by every call,
+so the tests make two different calls in a row: the second must not see the
 first one's leftovers.  The file name sorts last so that a run stopping at the
 first failure has run every other test first.
 """
@@ -33,6 +34,32 @@ def test_bconv_noalloc_matches_bconv_twice(fhe_lib):
         ctx.bconv_noalloc(xd, in_idx, out_idx, got)
         torch.cuda.synchronize()
         assert np.array_equal(binding.to_numpy(got), binding.to_numpy(want))
+    ctx.close()
+
+
+def test_bconv_noalloc_queued_behind_other_work(fhe_lib):
+    """Both calls are enqueued while the stream is still busy, so neither has run when the
+    second one returns: each call's tables travel with its own launch."""
+    import torch
+    from paper_2512_18345_gb300 import binding
+    P = inputs.workload_params("hrotate_N65536_L24_plain")
+    ctx = binding.Context.from_params(P)
+    g = inputs.rng(4343)
+    calls = [(list(range(16, 24)), list(range(16)) + list(range(24, 32))),
+             (list(range(0, 3)), list(range(3, 30)))]
+    xs = [binding.to_device(inputs.uniform_residues(g, [P.primes[i] for i in c[0]], P.N)) for c in calls]
+    wants = [ctx.bconv(x, c[0], c[1]) for x, c in zip(xs, calls)]
+    torch.cuda.synchronize()
+    outs = [binding.empty((len(c[1]), P.N)) for c in calls]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        torch.cuda._sleep(20_000_000)  # about 10 ms of one busy thread
+        for x, c, o in zip(xs, calls, outs):
+            ctx.bconv_noalloc(x, c[0], c[1], o, stream=s)
+    s.synchronize()
+    for o, w in zip(outs, wants):
+        assert np.array_equal(binding.to_numpy(o), binding.to_numpy(w))
     ctx.close()
 
 
