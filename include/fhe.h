@@ -144,13 +144,20 @@ FHE_API int fhe_ctx_set_pipelining(fhe_ctx *ctx, int on);
  *     from one loaded twiddle and a staged 8-entry table instead of loading each;
  *   FHE_NTT_SINGLE_PASS: each 2^16-point transform of a stage program runs as
  *     one launch with a cluster of 16 CTAs per limb, the first pass's tiles
- *     staying in shared memory for the second (no global round trip).
+ *     staying in shared memory for the second (no global round trip);
+ *   FHE_NTT_STREAM: the column and block passes run as persistent kernels: a
+ *     producer warp copies each tile into a ring of shared-memory stages ahead
+ *     of eight consumer warps, which keep their twiddles in registers across
+ *     consecutive tiles of the same prime (N = 2^16; the gather, reduce and
+ *     rescale forms keep the two-pass kernels).  With FHE_NTT_SINGLE_PASS, the
+ *     transforms the single-pass kernel covers use it and the others stream.
  * Results are identical in every mode.  Programs and plans built after the call
- * use the new mode.  FHE_EUNSUPPORTED for FHE_NTT_SINGLE_PASS at N != 2^16 or on
+ * use the new mode.  FHE_EUNSUPPORTED for FHE_NTT_STREAM at N != 2^16, for FHE_NTT_SINGLE_PASS at N != 2^16 or on
  * a device that cannot hold a 16-CTA cluster of the kernel; FHE_EINVAL for
  * unknown flags.  fhe_autotune with FHE_TUNE_NTT measures the modes. */
 #define FHE_NTT_OTF 1
 #define FHE_NTT_SINGLE_PASS 2
+#define FHE_NTT_STREAM 4
 FHE_API int fhe_ctx_set_ntt(fhe_ctx *ctx, int flags);
 
 /*

@@ -25,7 +25,7 @@ FHE_OP_KS, FHE_OP_ROTATE, FHE_OP_RELIN = 0, 1, 2
 FHE_PLAN_GRAPH = 1
 FHE_TUNE_BCONV = 1
 FHE_TUNE_NTT = 2
-FHE_NTT_OTF, FHE_NTT_SINGLE_PASS = 1, 2
+FHE_NTT_OTF, FHE_NTT_SINGLE_PASS, FHE_NTT_STREAM = 1, 2, 4
 
 # every entry point declared in include/fhe.h
 EXPORTS = (

@@ -102,7 +102,8 @@ extern "C" int fhe_autotune(fhe_ctx *c, int level, int n_items, int flags, fhe_t
   best.us_per_ks = 1e30;
   int rc = FHE_OK, tried = 0;
   const int saved_ip = c->tabs.ip_ctas_per_sm, saved_comp = c->comp_pipe;
-  const int saved_ntt = (c->tabs.ntt_otf ? FHE_NTT_OTF : 0) | (c->tabs.ntt_single ? FHE_NTT_SINGLE_PASS : 0);
+  const int saved_ntt = (c->tabs.ntt_otf ? FHE_NTT_OTF : 0) | (c->tabs.ntt_single ? FHE_NTT_SINGLE_PASS : 0) |
+                        (c->tabs.ntt_stream ? FHE_NTT_STREAM : 0);
   fhe_tune_result by_ip[2];  // fastest schedule with one / two inner-product CTAs per SM
   memset(by_ip, 0, sizeof by_ip);
   by_ip[0].us_per_ks = by_ip[1].us_per_ks = 1e30;
@@ -183,7 +184,8 @@ extern "C" int fhe_autotune(fhe_ctx *c, int level, int n_items, int flags, fhe_t
     c->tabs.ip_ctas_per_sm = best.ip_ctas_per_sm;
     c->comp_pipe = best.comp_pipe;
     const double base = best.us_per_ks;
-    for (int m : {0, FHE_NTT_OTF, FHE_NTT_SINGLE_PASS, FHE_NTT_SINGLE_PASS | FHE_NTT_OTF}) {
+    for (int m : {0, FHE_NTT_OTF, FHE_NTT_SINGLE_PASS, FHE_NTT_SINGLE_PASS | FHE_NTT_OTF, FHE_NTT_STREAM,
+                  FHE_NTT_STREAM | FHE_NTT_OTF, FHE_NTT_STREAM | FHE_NTT_SINGLE_PASS}) {
       if (m == saved_ntt || fhe_ctx_set_ntt(c, m) != FHE_OK) continue;
       fhe_plan *p = nullptr;
       rc = fhe_batch_plan(c, items.data(), n_items, FHE_PLAN_GRAPH, &p);
@@ -250,7 +252,7 @@ static bool tune_parse(const char *rest, fhe_tune_result *r) {
              &t.max_group, &t.bconv_mode, &t.ip_ctas_per_sm, &t.comp_pipe, &t.ntt_mode, &t.us_per_ks) != 8)
     return false;
   if (t.comp_pipe != 0 && t.comp_pipe != 1) return false;
-  if (t.ntt_mode & ~(FHE_NTT_OTF | FHE_NTT_SINGLE_PASS)) return false;
+  if (t.ntt_mode & ~(FHE_NTT_OTF | FHE_NTT_SINGLE_PASS | FHE_NTT_STREAM)) return false;
   if (t.lanes < 1 || t.lanes > 4 || t.ip_ctas_per_sm < 1 || t.ip_ctas_per_sm > 2 ||
       (t.bconv_mode != FHE_BCONV_SCALAR && t.bconv_mode != FHE_BCONV_TC) || t.max_group < 0)
     return false;

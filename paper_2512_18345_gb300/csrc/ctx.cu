@@ -262,6 +262,8 @@ static int build_tables(fhe_ctx *c) {
   c->tabs.ip_ctas_per_sm = 2;
   c->tabs.ntt_otf = 0;
   c->tabs.ntt_single = 0;
+  c->tabs.ntt_stream = 0;
+  c->tabs.ntt_stream_stages = 3;
   c->tabs.status = c->d_status;
   return FHE_OK;
 }
@@ -521,7 +523,10 @@ extern "C" int fhe_ctx_set_pipelining(fhe_ctx *c, int on) {
 
 extern "C" int fhe_ctx_set_ntt(fhe_ctx *c, int flags) {
   if (!c) return fhe_fail(FHE_EINVAL, "fhe_ctx_set_ntt: null");
-  if (flags & ~(FHE_NTT_OTF | FHE_NTT_SINGLE_PASS)) return fhe_fail(FHE_EINVAL, "fhe_ctx_set_ntt: flags 0x%x", flags);
+  if (flags & ~(FHE_NTT_OTF | FHE_NTT_SINGLE_PASS | FHE_NTT_STREAM))
+    return fhe_fail(FHE_EINVAL, "fhe_ctx_set_ntt: flags 0x%x", flags);
+  if ((flags & FHE_NTT_STREAM) && c->logn != 16)
+    return fhe_fail(FHE_EUNSUPPORTED, "fhe_ctx_set_ntt: the streaming NTT passes need N = 2^16");
   if (flags & FHE_NTT_SINGLE_PASS) {
     if (c->logn != 16) return fhe_fail(FHE_EUNSUPPORTED, "fhe_ctx_set_ntt: the single-pass NTT needs N = 2^16");
     cudaSetDevice(c->device);
@@ -530,6 +535,7 @@ extern "C" int fhe_ctx_set_ntt(fhe_ctx *c, int flags) {
   }
   c->tabs.ntt_otf = (flags & FHE_NTT_OTF) ? 1 : 0;
   c->tabs.ntt_single = (flags & FHE_NTT_SINGLE_PASS) ? 1 : 0;
+  c->tabs.ntt_stream = (flags & FHE_NTT_STREAM) ? 1 : 0;
   return FHE_OK;
 }
 

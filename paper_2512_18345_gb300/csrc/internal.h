@@ -61,6 +61,8 @@ struct DevTables {
   int ip_ctas_per_sm;      // resident CTAs per SM of the streaming inner product (1 or 2; autotuned)
   int ntt_otf;             // block passes form their register twiddles on the fly
   int ntt_single;          // 2^16-point transforms in one cluster launch instead of two passes
+  int ntt_stream;          // the passes as persistent kernels fed by a producer warp (ntt_bulk.cuh)
+  int ntt_stream_stages;   // shared-memory stages per CTA of those kernels
   int tc_k;                // K of the context's tensor-core BConv tables (48 or 64; 0: none)
 };
 

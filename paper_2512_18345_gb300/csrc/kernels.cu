@@ -8,6 +8,7 @@
 #include "elementwise.cuh"
 #include "internal.h"
 #include "ntt.cuh"
+#include "ntt_bulk.cuh"
 
 namespace fhe {
 
@@ -65,12 +66,48 @@ static cudaError_t ntt_go(const DevTables &t, const SegList &sl, cudaStream_t s)
   return cudaGetLastError();
 }
 
+// Streaming pass (ntt_bulk.cuh): persistent CTAs, two per SM, each walking a contiguous
+// range of the launch's units.
+template <bool COLUMN, bool FWD, int EPI>
+static cudaError_t ntt_bulk_go(const DevTables &t, const SegList &sl, cudaStream_t s) {
+  const int units = sl.total * kNbTiles;
+  if (units == 0) return cudaSuccess;
+  const int stages = t.ntt_stream_stages;
+  const int smem = ntt_bulk_smem(stages);
+  static PerDeviceOnce configured;
+  cudaError_t e = configured.run([] {
+    return cudaFuncSetAttribute(k_ntt_bulk<COLUMN, FWD, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                ntt_bulk_smem(8));
+  });
+  if (e != cudaSuccess) return e;
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::min(units, 3 * sms);
+  static const char *names[2][2] = {{"intt_blk", "ntt_blk"}, {"intt_col", "ntt_col"}};
+  const char *name = EPI == EPI_COMBINE ? "ntt_blk+combine" : EPI == EPI_SCALE ? "intt_col+scale"
+                     : EPI == EPI_PLAIN ? "ntt_blk" : names[COLUMN][FWD];
+  TraceScope ts(t, name, s);
+  k_ntt_bulk<COLUMN, FWD, EPI><<<grid, kNbThreads, smem, s>>>(sl, t.ntt, t.status, stages);
+  g_launches++;
+  return cudaGetLastError();
+}
+
 // The (column, fwd, pro, epi) combinations the library uses; on-the-fly twiddles apply to
 // the block passes.
 template <int LOGN>
 static cudaError_t ntt_dispatch(const DevTables &t, bool column, bool fwd, int pro, int epi, const SegList &sl,
                                 cudaStream_t s) {
   const bool otf = t.ntt_otf != 0;
+  if constexpr (LOGN == 16) {
+    if (t.ntt_stream && pro == PRO_PLAIN) {
+      if (column && fwd && epi == EPI_LAZY) return ntt_bulk_go<true, true, EPI_LAZY>(t, sl, s);
+      if (column && !fwd && epi == EPI_SCALE) return ntt_bulk_go<true, false, EPI_SCALE>(t, sl, s);
+      if (!column && fwd && epi == EPI_PLAIN) return ntt_bulk_go<false, true, EPI_PLAIN>(t, sl, s);
+      if (!column && fwd && epi == EPI_COMBINE) return ntt_bulk_go<false, true, EPI_COMBINE>(t, sl, s);
+      if (!column && !fwd && epi == EPI_LAZY) return ntt_bulk_go<false, false, EPI_LAZY>(t, sl, s);
+    }
+  }
 #define NTT_CASE(COL, FWDV, P, E)                                                              \
   if (column == COL && fwd == FWDV && pro == P && epi == E) {                                  \
     if constexpr (!COL) {                                                                      \

@@ -399,16 +399,25 @@ int upload_program(fhe_ctx *c, const Program &P, DevProgram &D) {
   for (size_t i = 0; i < P.stages.size(); i++) {
     const Stage &st = P.stages[i];
     memcpy(host.data() + seg_off[i], st.segs.data(), sizeof(Seg) * st.segs.size());
-    int2 *m = reinterpret_cast<int2 *>(host.data() + map_off[i]);
-    int v = 0;
-    for (size_t sidx = 0; sidx < st.segs.size(); sidx++)
-      for (int w = 0; w < st.segs[sidx].n; w++) m[v++] = make_int2((int)sidx, w);
+    // limb map: transform stages list their limbs grouped by prime (stable), so that the
+    // streaming passes' consecutive units share twiddles; the order of limbs within a launch
+    // does not change any result, and NTT1's two lists get the same permutation (same
+    // segment sizes and primes)
+    const bool by_prime = st.kind == Stage::NTT || st.kind == Stage::NTT1;
+    auto fill_map = [by_prime](const std::vector<Seg> &segs, int2 *m) {
+      std::vector<int2> v;
+      for (size_t sidx = 0; sidx < segs.size(); sidx++)
+        for (int w = 0; w < segs[sidx].n; w++) v.push_back(make_int2((int)sidx, w));
+      if (by_prime)
+        std::stable_sort(v.begin(), v.end(), [&segs](const int2 &a, const int2 &b) {
+          return segs[a.x].prime + a.y < segs[b.x].prime + b.y;
+        });
+      std::copy(v.begin(), v.end(), m);
+    };
+    fill_map(st.segs, reinterpret_cast<int2 *>(host.data() + map_off[i]));
     memcpy(host.data() + grp_off[i], st.groups.data(), sizeof(BconvGroup) * st.groups.size());
     memcpy(host.data() + seg2_off[i], st.segs2.data(), sizeof(Seg) * st.segs2.size());
-    int2 *m2 = reinterpret_cast<int2 *>(host.data() + map2_off[i]);
-    int v2 = 0;
-    for (size_t sidx = 0; sidx < st.segs2.size(); sidx++)
-      for (int w = 0; w < st.segs2[sidx].n; w++) m2[v2++] = make_int2((int)sidx, w);
+    fill_map(st.segs2, reinterpret_cast<int2 *>(host.data() + map2_off[i]));
   }
   if (cudaMalloc(&D.buf, bytes) != cudaSuccess) return fhe_fail(FHE_ENOMEM, "program upload: %zu bytes", bytes);
   if (cudaMemcpy(D.buf, host.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess)

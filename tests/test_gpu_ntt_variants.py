@@ -1,5 +1,5 @@
 """NTT kernel variants (fhe_ctx_set_ntt): on-the-fly register twiddles in the
-block passes and the single-pass cluster transform.  Every mode must give the
+block passes, the single-pass cluster transform and the streaming passes.  Every mode must give the
 oracle's residues bit for bit: the stage entry points, a batched graph plan of
 mixed key switches, hoisted rotations, HMult + rescale and the double-hoisted
 transform."""
@@ -12,7 +12,8 @@ from paper_2512_18345_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-MODES = [0, 1, 2, 3]  # 0, FHE_NTT_OTF, FHE_NTT_SINGLE_PASS, both
+# 0, FHE_NTT_OTF, FHE_NTT_SINGLE_PASS, both; FHE_NTT_STREAM alone, with OTF, with SINGLE_PASS
+MODES = [0, 1, 2, 3, 4, 5, 6]
 
 
 def dev(a):
@@ -118,7 +119,7 @@ def test_single_ops_each_mode(big, mode, fused):
     ctx.set_ntt(0)
 
 
-@pytest.mark.parametrize("mode", [1, 2, 3])
+@pytest.mark.parametrize("mode", [1, 2, 3, 4, 6])
 def test_double_hoisted_level_each_mode(fhe_lib, mode):
     from paper_2512_18345_gb300 import binding
     name = "cts_stc_N65536_L48_a12"
@@ -142,7 +143,7 @@ def test_double_hoisted_level_each_mode(fhe_lib, mode):
 
 
 def test_small_ring_modes(fhe_lib):
-    """N = 2^12: on-the-fly twiddles apply; the single-pass transform is 2^16-only."""
+    """N = 2^12: on-the-fly twiddles apply; the single-pass and streaming transforms are 2^16-only."""
     from paper_2512_18345_gb300 import binding
     P = inputs.workload_params("hmult_relin_rescale_N4096_L4")
     OP = oracle.OracleParams.from_params(P)
@@ -151,7 +152,10 @@ def test_small_ring_modes(fhe_lib):
         ctx.set_ntt(binding.FHE_NTT_SINGLE_PASS)
     assert e.value.code == binding.FHE_EUNSUPPORTED
     with pytest.raises(binding.FheError) as e:
-        ctx.set_ntt(4)
+        ctx.set_ntt(binding.FHE_NTT_STREAM)
+    assert e.value.code == binding.FHE_EUNSUPPORTED
+    with pytest.raises(binding.FheError) as e:
+        ctx.set_ntt(8)
     assert e.value.code == binding.FHE_EINVAL
     ctx.set_ntt(binding.FHE_NTT_OTF)
     g = inputs.rng(1900)
@@ -173,3 +177,29 @@ def test_autotune_measures_ntt_modes(big):
     d = inputs.uniform_residues(g, P.q, P.N)
     assert np.array_equal(host(ctx, ctx.keyswitch(dev(d), P.L)), oracle.keyswitch(OP, d, P.L, key))
     ctx.set_ntt(0)
+
+
+@pytest.mark.parametrize("n_limbs", [1, 7, 33, 130])
+def test_streaming_passes_ragged_unit_counts(big, n_limbs):
+    """Streaming passes with launches whose unit count does not divide evenly among the
+    persistent CTAs, runs of limbs shorter than a block-pass run, repeated primes in one
+    launch and all-(q - 1) limbs: equal to the oracle and to the two-pass kernels."""
+    from paper_2512_18345_gb300 import binding
+    P, OP, ctx = big
+    g = inputs.rng(2100 + n_limbs)
+    idx = [(7 * i) % len(P.primes) for i in range(n_limbs)]
+    primes = [P.primes[i] for i in idx]
+    a = np.stack([inputs.uniform_residues(g, [p], P.N)[0] for p in primes])
+    a[0] = primes[0] - 1
+    got = {}
+    for mode in (0, binding.FHE_NTT_STREAM):
+        ctx.set_ntt(mode)
+        t = dev(a)
+        ctx.ntt(t, idx)
+        f = host(ctx, t)
+        ctx.intt(t, idx)
+        got[mode] = (f, host(ctx, t))
+    ctx.set_ntt(0)
+    assert np.array_equal(got[0][0], got[binding.FHE_NTT_STREAM][0])
+    assert np.array_equal(got[binding.FHE_NTT_STREAM][0], oracle.ntt(a, primes))
+    assert np.array_equal(got[binding.FHE_NTT_STREAM][1], a)
