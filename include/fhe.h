@@ -160,6 +160,33 @@ FHE_API int fhe_ctx_set_pipelining(fhe_ctx *ctx, int on);
 #define FHE_NTT_STREAM 4
 FHE_API int fhe_ctx_set_ntt(fhe_ctx *ctx, int flags);
 
+/* Kernel shapes (results are identical for every shape; fhe_autotune with
+ * FHE_TUNE_SHAPE measures them):
+ *   fuse_ip_moddown: 1 runs the key inner product of the K special limbs and
+ *     the first pass of ModDown's inverse NTT as one kernel (Section IV,
+ *     stage 2 feeding stage 3): u's special limbs stay in registers; for key
+ *     switches whose digits are read directly (not hoisted rotations), N = 2^16
+ *     and at most four digits;
+ *   bconv_tc_ctas: resident CTAs per SM of the tensor-core BConv (1..4; fewer
+ *     leave shared memory and tensor memory to kernels of other lanes);
+ *   bconv_tc_pipeline: 1 gives each tensor-core BConv CTA two operand buffers
+ *     and two tensor-memory accumulators, so that a tile's MMA runs while the
+ *     previous tile's accumulator is reduced (at most two CTAs per SM for more
+ *     than 16 outputs, one for more than 32);
+ *   ntt_stream_stages, ntt_stream_ctas: shared-memory stages per CTA (2..3) and
+ *     persistent CTAs per SM (1..3) of the FHE_NTT_STREAM passes.
+ * Programs and plans built after the call use the new shape.  FHE_EINVAL for a
+ * value out of range; FHE_EUNSUPPORTED for fuse_ip_moddown at N != 2^16. */
+typedef struct {
+  int fuse_ip_moddown;
+  int bconv_tc_ctas;
+  int ntt_stream_stages;
+  int ntt_stream_ctas;
+  int bconv_tc_pipeline;
+} fhe_kernel_shape;
+FHE_API int fhe_ctx_set_kernel_shape(fhe_ctx *ctx, const fhe_kernel_shape *shape);
+FHE_API int fhe_ctx_get_kernel_shape(const fhe_ctx *ctx, fhe_kernel_shape *out);
+
 /*
  * Switching keys ([dnum][2][L + K][N] uint32, NTT form, host or device
  * pointer).  The context copies the key (it owns the copy); the copy is
@@ -344,6 +371,7 @@ FHE_API int fhe_ctx_set_batch(fhe_ctx *ctx, size_t l2_budget_bytes, int max_grou
  */
 #define FHE_TUNE_BCONV 1 /* also choose between the CUDA-core and tensor-core BConv */
 #define FHE_TUNE_NTT 2   /* then also measure the NTT variants (fhe_ctx_set_ntt) under the chosen schedule */
+#define FHE_TUNE_SHAPE 4 /* then also measure kernel shapes (fhe_ctx_set_kernel_shape) one parameter at a time */
 typedef struct {
   int lanes;              /* chosen lane count */
   size_t l2_budget_bytes; /* chosen group budget */
@@ -356,6 +384,7 @@ typedef struct {
   int ip_ctas_per_sm;     /* chosen residency of the streaming inner product */
   int comp_pipe;          /* 1: complementary pipelining (q-limb inner product on its own branch) */
   int ntt_mode;           /* chosen fhe_ctx_set_ntt flags (with FHE_TUNE_NTT; else the context's) */
+  fhe_kernel_shape shape; /* chosen kernel shape (with FHE_TUNE_SHAPE; else the context's) */
 } fhe_tune_result;
 FHE_API int fhe_autotune(fhe_ctx *ctx, int level, int n_items, int flags, fhe_tune_result *out, fhe_stream stream);
 /*

@@ -25,6 +25,7 @@ FHE_OP_KS, FHE_OP_ROTATE, FHE_OP_RELIN = 0, 1, 2
 FHE_PLAN_GRAPH = 1
 FHE_TUNE_BCONV = 1
 FHE_TUNE_NTT = 2
+FHE_TUNE_SHAPE = 4
 FHE_NTT_OTF, FHE_NTT_SINGLE_PASS, FHE_NTT_STREAM = 1, 2, 4
 
 # every entry point declared in include/fhe.h
@@ -34,7 +35,7 @@ EXPORTS = (
     "fhe_rotate_hoisted", "fhe_linear_transform", "fhe_linear_transform_dh", "fhe_pmult", "fhe_add", "fhe_ntt", "fhe_intt", "fhe_modup", "fhe_moddown",
     "fhe_bconv", "fhe_batch_plan", "fhe_batch_launch", "fhe_plan_destroy", "fhe_plan_kernel_count",
     "fhe_plan_groups", "fhe_ctx_set_batch",
-    "fhe_trace_enable", "fhe_trace_read", "fhe_probe_bandwidth", "fhe_probe_int", "fhe_autotune", "fhe_autotune_cached", "fhe_ctx_set_pipelining", "fhe_ctx_set_ntt", "fhe_ctx_set_memory_limit", "fhe_selftest_wait_timeout", "fhe_bconv_noalloc", "fhe_last_error",
+    "fhe_trace_enable", "fhe_trace_read", "fhe_probe_bandwidth", "fhe_probe_int", "fhe_autotune", "fhe_autotune_cached", "fhe_ctx_set_pipelining", "fhe_ctx_set_ntt", "fhe_ctx_set_kernel_shape", "fhe_ctx_get_kernel_shape", "fhe_ctx_set_memory_limit", "fhe_selftest_wait_timeout", "fhe_bconv_noalloc", "fhe_last_error",
 )
 
 
@@ -62,11 +63,18 @@ class IntPeaks(ctypes.Structure):
                 ("imad_hi_per_s", ctypes.c_double), ("add_min_per_s", ctypes.c_double), ("sms", ctypes.c_int)]
 
 
+class KernelShape(ctypes.Structure):
+    _fields_ = [("fuse_ip_moddown", ctypes.c_int), ("bconv_tc_ctas", ctypes.c_int),
+                ("ntt_stream_stages", ctypes.c_int), ("ntt_stream_ctas", ctypes.c_int),
+                ("bconv_tc_pipeline", ctypes.c_int)]
+
+
 class TuneResult(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_int), ("l2_budget_bytes", ctypes.c_size_t), ("max_group", ctypes.c_int),
                 ("bconv_mode", ctypes.c_int), ("n_groups", ctypes.c_int), ("us_per_ks", ctypes.c_double),
                 ("default_us_per_ks", ctypes.c_double), ("candidates", ctypes.c_int),
-                ("ip_ctas_per_sm", ctypes.c_int), ("comp_pipe", ctypes.c_int), ("ntt_mode", ctypes.c_int)]
+                ("ip_ctas_per_sm", ctypes.c_int), ("comp_pipe", ctypes.c_int), ("ntt_mode", ctypes.c_int),
+                ("shape", KernelShape)]
 
 
 class KsItem(ctypes.Structure):
@@ -130,6 +138,8 @@ def lib() -> ctypes.CDLL:
         "fhe_selftest_wait_timeout": [vp, vp],
         "fhe_ctx_set_pipelining": [vp, ctypes.c_int],
         "fhe_ctx_set_ntt": [vp, ctypes.c_int],
+        "fhe_ctx_set_kernel_shape": [vp, ctypes.POINTER(KernelShape)],
+        "fhe_ctx_get_kernel_shape": [vp, ctypes.POINTER(KernelShape)],
         "fhe_ctx_set_memory_limit": [vp, ctypes.c_size_t],
         "fhe_autotune": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(TuneResult), vp],
         "fhe_autotune_cached": [vp, ctypes.c_char_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -299,15 +309,33 @@ class Context:
                                             _stream(stream)))
         else:
             check(lib().fhe_autotune(self.h, level, n_items, flags, ctypes.byref(r), _stream(stream)))
-        return {f: getattr(r, f) for f, _ in TuneResult._fields_}
+        out = {f: getattr(r, f) for f, _ in TuneResult._fields_ if f != "shape"}
+        out["shape"] = {f: getattr(r.shape, f) for f, _ in KernelShape._fields_}
+        return out
 
     def set_memory_limit(self, nbytes: int) -> None:
         """Cap the device memory the context may still grow into (0: no cap)."""
         check(lib().fhe_ctx_set_memory_limit(self.h, int(nbytes)))
 
     def set_ntt(self, flags: int) -> None:
-        """NTT kernel variants: 0, FHE_NTT_OTF, FHE_NTT_SINGLE_PASS or both."""
+        """NTT kernel variants: 0 or FHE_NTT_OTF | FHE_NTT_SINGLE_PASS | FHE_NTT_STREAM flags."""
         check(lib().fhe_ctx_set_ntt(self.h, int(flags)))
+
+    def kernel_shape(self) -> dict:
+        r = KernelShape()
+        check(lib().fhe_ctx_get_kernel_shape(self.h, ctypes.byref(r)))
+        return {f: getattr(r, f) for f, _ in KernelShape._fields_}
+
+    def set_kernel_shape(self, **kw) -> None:
+        """Change some fields of the kernel shape (fuse_ip_moddown, bconv_tc_ctas,
+        ntt_stream_stages, ntt_stream_ctas, bconv_tc_pipeline); the others keep their values."""
+        cur = self.kernel_shape()
+        unknown = set(kw) - set(cur)
+        if unknown:
+            raise ValueError(f"unknown kernel-shape fields {sorted(unknown)}")
+        cur.update(kw)
+        r = KernelShape(**{k: int(v) for k, v in cur.items()})
+        check(lib().fhe_ctx_set_kernel_shape(self.h, ctypes.byref(r)))
 
     def set_pipelining(self, on: bool) -> None:
         check(lib().fhe_ctx_set_pipelining(self.h, 1 if on else 0))

@@ -40,7 +40,8 @@ extern "C" int fhe_autotune(fhe_ctx *c, int level, int n_items, int flags, fhe_t
   if (!c || !out) return fhe_fail(FHE_EINVAL, "fhe_autotune: null argument");
   if (level < 1 || level > c->L) return fhe_fail(FHE_ELEVEL, "fhe_autotune: level %d", level);
   if (n_items < 1 || n_items > 64) return fhe_fail(FHE_EINVAL, "fhe_autotune: n_items %d (1..64)", n_items);
-  if (flags & ~(FHE_TUNE_BCONV | FHE_TUNE_NTT)) return fhe_fail(FHE_EINVAL, "fhe_autotune: flags %d", flags);
+  if (flags & ~(FHE_TUNE_BCONV | FHE_TUNE_NTT | FHE_TUNE_SHAPE))
+    return fhe_fail(FHE_EINVAL, "fhe_autotune: flags %d", flags);
   cudaSetDevice(c->device);
   cudaStream_t s = (cudaStream_t)stream;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -104,6 +105,8 @@ extern "C" int fhe_autotune(fhe_ctx *c, int level, int n_items, int flags, fhe_t
   const int saved_ip = c->tabs.ip_ctas_per_sm, saved_comp = c->comp_pipe;
   const int saved_ntt = (c->tabs.ntt_otf ? FHE_NTT_OTF : 0) | (c->tabs.ntt_single ? FHE_NTT_SINGLE_PASS : 0) |
                         (c->tabs.ntt_stream ? FHE_NTT_STREAM : 0);
+  fhe_kernel_shape saved_shape;
+  fhe_ctx_get_kernel_shape(c, &saved_shape);
   fhe_tune_result by_ip[2];  // fastest schedule with one / two inner-product CTAs per SM
   memset(by_ip, 0, sizeof by_ip);
   by_ip[0].us_per_ks = by_ip[1].us_per_ks = 1e30;
@@ -174,6 +177,7 @@ extern "C" int fhe_autotune(fhe_ctx *c, int level, int n_items, int flags, fhe_t
     best.default_us_per_ks = dflt;
   }
   best.ntt_mode = saved_ntt;
+  best.shape = saved_shape;
   // the NTT variants under the chosen schedule: another mode only when it is faster by more
   // than the timing noise (1 %)
   if (rc == FHE_OK && tried > 0 && (flags & FHE_TUNE_NTT)) {
@@ -204,6 +208,70 @@ extern "C" int fhe_autotune(fhe_ctx *c, int level, int n_items, int flags, fhe_t
     }
     fhe_ctx_set_ntt(c, saved_ntt);
   }
+  // kernel shapes under the chosen schedule and NTT mode, one parameter at a time: another
+  // value only when it is faster by more than the timing noise (1 %)
+  if (rc == FHE_OK && tried > 0 && (flags & FHE_TUNE_SHAPE)) {
+    c->batch_budget = best.l2_budget_bytes;
+    c->batch_lanes = best.lanes;
+    c->batch_max_group = best.max_group;
+    c->bconv_mode = best.bconv_mode;
+    c->tabs.ip_ctas_per_sm = best.ip_ctas_per_sm;
+    c->comp_pipe = best.comp_pipe;
+    fhe_ctx_set_ntt(c, best.ntt_mode);
+    fhe_kernel_shape cur = saved_shape;
+    double cur_us = best.us_per_ks;
+    auto try_shape = [&](const fhe_kernel_shape &cand) {
+      if (rc != FHE_OK || memcmp(&cand, &cur, sizeof cand) == 0) return;
+      if (fhe_ctx_set_kernel_shape(c, &cand) != FHE_OK) return;  // not available here: skip
+      fhe_plan *p = nullptr;
+      rc = fhe_batch_plan(c, items.data(), n_items, FHE_PLAN_GRAPH, &p);
+      if (rc != FHE_OK) return;
+      const int ng = fhe_plan_groups(p, nullptr, 0);
+      double us = 0;
+      rc = measure(p, us);
+      fhe_plan_destroy(p);
+      if (rc != FHE_OK) return;
+      tried++;
+      if (us < 0.99 * cur_us) {
+        cur_us = us;
+        cur = cand;
+        best.n_groups = ng;
+      }
+    };
+    for (int f = 0; f <= 1; f++) {
+      fhe_kernel_shape k = cur;
+      k.fuse_ip_moddown = f;
+      try_shape(k);
+    }
+    if (best.bconv_mode == FHE_BCONV_TC) {
+      for (int pl = 0; pl <= 1; pl++) {
+        fhe_kernel_shape k = cur;
+        k.bconv_tc_pipeline = pl;
+        try_shape(k);
+      }
+      for (int n : {2, 3, 4}) {
+        fhe_kernel_shape k = cur;
+        k.bconv_tc_ctas = n;
+        try_shape(k);
+      }
+    }
+    if (best.ntt_mode & FHE_NTT_STREAM) {
+      for (int st : {2, 3}) {
+        fhe_kernel_shape k = cur;
+        k.ntt_stream_stages = st;
+        try_shape(k);
+      }
+      for (int n : {2, 3}) {
+        fhe_kernel_shape k = cur;
+        k.ntt_stream_ctas = n;
+        try_shape(k);
+      }
+    }
+    best.shape = cur;
+    best.us_per_ks = cur_us;
+    fhe_ctx_set_kernel_shape(c, &saved_shape);
+    fhe_ctx_set_ntt(c, saved_ntt);
+  }
   if (rc == FHE_OK) rc = fhe_ctx_sync(c);  // an expired bounded device wait voids the timings
   if (rc == FHE_OK && tried > 0) {
     best.candidates = tried;
@@ -214,6 +282,7 @@ extern "C" int fhe_autotune(fhe_ctx *c, int level, int n_items, int flags, fhe_t
     c->tabs.ip_ctas_per_sm = best.ip_ctas_per_sm;
     c->comp_pipe = best.comp_pipe;
     fhe_ctx_set_ntt(c, best.ntt_mode);
+    fhe_ctx_set_kernel_shape(c, &best.shape);
     *out = best;
   } else {
     c->tabs.ip_ctas_per_sm = saved_ip;
@@ -223,6 +292,7 @@ extern "C" int fhe_autotune(fhe_ctx *c, int level, int n_items, int flags, fhe_t
     c->batch_lanes = saved_lanes;
     c->batch_max_group = saved_group;
     c->bconv_mode = saved_mode;
+    fhe_ctx_set_kernel_shape(c, &saved_shape);
   }
   release();
   return rc;
@@ -244,12 +314,26 @@ static std::string tune_key(const fhe_ctx *c, int level, int n_items, int flags)
   return buf;
 }
 
-static bool tune_parse(const char *rest, fhe_tune_result *r) {
+static bool tune_parse(const char *rest, const fhe_kernel_shape &dflt, fhe_tune_result *r) {
   fhe_tune_result t;
   memset(&t, 0, sizeof t);
   unsigned long long budget = 0;
-  if (sscanf(rest, " lanes=%d budget=%llu group=%d bconv=%d ip=%d comp=%d ntt=%d us=%lf", &t.lanes, &budget,
-             &t.max_group, &t.bconv_mode, &t.ip_ctas_per_sm, &t.comp_pipe, &t.ntt_mode, &t.us_per_ks) != 8)
+  fhe_kernel_shape &k = t.shape;
+  // entries with the kernel shape, and older ones without it (the context's shape then)
+  if (sscanf(rest,
+             " lanes=%d budget=%llu group=%d bconv=%d ip=%d comp=%d ntt=%d fuse=%d tcctas=%d tcpipe=%d nst=%d nsc=%d "
+             "us=%lf",
+             &t.lanes, &budget, &t.max_group, &t.bconv_mode, &t.ip_ctas_per_sm, &t.comp_pipe, &t.ntt_mode,
+             &k.fuse_ip_moddown, &k.bconv_tc_ctas, &k.bconv_tc_pipeline, &k.ntt_stream_stages, &k.ntt_stream_ctas,
+             &t.us_per_ks) != 13) {
+    k = dflt;
+    if (sscanf(rest, " lanes=%d budget=%llu group=%d bconv=%d ip=%d comp=%d ntt=%d us=%lf", &t.lanes, &budget,
+               &t.max_group, &t.bconv_mode, &t.ip_ctas_per_sm, &t.comp_pipe, &t.ntt_mode, &t.us_per_ks) != 8)
+      return false;
+  }
+  if (k.fuse_ip_moddown < 0 || k.fuse_ip_moddown > 1 || k.bconv_tc_ctas < 1 || k.bconv_tc_ctas > 4 ||
+      k.ntt_stream_stages < 2 || k.ntt_stream_stages > 3 || k.ntt_stream_ctas < 1 || k.ntt_stream_ctas > 3 ||
+      k.bconv_tc_pipeline < 0 || k.bconv_tc_pipeline > 1)
     return false;
   if (t.comp_pipe != 0 && t.comp_pipe != 1) return false;
   if (t.ntt_mode & ~(FHE_NTT_OTF | FHE_NTT_SINGLE_PASS | FHE_NTT_STREAM)) return false;
@@ -274,7 +358,9 @@ extern "C" int fhe_autotune_cached(fhe_ctx *c, const char *path, int level, int 
       const char *bar = strchr(line, '|');
       if (!bar || (size_t)(bar - line) != key.size() + 1 || strncmp(line, key.c_str(), key.size()) != 0) continue;
       fhe_tune_result r;
-      if (tune_parse(bar + 1, &r)) {
+      fhe_kernel_shape dflt;
+      fhe_ctx_get_kernel_shape(c, &dflt);
+      if (tune_parse(bar + 1, dflt, &r)) {
         hit = r;
         found = true;
       }
@@ -291,6 +377,7 @@ extern "C" int fhe_autotune_cached(fhe_ctx *c, const char *path, int level, int 
     c->tabs.ip_ctas_per_sm = hit.ip_ctas_per_sm;
     c->comp_pipe = hit.comp_pipe;
     if (fhe_ctx_set_ntt(c, hit.ntt_mode) != FHE_OK) hit.ntt_mode = 0, fhe_ctx_set_ntt(c, 0);
+    if (fhe_ctx_set_kernel_shape(c, &hit.shape) != FHE_OK) fhe_ctx_get_kernel_shape(c, &hit.shape);
     hit.candidates = 0;  // served from the cache
     *out = hit;
     return FHE_OK;
@@ -299,9 +386,12 @@ extern "C" int fhe_autotune_cached(fhe_ctx *c, const char *path, int level, int 
   if (rc != FHE_OK) return rc;
   char line[1024];
   const int len = snprintf(line, sizeof line,
-                           "%s | lanes=%d budget=%llu group=%d bconv=%d ip=%d comp=%d ntt=%d us=%.3f\n", key.c_str(),
-                           out->lanes, (unsigned long long)out->l2_budget_bytes, out->max_group, out->bconv_mode,
-                           out->ip_ctas_per_sm, out->comp_pipe, out->ntt_mode, out->us_per_ks);
+                           "%s | lanes=%d budget=%llu group=%d bconv=%d ip=%d comp=%d ntt=%d fuse=%d tcctas=%d "
+                           "tcpipe=%d nst=%d nsc=%d us=%.3f\n",
+                           key.c_str(), out->lanes, (unsigned long long)out->l2_budget_bytes, out->max_group,
+                           out->bconv_mode, out->ip_ctas_per_sm, out->comp_pipe, out->ntt_mode,
+                           out->shape.fuse_ip_moddown, out->shape.bconv_tc_ctas, out->shape.bconv_tc_pipeline,
+                           out->shape.ntt_stream_stages, out->shape.ntt_stream_ctas, out->us_per_ks);
   FILE *f = fopen(path, "a");
   if (!f) return fhe_fail(FHE_EINVAL, "fhe_autotune_cached: cannot append to %s", path);
   const bool ok = fwrite(line, 1, (size_t)len, f) == (size_t)len;  // one write per entry

@@ -267,6 +267,208 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_bconv_tc(const __grid_constan
   }
 }
 
+// Pipelined form (kernel shape bconv_tc_pipeline): two A buffers and two accumulators per
+// CTA, so that tile t's MMA runs while the CTA reduces tile t - 1's accumulator.  Per
+// iteration: build A(t) (inputs prefetched one tile ahead), one barrier, thread 0 issues
+// MMA(t) into accumulator t & 1 and commits to mbarrier t & 1, every thread then waits
+// (bounded) for MMA(t - 1) and runs its epilogue, one barrier (which also carries the
+// CTA-wide verdict of the waits).  A group change first drains the pending epilogue.  The
+// arithmetic is the unpipelined kernel's exactly.  Tensor memory: 2 x ncols per CTA, so at
+// most two CTAs per SM for outputs of more than 16 limbs.
+template <int KT>
+__global__ void __launch_bounds__(kTcThreads, 2) k_bconv_tc_pipe(const __grid_constant__ BconvArgs a, const PrimeC *pc,
+                                                              int logn, unsigned int *status, int npad_max,
+                                                              int tiles_per_group) {
+  static_assert(KT == kTcK || KT == kTcK12, "K is 48 or 64");
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  constexpr uint32_t kRowBytes = KT * 2;
+  constexpr uint32_t kSbo = (KT / 8) * 128u;
+  constexpr int kDataChunks = KT == kTcK ? 4 : 6;
+  constexpr int kNch = kDataChunks / 2;
+  constexpr uint32_t kBigPrime = KT == kTcK ? (1u << 30) : (1u << 30) + (1u << 23);
+  constexpr uint32_t kAbytes = kTcM * kRowBytes;
+  uint8_t *sA = smem;  // two buffers
+  uint8_t *sB = smem + 2 * kAbytes;
+  TcOut *sO = reinterpret_cast<TcOut *>(sB + (size_t)npad_max * kRowBytes);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sO + 64);  // two
+  uint32_t *s_taddr = reinterpret_cast<uint32_t *>(bar + 2);
+  const uint32_t ncols = npad_max <= 32 ? 32u : npad_max <= 64 ? 64u : npad_max <= 128 ? 128u : 256u;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(s_taddr)),
+                 "r"(2 * ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+  }
+  if (tid < kTcM)  // the constant K chunks of both A buffers
+    for (int b = 0; b < 2; b++) {
+      uint8_t *row = sA + b * kAbytes + (tid >> 3) * kSbo + (tid & 7) * 16;
+      if (KT == kTcK)
+        *reinterpret_cast<uint4 *>(row + kDataChunks * 128) = make_uint4(0x64006400u, 0x64006400u, 0u, 0u);
+      else
+        *reinterpret_cast<uint4 *>(row + kDataChunks * 128) =
+            make_uint4(0x64006400u, 0x64006400u, 0x64006400u, 0x64006400u);
+      *reinterpret_cast<uint4 *>(row + (kDataChunks + 1) * 128) = make_uint4(0u, 0u, 0u, 0u);
+    }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr0 = *s_taddr;
+
+  const size_t N = (size_t)1 << logn;
+  const int total = tiles_per_group * a.ngroups;
+  const int per_cta = (total + gridDim.x - 1) / gridDim.x;
+  const int t0 = blockIdx.x * per_cta, t1 = min(total, t0 + per_cta);
+  int cur_group = -1, n_in = 0, n_out = 0;
+  const BconvGroup *gp = nullptr;
+  uint32_t ph = 0u;  // bit b: the phase the next wait on bar[b] expects
+  bool ok = true;
+  const int r = tid & (kTcM - 1);
+  const int kc0 = tid >> 7;
+  uint32_t y[2 * kNch];
+  auto load_inputs = [&](const BconvGroup *g, int nin, size_t m0) {
+#pragma unroll
+    for (int h = 0; h < 2 * kNch; h++) {
+      const int j = 2 * (kc0 + 2 * (h >> 1)) + (h & 1);
+      y[h] = j < nin ? __ldg(g->in + (size_t)j * N + m0 + r) : 0u;
+    }
+  };
+#pragma unroll
+  for (int h = 0; h < 2 * kNch; h++) y[h] = 0u;
+  bool prefetched = false;
+  bool big_primes = true;
+  uint32_t *gout = nullptr;
+  int pending = -1;  // tile whose MMA is in flight and whose epilogue has not run
+  // epilogue of tile p (accumulator p & 1): the unpipelined kernel's
+  auto epilogue = [&](int p) {
+    const int b = p & 1;
+    const bool w = mbar_wait_bounded(&bar[b], (ph >> b) & 1u);
+    ph ^= 1u << b;
+    if (!__all_sync(0xffffffffu, w)) {
+      ok = false;
+      if ((tid & 31) == 0) atomicOr(status, 1u);
+      return;
+    }
+    tc_fence_after();
+    const size_t n0 = (size_t)(p % tiles_per_group) * kTcM;
+    const int q4 = warp & 3;
+    const uint32_t n = (uint32_t)(n0 + (size_t)q4 * 32 + (tid & 31));
+    const uint32_t tbase = taddr0 + (uint32_t)b * ncols + ((uint32_t)(q4 * 32) << 16);
+    const int H = ((n_out + 1) / 2 + 3) & ~3;
+    const int o_end = (warp >> 2) ? n_out : min(H, n_out);
+    for (int o0 = (warp >> 2) ? H : 0; o0 < o_end; o0 += 8) {
+      uint32_t rr[32];
+      tmem_ld16(rr, tbase + (uint32_t)(4 * o0));
+      if (o0 + 4 < o_end) tmem_ld16(rr + 16, tbase + (uint32_t)(4 * (o0 + 4)));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      const int cnt = min(8, o_end - o0);
+#pragma unroll
+      for (int i = 0; i < 8; i++) {
+        if (i < cnt) {
+          const TcOut t = sO[o0 + i];
+          const uint32_t lo = rr[4 * i + 1] * 256u + rr[4 * i] - 0x4B000000u;
+          const uint32_t hi = rr[4 * i + 3] * 256u + rr[4 * i + 2] - 0x4B000000u;
+          const uint32_t sum = lo + red2(shoup_lazy(hi, 65536u, t.w16s, t.q), t.q);
+          const uint32_t v = big_primes ? red2(sum, t.q) : red2(shoup_lazy(sum, 1u, t.div32, t.q), t.q);
+          gout[t.off + n] = v;
+        }
+      }
+    }
+  };
+  for (int tile = t0; tile < t1 && ok; tile++) {
+    const int grp = tile / tiles_per_group;
+    const size_t n0 = (size_t)(tile % tiles_per_group) * kTcM;
+    if (grp != cur_group) {
+      if (pending >= 0) {  // drain: the table and output constants are about to change
+        epilogue(pending);
+        pending = -1;
+        tc_fence_before();
+        ok = __syncthreads_and(ok ? 1 : 0) != 0;
+        if (!ok) break;
+      }
+      cur_group = grp;
+      gp = a.dev ? &a.dev[grp] : &a.g[grp];
+      n_in = gp->n_in;
+      n_out = gp->n_out;
+      const uint4 *src = reinterpret_cast<const uint4 *>(gp->Btc);
+      uint4 *dst = reinterpret_cast<uint4 *>(sB);
+      const int n16 = gp->npad * (int)kRowBytes / 16;
+      for (int i = tid; i < n16; i += kTcThreads) dst[i] = __ldg(src + i);
+      bool big = true;
+      for (int o = tid; o < n_out; o += kTcThreads) {
+        const int2 m = gp->omap[o];
+        const PrimeC pr = pc[m.y];
+        TcOut t;
+        t.q = pr.q;
+        t.w16s = (uint32_t)(((uint64_t)65536u << 32) / pr.q);
+        t.div32 = pr.div32;
+        t.off = (uint32_t)m.x << logn;
+        sO[o] = t;
+        big = big && pr.q > kBigPrime;
+      }
+      big_primes = __syncthreads_and(big ? 1 : 0) != 0;
+      gout = gp->out;
+    }
+    uint8_t *Ab = sA + (tile & 1) * kAbytes;
+    {
+      if (!prefetched) load_inputs(gp, n_in, n0);
+      uint8_t *row = Ab + (r >> 3) * kSbo + (r & 7) * 16;
+#pragma unroll
+      for (int i = 0; i < kNch; i++) {
+        const uint32_t y0 = y[2 * i], y1 = y[2 * i + 1];
+        *reinterpret_cast<uint4 *>(row + (kc0 + 2 * i) * 128) =
+            make_uint4(__byte_perm(y0, 0x64006400u, 0x7150), __byte_perm(y0, 0x64006400u, 0x7352),
+                       __byte_perm(y1, 0x64006400u, 0x7150), __byte_perm(y1, 0x64006400u, 0x7352));
+      }
+    }
+    prefetched = tile + 1 < t1 && (tile + 1) / tiles_per_group == grp;
+    if (prefetched) load_inputs(gp, n_in, (size_t)((tile + 1) % tiles_per_group) * kTcM);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+      const uint32_t aaddr = smem_addr(Ab), baddr = smem_addr(sB);
+      const uint32_t idesc = idesc_f16(kTcM, gp->npad);
+      const uint32_t tacc = taddr0 + (uint32_t)(tile & 1) * ncols;
+#pragma unroll
+      for (int kk = 0; kk < KT / 16; kk++) {
+        const uint64_t ad = smem_desc(aaddr + kk * 256u, 128u, kSbo);
+        const uint64_t bd = smem_desc(baddr + kk * 256u, 128u, kSbo);
+        const uint32_t acc = kk > 0 ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tacc),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_addr(&bar[tile & 1]))
+                   : "memory");
+    }
+    if (pending >= 0) epilogue(pending);
+    pending = tile;
+    tc_fence_before();
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;  // A and the accumulator of tile - 1 are free
+  }
+  if (ok && pending >= 0) epilogue(pending);
+  if (!ok) {  // give the MMAs in flight a second bounded chance before the memory goes away
+    mbar_wait_bounded(&bar[0], ph & 1u);
+    mbar_wait_bounded(&bar[1], (ph >> 1) & 1u);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr0), "r"(2 * ncols) : "memory");
+  }
+}
+
 template <int KT>
 static cudaError_t bconv_tc_go(const DevTables &t, const BconvArgs &a, int max_out, cudaStream_t s) {
   const int npad = tc_npad(max_out);
@@ -274,7 +476,8 @@ static cudaError_t bconv_tc_go(const DevTables &t, const BconvArgs &a, int max_o
   // operands, output constants, barrier; at least enough shared memory that no
   // more CTAs fit on an SM than its 512 tensor-memory columns hold
   const int need = kTcM * KT * 2 + npad * KT * 2 + 64 * (int)sizeof(TcOut) + 64;
-  const int per_sm = std::min(512 / ncols, 2048 / kTcThreads);
+  // resident CTAs per SM: what the 512 tensor-memory columns hold, capped by the context's shape
+  const int per_sm = std::max(1, std::min(std::min(512 / ncols, 2048 / kTcThreads), t.bconv_tc_ctas));
   int smem = std::max(need, 233472 / (per_sm + 1) + 1024);  // 228 KB of shared memory per SM
   if (smem > 232448) smem = 232448;
   static PerDeviceOnce configured;
@@ -286,9 +489,23 @@ static cudaError_t bconv_tc_go(const DevTables &t, const BconvArgs &a, int max_o
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int tiles_per_group = (int)((1u << t.logn) / kTcM);
   const int total = tiles_per_group * a.ngroups;
-  const int grid = std::min(total, std::max(1, sms * per_sm));
   TraceScope ts(t, "bconv_tc", s);
-  k_bconv_tc<KT><<<grid, kTcThreads, smem, s>>>(a, t.pc, t.logn, t.status, npad, tiles_per_group);
+  if (t.bconv_tc_pipe) {
+    // two accumulators per CTA: what the 512 tensor-memory columns hold, within the shape's cap
+    const int per_sm2 = std::max(1, std::min(std::min(256 / ncols, 2048 / kTcThreads), t.bconv_tc_ctas));
+    const int need2 = 2 * kTcM * KT * 2 + npad * KT * 2 + 64 * (int)sizeof(TcOut) + 64;
+    int smem2 = std::max(need2, 233472 / (per_sm2 + 1) + 1024);
+    if (smem2 > 232448) smem2 = 232448;
+    static PerDeviceOnce configured2;
+    const cudaError_t ce2 = configured2.run(
+        [] { return cudaFuncSetAttribute(k_bconv_tc_pipe<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448); });
+    if (ce2 != cudaSuccess) return ce2;
+    const int grid2 = std::min(total, std::max(1, sms * per_sm2));
+    k_bconv_tc_pipe<KT><<<grid2, kTcThreads, smem2, s>>>(a, t.pc, t.logn, t.status, npad, tiles_per_group);
+  } else {
+    const int grid = std::min(total, std::max(1, sms * per_sm));
+    k_bconv_tc<KT><<<grid, kTcThreads, smem, s>>>(a, t.pc, t.logn, t.status, npad, tiles_per_group);
+  }
   note_launch();
   return cudaGetLastError();
 }

@@ -264,6 +264,9 @@ static int build_tables(fhe_ctx *c) {
   c->tabs.ntt_single = 0;
   c->tabs.ntt_stream = 0;
   c->tabs.ntt_stream_stages = 3;
+  c->tabs.ntt_stream_ctas = 3;
+  c->tabs.bconv_tc_ctas = 4;
+  c->tabs.bconv_tc_pipe = 0;
   c->tabs.status = c->d_status;
   return FHE_OK;
 }
@@ -536,6 +539,34 @@ extern "C" int fhe_ctx_set_ntt(fhe_ctx *c, int flags) {
   c->tabs.ntt_otf = (flags & FHE_NTT_OTF) ? 1 : 0;
   c->tabs.ntt_single = (flags & FHE_NTT_SINGLE_PASS) ? 1 : 0;
   c->tabs.ntt_stream = (flags & FHE_NTT_STREAM) ? 1 : 0;
+  return FHE_OK;
+}
+
+extern "C" int fhe_ctx_set_kernel_shape(fhe_ctx *c, const fhe_kernel_shape *sh) {
+  if (!c || !sh) return fhe_fail(FHE_EINVAL, "fhe_ctx_set_kernel_shape: null");
+  if ((sh->fuse_ip_moddown != 0 && sh->fuse_ip_moddown != 1) || sh->bconv_tc_ctas < 1 || sh->bconv_tc_ctas > 4 ||
+      sh->ntt_stream_stages < 2 || sh->ntt_stream_stages > 3 || sh->ntt_stream_ctas < 1 || sh->ntt_stream_ctas > 3 ||
+      (sh->bconv_tc_pipeline != 0 && sh->bconv_tc_pipeline != 1))
+    return fhe_fail(FHE_EINVAL, "fhe_ctx_set_kernel_shape: fuse %d (0, 1), bconv_tc_ctas %d (1..4), stages %d (2..3), "
+                    "stream ctas %d (1..3), pipeline %d (0, 1)", sh->fuse_ip_moddown, sh->bconv_tc_ctas,
+                    sh->ntt_stream_stages, sh->ntt_stream_ctas, sh->bconv_tc_pipeline);
+  if (sh->fuse_ip_moddown && c->logn != 16)
+    return fhe_fail(FHE_EUNSUPPORTED, "fhe_ctx_set_kernel_shape: the fused inner product needs N = 2^16");
+  c->fuse_ip_md = sh->fuse_ip_moddown;
+  c->tabs.bconv_tc_ctas = sh->bconv_tc_ctas;
+  c->tabs.ntt_stream_stages = sh->ntt_stream_stages;
+  c->tabs.ntt_stream_ctas = sh->ntt_stream_ctas;
+  c->tabs.bconv_tc_pipe = sh->bconv_tc_pipeline;
+  return FHE_OK;
+}
+
+extern "C" int fhe_ctx_get_kernel_shape(const fhe_ctx *c, fhe_kernel_shape *out) {
+  if (!c || !out) return fhe_fail(FHE_EINVAL, "fhe_ctx_get_kernel_shape: null");
+  out->fuse_ip_moddown = c->fuse_ip_md;
+  out->bconv_tc_ctas = c->tabs.bconv_tc_ctas;
+  out->ntt_stream_stages = c->tabs.ntt_stream_stages;
+  out->ntt_stream_ctas = c->tabs.ntt_stream_ctas;
+  out->bconv_tc_pipeline = c->tabs.bconv_tc_pipe;
   return FHE_OK;
 }
 

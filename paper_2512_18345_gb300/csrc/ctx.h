@@ -17,6 +17,7 @@ struct fhe_ctx {
   int bconv_mode = 0;  // FHE_BCONV_SCALAR / FHE_BCONV_TC
   int fused = 1;
   int comp_pipe = 1;  // complementary pipelining of the inner product (autotuned)
+  int fuse_ip_md = 0; // special limbs' inner product fused with ModDown's first INTT pass (autotuned)
   size_t batch_budget = 0;  // L2 bytes per batched group (0: 3/4 of the L2 size)
   int batch_max_group = 0;  // items per batched group (0: 8)
 

@@ -63,6 +63,9 @@ struct DevTables {
   int ntt_single;          // 2^16-point transforms in one cluster launch instead of two passes
   int ntt_stream;          // the passes as persistent kernels fed by a producer warp (ntt_bulk.cuh)
   int ntt_stream_stages;   // shared-memory stages per CTA of those kernels
+  int ntt_stream_ctas;     // persistent CTAs per SM of those kernels (1..3)
+  int bconv_tc_ctas;       // resident CTAs per SM of the tensor-core BConv (1..4)
+  int bconv_tc_pipe;       // the tensor-core BConv with two accumulators per CTA (MMA beside epilogue)
   int tc_k;                // K of the context's tensor-core BConv tables (48 or 64; 0: none)
 };
 
@@ -105,6 +108,9 @@ cudaError_t launch_ew(const DevTables &t, int op, const SegList &sl, cudaStream_
 // beta_max: the largest digit count among the segments' items (sizes the stages)
 cudaError_t launch_ip(const DevTables &t, const SegList &sl, bool gather_own, bool gather_ext, int beta_max,
                       cudaStream_t s);
+// the special limbs' inner product fused with ModDown's first inverse-NTT pass (ip_intt.cuh);
+// sl: one segment per item over its K special limbs, dst = the item's UC [2][K][N]
+cudaError_t launch_ip_intt(const DevTables &t, const SegList &sl, int beta_max, cudaStream_t s);
 
 // number of kernels launched since the counter was last read (for the benchmark's launch count)
 long long kernel_launches();

@@ -9,6 +9,7 @@
 #include "internal.h"
 #include "ntt.cuh"
 #include "ntt_bulk.cuh"
+#include "ip_intt.cuh"
 
 namespace fhe {
 
@@ -83,7 +84,7 @@ static cudaError_t ntt_bulk_go(const DevTables &t, const SegList &sl, cudaStream
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = std::min(units, 3 * sms);
+  const int grid = std::min(units, std::max(1, std::min(3, t.ntt_stream_ctas)) * sms);
   static const char *names[2][2] = {{"intt_blk", "ntt_blk"}, {"intt_col", "ntt_col"}};
   const char *name = EPI == EPI_COMBINE ? "ntt_blk+combine" : EPI == EPI_SCALE ? "intt_col+scale"
                      : EPI == EPI_PLAIN ? "ntt_blk" : names[COLUMN][FWD];
@@ -302,6 +303,21 @@ cudaError_t launch_ew(const DevTables &t, int op, const SegList &sl, cudaStream_
     case EW_COPY: k_ew<EW_COPY><<<grid, kEwThreads, 0, s>>>(sl, t.pc, t.logn); break;
     case EW_TENSOR: k_ew<EW_TENSOR><<<grid, kEwThreads, 0, s>>>(sl, t.pc, t.logn); break;
     default: return cudaErrorInvalidValue;
+  }
+  g_launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ip_intt(const DevTables &t, const SegList &sl, int beta_max, cudaStream_t s) {
+  if (sl.total == 0) return cudaSuccess;
+  if (t.logn != 16 || beta_max < 1 || beta_max > 4) return cudaErrorInvalidValue;
+  TraceScope ts(t, "ip+intt_blk", s);
+  const unsigned grid = (unsigned)sl.total * 32u;  // 16 tiles x 2 halves per special limb
+  switch (beta_max) {
+    case 1: k_ip_intt<1><<<grid, kIpIttThreads, 0, s>>>(sl, t.ntt); break;
+    case 2: k_ip_intt<2><<<grid, kIpIttThreads, 0, s>>>(sl, t.ntt); break;
+    case 3: k_ip_intt<3><<<grid, kIpIttThreads, 0, s>>>(sl, t.ntt); break;
+    default: k_ip_intt<4><<<grid, kIpIttThreads, 0, s>>>(sl, t.ntt); break;
   }
   g_launches++;
   return cudaGetLastError();

@@ -210,6 +210,8 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
   Stage ipq;
   ipq.kind = Stage::IP;
   Stage ipp = ipq;
+  Stage ipn;  // fused special-limb inner product + first inverse pass (items with plain digits)
+  ipn.kind = Stage::IPN;
   Stage m1 = ntt_stage(false, false, PRO_PLAIN, EPI_LAZY);
   Stage m2 = ntt_stage(true, false, PRO_PLAIN, EPI_SCALE);
   Stage msc = ew_stage(EW_SCALE);
@@ -225,6 +227,15 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
     const KsArgs &k = P.ks[i];
     // u: the slot's workspace, the caller's extended-basis output (IPX) or input (MDX)
     uint32_t *U = it.kind == IT_IPX ? it.out : it.kind == IT_MDX ? const_cast<uint32_t *>(it.in) : S.U;
+    // the fused kernel takes the special limbs of a key switch whose digits are read directly
+    const bool fuse = fused && c->fuse_ip_md && c->logn == 16 && has_ip(it) && has_moddown(it) &&
+                      k.galois_ext == 1u && c->beta(level) <= 4;
+    if (fuse) {
+      Seg f = seg(nullptr, S.UC, K, L, (int)i);
+      f.t0 = level;
+      f.key_row0 = L;
+      add(ipn, f);
+    }
     if (has_ip(it)) {
       ipq.gather_own |= k.galois_own != 1u;
       ipq.gather_ext |= k.galois_ext != 1u;
@@ -232,16 +243,18 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
       a.t0 = 0;
       a.key_row0 = 0;
       add(ipq, a);
-      Seg b = seg(nullptr, U + (size_t)level * N, K, L, (int)i);
-      b.t0 = level;
-      b.key_row0 = L;
-      add(ipp, b);
+      if (!fuse) {
+        Seg b = seg(nullptr, U + (size_t)level * N, K, L, (int)i);
+        b.t0 = level;
+        b.key_row0 = L;
+        add(ipp, b);
+      }
     }
     if (!has_moddown(it)) continue;
     const int npoly = it.kind == IT_MDX ? it.npoly : 2;
     for (int cc = 0; cc < npoly; cc++) {
       uint32_t *uc = S.UC + (size_t)cc * K * N, *r = S.R + (size_t)cc * level * N;
-      add(m1, seg(U + ((size_t)cc * n_ext + level) * N, uc, K, L, (int)i));
+      if (!fuse) add(m1, seg(U + ((size_t)cc * n_ext + level) * N, uc, K, L, (int)i));
       Seg x = seg(uc, uc, K, L, (int)i);
       if (fused) x.scale = c->d_md_scale;
       add(m2, x);
@@ -276,7 +289,7 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
   ipp.gather_ext = ipq.gather_ext;
   // complementary pipelining (Section IV-B): the q-limb inner product on an auxiliary
   // branch beside ModDown's special-limb chain; otherwise one launch over all limbs
-  const bool has_md = !m1.segs.empty();
+  const bool has_md = !m2.segs.empty();
   const bool split = fused && c->comp_pipe && has_md && !ipq.segs.empty();
   if (!ipq.segs.empty()) {
     if (split) {
@@ -284,7 +297,7 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
       ipq.aux = true;
       P.stages.push_back(ipq);
       P.stages.push_back(marker(Stage::JOIN_RECORD));
-      P.stages.push_back(ipp);
+      if (!ipp.segs.empty()) P.stages.push_back(ipp);
     } else {
       Stage all = ipq;
       all.segs.insert(all.segs.end(), ipp.segs.begin(), ipp.segs.end());
@@ -292,7 +305,15 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
     }
   }
   if (has_md) {
-    push_transform(c, P, m1, m2);
+    if (!ipn.segs.empty()) {
+      // the fused stage replaces the first inverse pass of its items: the other items' first
+      // pass, then one column pass over every item's special limbs
+      P.stages.push_back(ipn);
+      if (!m1.segs.empty()) P.stages.push_back(m1);
+      P.stages.push_back(m2);
+    } else {
+      push_transform(c, P, m1, m2);
+    }
     if (!fused) P.stages.push_back(msc);
     P.stages.push_back(mbc);
     if (c->tabs.ntt_single && fhe::ntt_single_pass_ok(c->tabs, r1.pro, r2.epi, true)) {
@@ -327,6 +348,7 @@ static cudaError_t launch_stage(fhe_ctx *c, const Stage &st, const SegList &sl, 
     case Stage::NTT1: return launch_ntt_single(c->tabs, st.fwd, st.pro, st.epi, sl, *sl2, q);
     case Stage::EW: return launch_ew(c->tabs, st.ewop, sl, q);
     case Stage::IP: return launch_ip(c->tabs, sl, st.gather_own, st.gather_ext, c->dnum, q);
+    case Stage::IPN: return launch_ip_intt(c->tabs, sl, std::min(c->dnum, 4), q);
     case Stage::BCONV:
       return c->bconv_mode == FHE_BCONV_TC ? launch_bconv_tc(c->tabs, ba, st.max_in, st.max_out, q, c->tabs.tc_k)
                                            : launch_bconv(c->tabs, ba, st.max_in, st.max_out, q);

@@ -31,7 +31,8 @@ struct Item {
 struct Stage {
   // NTT1: both passes of a transform in one cluster launch (segs: the first pass's limbs
   // and prologue; segs2: the same limbs with the second pass's destination and epilogue)
-  enum Kind { NTT, BCONV, IP, EW, FORK, JOIN_RECORD, JOIN_WAIT, NTT1 } kind = NTT;
+  // IPN: the special limbs' inner product fused with ModDown's first inverse-NTT pass
+  enum Kind { NTT, BCONV, IP, EW, FORK, JOIN_RECORD, JOIN_WAIT, NTT1, IPN } kind = NTT;
   bool column = false, fwd = false;
   int pro = 0, epi = 0, ewop = 0;
   bool aux = false;

@@ -75,7 +75,7 @@ def test_autotune_full_size_keeps_the_relin_key(fhe_lib):
 
 @pytest.mark.parametrize("level,n_items,flags,code", [(0, 4, 0, "FHE_ELEVEL"), (5, 4, 0, "FHE_ELEVEL"),
                                                       (4, 0, 0, "FHE_EINVAL"), (4, 65, 0, "FHE_EINVAL"),
-                                                      (4, 4, 6, "FHE_EINVAL")])
+                                                      (4, 4, 8, "FHE_EINVAL")])
 def test_autotune_rejects_bad_arguments(fhe_lib, level, n_items, flags, code):
     from paper_2512_18345_gb300 import binding
     P = inputs.workload_params("hmult_relin_rescale_N4096_L4")
