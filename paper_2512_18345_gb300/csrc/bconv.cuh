@@ -41,6 +41,7 @@ __host__ __device__ constexpr int tc_npad(int n_out) { return (4 * n_out + 15) /
 constexpr int kMaxBconvGroups = 48;
 struct BconvArgs {
   int ngroups;
+  int lazy;               // outputs may be left in [0, 2p) (they feed a forward NTT); else reduced
   const BconvGroup *dev;  // device array (batched plans), else g[]
   BconvGroup g[kMaxBconvGroups];
 };

@@ -75,9 +75,46 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 
 constexpr int kTcThreads = 256;  // 8 warps: warps w and w + 4 share accumulator lanes 32 (w % 4)..
 
-struct TcOut {  // per output prime of the current group, read by whole warps (broadcast)
+struct TcOut {  // per output prime of the current group, read by whole warps (one 16-byte broadcast)
   uint32_t q, w16s, div32, off;  // prime, Shoup companion of 2^16, floor(2^32 / q), limb offset * N
 };
+
+// One warp's share of a tile's epilogue: outputs [o_beg, o_end) of the accumulator at tbase
+// (columns 4 o + b hold 2^23 + S_b[o]) for coefficient n, four outputs (one 16-column load)
+// at a time with no predicated slots except in a last partial group.  lo = S_0 + 2^8 S_1 and
+// hi = S_2 + 2^8 S_3 (the 0x4B000000 of each accumulator cancels modulo 2^32), then
+// lo + (2^16 hi mod p) reduced once.  LAZY: the value is left in [0, 2p) (the conversions
+// inside the key-switching pipeline feed a forward NTT, which takes such inputs).
+template <bool LAZY>
+__device__ __forceinline__ void tc_out1(const uint32_t *r, const TcOut &t, uint32_t *gn, bool big_primes) {
+  const uint32_t lo = r[1] * 256u + r[0] - 0x4B000000u;
+  const uint32_t hi = r[3] * 256u + r[2] - 0x4B000000u;
+  const uint32_t sum = lo + red2(shoup_lazy(hi, 65536u, t.w16s, t.q), t.q);  // < 2^30 + 2^22 + q
+  uint32_t v;
+  if (big_primes) v = LAZY ? sum : red2(sum, t.q);
+  else {
+    v = shoup_lazy(sum, 1u, t.div32, t.q);
+    if (!LAZY) v = red2(v, t.q);
+  }
+  gn[t.off] = v;
+}
+template <bool LAZY>
+__device__ __forceinline__ void tc_reduce_outputs(uint32_t tbase, int o_beg, int o_end, const TcOut *sO, uint32_t *gn,
+                                                  bool big_primes) {
+  for (int o0 = o_beg; o0 < o_end; o0 += 4) {
+    uint32_t rr[16];
+    tmem_ld16(rr, tbase + (uint32_t)(4 * o0));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (o0 + 4 <= o_end) {
+#pragma unroll
+      for (int i = 0; i < 4; i++) tc_out1<LAZY>(rr + 4 * i, sO[o0 + i], gn, big_primes);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 3; i++)
+        if (o0 + i < o_end) tc_out1<LAZY>(rr + 4 * i, sO[o0 + i], gn, big_primes);
+    }
+  }
+}
 
 // Persistent: a CTA walks tiles (group, 128-coefficient block) in group-major
 // order, reloading the digit table only when the group changes; tensor memory
@@ -102,7 +139,6 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_bconv_tc(const __grid_constan
   TcOut *sO = reinterpret_cast<TcOut *>(sB + (size_t)npad_max * kRowBytes);
   uint64_t *bar = reinterpret_cast<uint64_t *>(sO + 64);
   uint32_t *s_taddr = reinterpret_cast<uint32_t *>(bar + 1);
-  int *s_ok = reinterpret_cast<int *>(s_taddr + 1);
   const uint32_t ncols = npad_max <= 32 ? 32u : npad_max <= 64 ? 64u : npad_max <= 128 ? 128u : 256u;
 
   if (warp == 0) {
@@ -150,7 +186,6 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_bconv_tc(const __grid_constan
   for (int h = 0; h < 2 * kNch; h++) y[h] = 0u;
   bool prefetched = false;  // y holds the current tile's inputs
   bool big_primes = true;   // the current group's output primes all exceed 2^30
-  uint32_t *gout = nullptr; // the current group's output base
   for (int tile = t0; tile < t1 && ok; tile++) {
     const int grp = tile / tiles_per_group;
     const size_t n0 = (size_t)(tile % tiles_per_group) * kTcM;
@@ -177,7 +212,6 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_bconv_tc(const __grid_constan
         big = big && p.q > kBigPrime;
       }
       big_primes = __syncthreads_and(big ? 1 : 0) != 0;
-      gout = gp->out;
     }
     // A: row r = coefficient n0 + r; chunk kc holds inputs 2 kc, 2 kc + 1 as the f16
     // values 1024 + byte (byte permutes against 0x64006400), absent inputs as 1024.
@@ -219,14 +253,13 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_bconv_tc(const __grid_constan
                        smem_addr(bar))
                    : "memory");
     }
-    // bounded wait by thread 0 alone, made CTA-uniform through the barrier (the
-    // tensor-memory loads are warp-synchronous)
-    if (tid == 0) *s_ok = mbar_wait_bounded(bar, phase) ? 1 : 0;
-    __syncthreads();
-    ok = *s_ok != 0;
+    // every thread waits (bounded) for the MMA itself, made warp-uniform for the
+    // warp-synchronous tensor-memory loads; the CTA-wide verdict rides on the tile's
+    // closing barrier
+    const bool w = __all_sync(0xffffffffu, mbar_wait_bounded(bar, phase));
     phase ^= 1u;
     tc_fence_after();
-    if (ok) {
+    if (w) {
       // epilogue: warp w reads lanes 32 (w % 4).. = coefficients n0 + 32 (w % 4) + lane; warps
       // w < 4 take outputs [0, H), the others [H, n_out) (H a multiple of 4), eight outputs
       // (two 16-column loads, one wait) at a time; columns 4 o + b hold 2^23 + S_b[o]
@@ -235,31 +268,15 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_bconv_tc(const __grid_constan
       const uint32_t tbase = taddr + ((uint32_t)(q4 * 32) << 16);
       const int H = ((n_out + 1) / 2 + 3) & ~3;
       const int o_end = (warp >> 2) ? n_out : min(H, n_out);
-      for (int o0 = (warp >> 2) ? H : 0; o0 < o_end; o0 += 8) {
-        uint32_t rr[32];
-        tmem_ld16(rr, tbase + (uint32_t)(4 * o0));
-        if (o0 + 4 < o_end) tmem_ld16(rr + 16, tbase + (uint32_t)(4 * (o0 + 4)));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const int cnt = min(8, o_end - o0);
-#pragma unroll
-        for (int i = 0; i < 8; i++) {
-          if (i < cnt) {
-            const TcOut t = sO[o0 + i];
-            // lo, hi < 2^30 + 2^22; the 0x4B000000 of each accumulator cancels modulo 2^32
-            const uint32_t lo = rr[4 * i + 1] * 256u + rr[4 * i] - 0x4B000000u;
-            const uint32_t hi = rr[4 * i + 3] * 256u + rr[4 * i + 2] - 0x4B000000u;
-            const uint32_t sum = lo + red2(shoup_lazy(hi, 65536u, t.w16s, t.q), t.q);  // < 2^30 + 2^22 + q
-            const uint32_t v = big_primes ? red2(sum, t.q) : red2(shoup_lazy(sum, 1u, t.div32, t.q), t.q);
-            gout[t.off + n] = v;
-          }
-        }
-      }
+      uint32_t *gn = gp->out + n;  // this thread's coefficient of the group's output limb 0
+      if (a.lazy) tc_reduce_outputs<true>(tbase, (warp >> 2) ? H : 0, o_end, sO, gn, big_primes);
+      else tc_reduce_outputs<false>(tbase, (warp >> 2) ? H : 0, o_end, sO, gn, big_primes);
     } else {
-      atomicOr(status, 1u);  // expired wait: report, give the MMA a second bounded chance
+      if ((tid & 31) == 0) atomicOr(status, 1u);  // expired wait: report, give the MMA a second bounded chance
       mbar_wait_bounded(bar, phase ^ 1u);
     }
     tc_fence_before();
-    __syncthreads();  // A, B and the accumulator are reused by the next tile
+    ok = __syncthreads_and(w ? 1 : 0) != 0;  // A, B and the accumulator are reused by the next tile
   }
   if (warp == 0) {
     tc_fence_after();
@@ -342,14 +359,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_bconv_tc_pipe(const __grid_co
   for (int h = 0; h < 2 * kNch; h++) y[h] = 0u;
   bool prefetched = false;
   bool big_primes = true;
-  uint32_t *gout = nullptr;
   int pending = -1;  // tile whose MMA is in flight and whose epilogue has not run
   // epilogue of tile p (accumulator p & 1): the unpipelined kernel's
   auto epilogue = [&](int p) {
     const int b = p & 1;
-    const bool w = mbar_wait_bounded(&bar[b], (ph >> b) & 1u);
+    const bool w = __all_sync(0xffffffffu, mbar_wait_bounded(&bar[b], (ph >> b) & 1u));
     ph ^= 1u << b;
-    if (!__all_sync(0xffffffffu, w)) {
+    if (!w) {
       ok = false;
       if ((tid & 31) == 0) atomicOr(status, 1u);
       return;
@@ -361,24 +377,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_bconv_tc_pipe(const __grid_co
     const uint32_t tbase = taddr0 + (uint32_t)b * ncols + ((uint32_t)(q4 * 32) << 16);
     const int H = ((n_out + 1) / 2 + 3) & ~3;
     const int o_end = (warp >> 2) ? n_out : min(H, n_out);
-    for (int o0 = (warp >> 2) ? H : 0; o0 < o_end; o0 += 8) {
-      uint32_t rr[32];
-      tmem_ld16(rr, tbase + (uint32_t)(4 * o0));
-      if (o0 + 4 < o_end) tmem_ld16(rr + 16, tbase + (uint32_t)(4 * (o0 + 4)));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      const int cnt = min(8, o_end - o0);
-#pragma unroll
-      for (int i = 0; i < 8; i++) {
-        if (i < cnt) {
-          const TcOut t = sO[o0 + i];
-          const uint32_t lo = rr[4 * i + 1] * 256u + rr[4 * i] - 0x4B000000u;
-          const uint32_t hi = rr[4 * i + 3] * 256u + rr[4 * i + 2] - 0x4B000000u;
-          const uint32_t sum = lo + red2(shoup_lazy(hi, 65536u, t.w16s, t.q), t.q);
-          const uint32_t v = big_primes ? red2(sum, t.q) : red2(shoup_lazy(sum, 1u, t.div32, t.q), t.q);
-          gout[t.off + n] = v;
-        }
-      }
-    }
+    uint32_t *gn = gp->out + n;
+    if (a.lazy) tc_reduce_outputs<true>(tbase, (warp >> 2) ? H : 0, o_end, sO, gn, big_primes);
+    else tc_reduce_outputs<false>(tbase, (warp >> 2) ? H : 0, o_end, sO, gn, big_primes);
   };
   for (int tile = t0; tile < t1 && ok; tile++) {
     const int grp = tile / tiles_per_group;
@@ -412,7 +413,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_bconv_tc_pipe(const __grid_co
         big = big && pr.q > kBigPrime;
       }
       big_primes = __syncthreads_and(big ? 1 : 0) != 0;
-      gout = gp->out;
     }
     uint8_t *Ab = sA + (tile & 1) * kAbytes;
     {

@@ -387,6 +387,7 @@ int run_program_inline(fhe_ctx *c, const Program &P, cudaStream_t s) {
     }
     for (size_t i = 0; i < P.ks.size(); i++) sl.ks[i] = sl2.ks[i] = P.ks[i];
     for (const BconvGroup &g : st.groups) ba.g[ba.ngroups++] = g;
+    ba.lazy = 1;  // every conversion of a program feeds a forward NTT
     cudaError_t e = launch_stage(c, st, sl, ba, s, 0, &sl2);
     if (e != cudaSuccess) return fhe_fail(FHE_ECUDA, "stage launch: %s", cudaGetErrorString(e));
   }
@@ -467,6 +468,7 @@ int upload_program(fhe_ctx *c, const Program &P, DevProgram &D) {
     BconvArgs &ba = D.bargs[i];
     memset(&ba, 0, sizeof ba);
     ba.ngroups = (int)st.groups.size();
+    ba.lazy = 1;  // every conversion of a program feeds a forward NTT
     ba.dev = reinterpret_cast<const BconvGroup *>(base + grp_off[i]);
   }
   (void)c;
