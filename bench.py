@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--sweep", action="store_true",
                     help="kernel-utilisation sweep (NTT over 10..250 limbs, BConv over output counts, key-switch "
                          "batch sizes) as one JSON line instead of the benchmark line")
+    ap.add_argument("--shape", default="",
+                    help="kernel shape for --profile-run, comma-separated key=value (fhe_ctx_set_kernel_shape fields, "
+                         "e.g. fuse_ip_moddown=1)")
     ap.add_argument("--profile-run", choices=["scalar", "tc", "cts", "lt"], default=None,
                     help="only launch the batched stage programs (one lane, no graph) warmup + steps times, "
                          "in a fixed launch order for profilers ('cts': the CoeffToSlot chain at N = 2^16, "
@@ -241,7 +244,7 @@ def bench_batch64(binding, inputs, roofline, dev, timed, steps, bconv_mode):
             items.append(dict(op=binding.FHE_OP_RELIN, level=lv, **{"in": a}, in2=b, out=out))
         nbytes += roofline.ks_bytes(P.N, lv, P.K, P.alpha)
     # schedule: measured by the library's autotuner at the mean level of the mix
-    tune = ctx.autotune(sum(it["level"] for it in items) // len(items), 16)
+    tune = ctx.autotune(sum(it["level"] for it in items) // len(items), 16, binding.FHE_TUNE_SHAPE)
     plan = ctx.batch_plan(items, binding.FHE_PLAN_GRAPH)
     for _ in range(3):
         plan.launch()
@@ -405,7 +408,7 @@ def bench_paper_shapes(binding, inputs, roofline, dev, timed, steps, l2_gbs, B=8
             ct = binding.to_device(np.stack([inputs.uniform_residues(g, P.q, P.N) for _ in range(2)]), dev)
             items.append(dict(op=binding.FHE_OP_ROTATE, level=P.L, rot=r, **{"in": ct},
                               out=binding.empty((2, P.L, P.N), dev)))
-        tune = ctx.autotune(P.L, B, binding.FHE_TUNE_BCONV)
+        tune = ctx.autotune(P.L, B, binding.FHE_TUNE_BCONV | binding.FHE_TUNE_SHAPE)
         plan = ctx.batch_plan(items, binding.FHE_PLAN_GRAPH)
         for _ in range(3):
             plan.launch()
@@ -514,12 +517,15 @@ def run_sweep(args, dev):
     print(json.dumps({"sweep": out}), flush=True)
 
 
-def kernel_model(name, P, level, G):
+def kernel_model(name, P, level, G, fused_ip_md=False):
     """Algorithmic bytes and operations of the stage kernel `name` summed over its
     launches in one batched group of G HRotates at `level` (fused pipeline): each
     NTT pass reads and writes its limbs once, the base conversions read their input
     and write their output limbs once, the inner product reads the decomposed limbs
-    and both key halves and writes two extended polynomials."""
+    and both key halves and writes two extended polynomials.  With fused_ip_md the
+    special limbs' inner product and ModDown's first inverse pass are one kernel
+    ("ip+intt_blk": the K special limbs' digits and keys read once, the pass's two
+    outputs written), and the inner product covers the ciphertext limbs only."""
     W = 4 * P.N
     K, A, beta = P.K, P.alpha, P.beta(level)
     widths = [min(A, level - j * A) for j in range(beta)]
@@ -540,6 +546,9 @@ def kernel_model(name, P, level, G):
         # pass-through limb (sigma(c0)) each q-limb reads for the u += P sigma(c0) fold
         "inner_product": (((level + K) * (3 * beta + 2) + level) * W, 2 * beta * (level + K) * P.N, "mac"),
     }
+    if fused_ip_md:
+        m["inner_product"] = ((level * (3 * beta + 2) + level) * W, 2 * beta * level * P.N, "mac")
+        m["ip+intt_blk"] = (K * (3 * beta + 2) * W, 2 * beta * K * P.N + 2 * K * bf_blk, "mac")
     b, o, unit = m.get(name, (0, 0, "bfly"))
     return b * G, o * G, unit
 
@@ -554,10 +563,11 @@ ALU_PEAK_SOURCE = ["derived from probe unit counts x 152 SMs x 2.07 GHz"]
 NTT_KERNELS = ("intt_blk+gather", "intt_col+scale", "ntt_col", "ntt_blk", "intt_blk", "ntt_blk+combine")
 
 
-def measured_traffic_per_item(name):
+def measured_traffic_per_item(name, fused_ip_md=False):
     """DRAM bytes per item of kernel `name` (summed over its launches in one group) from
     its committed ncu summary, or None when there is none or the kernel's sources
-    changed since the capture."""
+    changed since the capture.  With the fused special-limb kernel the inner product
+    covers the q-limbs only (its own figure in the summary)."""
     import hashlib
     import re
     files = {"inner_product": "inner_product_N65536_L24.md"}
@@ -565,7 +575,8 @@ def measured_traffic_per_item(name):
         return None
     try:
         text = open(os.path.join(ROOT, "profiles", files[name])).read()
-        per_item = int(re.search(r"^traffic_bytes_per_item: (\d+)$", text, re.M).group(1))
+        key = "traffic_bytes_per_item_qlimbs" if fused_ip_md else "traffic_bytes_per_item"
+        per_item = int(re.search(r"^" + key + r": (\d+)$", text, re.M).group(1))
         want = re.search(r"^kernel_sources_sha256: ([0-9a-f]+)$", text, re.M).group(1)
         srcs = re.search(r"^kernel_sources: (.+)$", text, re.M).group(1).split()
         h = hashlib.sha256()
@@ -576,16 +587,16 @@ def measured_traffic_per_item(name):
     return per_item if h.hexdigest() == want else None
 
 
-def kernel_roofline(name, launches_per_group, launch_ms, P, level, G, hbm_peak):
+def kernel_roofline(name, launches_per_group, launch_ms, P, level, G, hbm_peak, fused_ip_md=False):
     """Roofline entry of one kernel: the bound (HBM bytes or ALU operations) with the
     larger achieved fraction of its peak."""
-    nbytes, ops, unit = kernel_model(name, P, level, G)
+    nbytes, ops, unit = kernel_model(name, P, level, G, fused_ip_md)
     lpg = max(launches_per_group, 1e-9)
     per_launch_bytes, per_launch_ops = nbytes / lpg, ops / lpg
     gbs = per_launch_bytes / (launch_ms / 1e3) / 1e9
     ach_ops = per_launch_ops / (launch_ms / 1e3)
     f_hbm, f_alu = gbs / hbm_peak, ach_ops / ALU_PEAK[unit]
-    per_item = measured_traffic_per_item(name)
+    per_item = measured_traffic_per_item(name, fused_ip_md)
     common = {"traffic": per_item * G / lpg if per_item else None, "kernel": name, "launch_ms": launch_ms,
               "algorithmic_bytes_per_launch": per_launch_bytes, "algorithmic_ops_per_launch": per_launch_ops,
               "frac_hbm": f_hbm, "frac_alu": f_alu}
@@ -610,13 +621,13 @@ def measure_alu_peaks(binding, dev):
         return {"failed": str(ex)}
 
 
-def kernel_rates(stats, P, level, G, groups_traced, hbm_peak):
+def kernel_rates(stats, P, level, G, groups_traced, hbm_peak, fused_ip_md=False):
     """Per traced kernel: its algorithmic rate over its summed event time and the fraction of
     the peak that bounds it; and the NTT family's aggregate butterfly rate (all forward and
     inverse passes of the key switch: their butterflies over their summed time)."""
     rows, ntt_ops, ntt_ms = {}, 0.0, 0.0
     for name, (n, t_ms) in stats.items():
-        nbytes, ops, unit = kernel_model(name, P, level, G)
+        nbytes, ops, unit = kernel_model(name, P, level, G, fused_ip_md)
         if not t_ms or not (nbytes or ops):
             continue
         secs = t_ms / 1e3
@@ -707,6 +718,8 @@ def main():
         ctx.set_batch(0, 0, 1)
         if args.ntt != "auto":
             ctx.set_ntt(int(args.ntt))
+        if args.shape:
+            ctx.set_kernel_shape(**{k: int(v) for k, v in (kv.split("=") for kv in args.shape.split(","))})
         plan_p = ctx.batch_plan(items, 0)
         for _ in range(args.warmup + args.steps):
             plan_p.launch()
@@ -741,7 +754,7 @@ def main():
         ctx.set_batch(args.l2_budget_mb << 20, 0, args.lanes)
     else:
         ctx.set_bconv(binding.FHE_BCONV_TC)
-        tune = ctx.autotune(level, B, binding.FHE_TUNE_NTT if args.ntt == "auto" else 0)
+        tune = ctx.autotune(level, B, binding.FHE_TUNE_SHAPE | (binding.FHE_TUNE_NTT if args.ntt == "auto" else 0))
     if args.ntt != "auto":
         ctx.set_ntt(int(args.ntt))
     budget = tune["l2_budget_bytes"] if tune else args.l2_budget_mb << 20
@@ -858,10 +871,11 @@ def main():
 
     # dominant kernel of the batched step: algorithmic bytes and operations per launch
     ngroups = max(1, len(groups))
+    fused_md = bool(ctx.kernel_shape()["fuse_ip_moddown"])
     roof = kernel_roofline(top_name, top_n / (cmp_steps * ngroups), per_launch_ms, P, level, B / ngroups,
-                           hbm_peak)
+                           hbm_peak, fused_md)
     roof["share"] = top_ms / total_ms if total_ms else None
-    krates, ntt_family = kernel_rates(stats, P, level, B / ngroups, cmp_steps * ngroups, hbm_peak)
+    krates, ntt_family = kernel_rates(stats, P, level, B / ngroups, cmp_steps * ngroups, hbm_peak, fused_md)
 
     # --- e2e: every step copies its inputs from pinned host memory and its results back,
     # inside the timed region, through the same public API.  Steps alternate between two
