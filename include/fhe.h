@@ -174,7 +174,15 @@ FHE_API int fhe_ctx_set_ntt(fhe_ctx *ctx, int flags);
  *     previous tile's accumulator is reduced (at most two CTAs per SM for more
  *     than 16 outputs, one for more than 32);
  *   ntt_stream_stages, ntt_stream_ctas: shared-memory stages per CTA (2..3) and
- *     persistent CTAs per SM (1..3) of the FHE_NTT_STREAM passes.
+ *     persistent CTAs per SM (1..3) of the FHE_NTT_STREAM passes;
+ *   ip_staged_gather: 1 (the default) has the hoisted inner product (digits
+ *     read through an automorphism, Section V-C) copy each digit's permuted
+ *     32-coefficient blocks into shared memory with bulk copies, so that every
+ *     digit value is a shared-memory read; 0 gathers them with 4-byte global
+ *     loads.  Launches that add the pass-through polynomial to both halves
+ *     (relinearisation) use the gathering kernel either way;
+ *   ip_staged_ctas: resident CTAs per SM of that staged kernel (1: one CTA
+ *     with up to four stages in 227 KB; 2: two CTAs of up to 113 KB).
  * Programs and plans built after the call use the new shape.  FHE_EINVAL for a
  * value out of range; FHE_EUNSUPPORTED for fuse_ip_moddown at N != 2^16. */
 typedef struct {
@@ -183,6 +191,8 @@ typedef struct {
   int ntt_stream_stages;
   int ntt_stream_ctas;
   int bconv_tc_pipeline;
+  int ip_staged_gather;
+  int ip_staged_ctas;
 } fhe_kernel_shape;
 FHE_API int fhe_ctx_set_kernel_shape(fhe_ctx *ctx, const fhe_kernel_shape *shape);
 FHE_API int fhe_ctx_get_kernel_shape(const fhe_ctx *ctx, fhe_kernel_shape *out);

@@ -331,6 +331,8 @@ static bool tune_parse(const char *rest, const fhe_kernel_shape &dflt, fhe_tune_
                &t.max_group, &t.bconv_mode, &t.ip_ctas_per_sm, &t.comp_pipe, &t.ntt_mode, &t.us_per_ks) != 8)
       return false;
   }
+  k.ip_staged_gather = dflt.ip_staged_gather;  // not tuned (key switches read their digits directly)
+  k.ip_staged_ctas = dflt.ip_staged_ctas;
   if (k.fuse_ip_moddown < 0 || k.fuse_ip_moddown > 1 || k.bconv_tc_ctas < 1 || k.bconv_tc_ctas > 4 ||
       k.ntt_stream_stages < 2 || k.ntt_stream_stages > 3 || k.ntt_stream_ctas < 1 || k.ntt_stream_ctas > 3 ||
       k.bconv_tc_pipeline < 0 || k.bconv_tc_pipeline > 1)

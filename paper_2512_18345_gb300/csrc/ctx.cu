@@ -267,6 +267,8 @@ static int build_tables(fhe_ctx *c) {
   c->tabs.ntt_stream_ctas = 3;
   c->tabs.bconv_tc_ctas = 4;
   c->tabs.bconv_tc_pipe = 0;
+  c->tabs.ip_staged = 1;
+  c->tabs.ip_staged_ctas = 2;
   c->tabs.status = c->d_status;
   return FHE_OK;
 }
@@ -546,10 +548,12 @@ extern "C" int fhe_ctx_set_kernel_shape(fhe_ctx *c, const fhe_kernel_shape *sh) 
   if (!c || !sh) return fhe_fail(FHE_EINVAL, "fhe_ctx_set_kernel_shape: null");
   if ((sh->fuse_ip_moddown != 0 && sh->fuse_ip_moddown != 1) || sh->bconv_tc_ctas < 1 || sh->bconv_tc_ctas > 4 ||
       sh->ntt_stream_stages < 2 || sh->ntt_stream_stages > 3 || sh->ntt_stream_ctas < 1 || sh->ntt_stream_ctas > 3 ||
-      (sh->bconv_tc_pipeline != 0 && sh->bconv_tc_pipeline != 1))
+      (sh->bconv_tc_pipeline != 0 && sh->bconv_tc_pipeline != 1) ||
+      (sh->ip_staged_gather != 0 && sh->ip_staged_gather != 1) || sh->ip_staged_ctas < 1 || sh->ip_staged_ctas > 2)
     return fhe_fail(FHE_EINVAL, "fhe_ctx_set_kernel_shape: fuse %d (0, 1), bconv_tc_ctas %d (1..4), stages %d (2..3), "
-                    "stream ctas %d (1..3), pipeline %d (0, 1)", sh->fuse_ip_moddown, sh->bconv_tc_ctas,
-                    sh->ntt_stream_stages, sh->ntt_stream_ctas, sh->bconv_tc_pipeline);
+                    "stream ctas %d (1..3), pipeline %d (0, 1), staged gather %d (0, 1), staged ctas %d (1, 2)",
+                    sh->fuse_ip_moddown, sh->bconv_tc_ctas, sh->ntt_stream_stages, sh->ntt_stream_ctas,
+                    sh->bconv_tc_pipeline, sh->ip_staged_gather, sh->ip_staged_ctas);
   if (sh->fuse_ip_moddown && c->logn != 16)
     return fhe_fail(FHE_EUNSUPPORTED, "fhe_ctx_set_kernel_shape: the fused inner product needs N = 2^16");
   c->fuse_ip_md = sh->fuse_ip_moddown;
@@ -557,6 +561,8 @@ extern "C" int fhe_ctx_set_kernel_shape(fhe_ctx *c, const fhe_kernel_shape *sh) 
   c->tabs.ntt_stream_stages = sh->ntt_stream_stages;
   c->tabs.ntt_stream_ctas = sh->ntt_stream_ctas;
   c->tabs.bconv_tc_pipe = sh->bconv_tc_pipeline;
+  c->tabs.ip_staged = sh->ip_staged_gather;
+  c->tabs.ip_staged_ctas = sh->ip_staged_ctas;
   return FHE_OK;
 }
 
@@ -567,6 +573,8 @@ extern "C" int fhe_ctx_get_kernel_shape(const fhe_ctx *c, fhe_kernel_shape *out)
   out->ntt_stream_stages = c->tabs.ntt_stream_stages;
   out->ntt_stream_ctas = c->tabs.ntt_stream_ctas;
   out->bconv_tc_pipeline = c->tabs.bconv_tc_pipe;
+  out->ip_staged_gather = c->tabs.ip_staged;
+  out->ip_staged_ctas = c->tabs.ip_staged_ctas;
   return FHE_OK;
 }
 

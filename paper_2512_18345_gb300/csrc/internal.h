@@ -66,6 +66,8 @@ struct DevTables {
   int ntt_stream_ctas;     // persistent CTAs per SM of those kernels (1..3)
   int bconv_tc_ctas;       // resident CTAs per SM of the tensor-core BConv (1..4)
   int bconv_tc_pipe;       // the tensor-core BConv with two accumulators per CTA (MMA beside epilogue)
+  int ip_staged;           // hoisted inner product: digits' permuted blocks staged (ip_hoisted.cuh)
+  int ip_staged_ctas;      // resident CTAs per SM of that kernel (1 or 2)
   int tc_k;                // K of the context's tensor-core BConv tables (48 or 64; 0: none)
 };
 
@@ -106,7 +108,7 @@ cudaError_t launch_bconv_tc(const DevTables &t, const BconvArgs &a, int max_in, 
 cudaError_t launch_ew(const DevTables &t, int op, const SegList &sl, cudaStream_t s);
 // key inner product (both halves) for the ext limbs of sl; seg.dst = u_0[t0]
 // beta_max: the largest digit count among the segments' items (sizes the stages)
-cudaError_t launch_ip(const DevTables &t, const SegList &sl, bool gather_own, bool gather_ext, int beta_max,
+cudaError_t launch_ip(const DevTables &t, const SegList &sl, bool gather_own, bool gather_ext, bool add_c1, int beta_max,
                       cudaStream_t s);
 // the special limbs' inner product fused with ModDown's first inverse-NTT pass (ip_intt.cuh);
 // sl: one segment per item over its K special limbs, dst = the item's UC [2][K][N]

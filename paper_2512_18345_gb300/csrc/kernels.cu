@@ -10,6 +10,7 @@
 #include "ntt.cuh"
 #include "ntt_bulk.cuh"
 #include "ip_intt.cuh"
+#include "ip_hoisted.cuh"
 
 namespace fhe {
 
@@ -235,11 +236,31 @@ cudaError_t launch_bconv(const DevTables &t, const BconvArgs &a, int max_in, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_ip(const DevTables &t, const SegList &sl, bool gather_own, bool gather_ext, int beta_max,
-                      cudaStream_t s) {
+cudaError_t launch_ip(const DevTables &t, const SegList &sl, bool gather_own, bool gather_ext, bool add_c1,
+                      int beta_max, cudaStream_t s) {
   if (sl.total == 0) return cudaSuccess;
   TraceScope ts(t, "inner_product", s);
   const bool go = gather_own, ge = gather_ext;
+  if (ge && t.ip_staged && !add_c1 && beta_max >= 1 && beta_max <= 4 && (1 << t.logn) % kIpChunk == 0) {
+    // hoisted: every row's permuted 32-coefficient blocks staged in shared memory (ip_hoisted.cuh);
+    // as many stages (up to four) as fit one or two CTAs per SM
+    const int ctas = std::max(1, std::min(2, t.ip_staged_ctas));
+    const int per_stage = ip_hoisted_stage_words(beta_max) * 4 + 16 + (int)sizeof(IhUnit);
+    const int stages = std::min(4, ((ctas == 2 ? 113 : 227) * 1024 - 256) / per_stage);
+    static PerDeviceOnce configured;
+    const cudaError_t e = configured.run([] {
+      return cudaFuncSetAttribute(k_ip_hoisted, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    });
+    if (e != cudaSuccess) return e;
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int units = sl.total * ((1 << t.logn) / kIpChunk);
+    const unsigned grid = (unsigned)std::min(units, ctas * sms);
+    k_ip_hoisted<<<grid, kIpThreads + 32, stages * per_stage, s>>>(sl, t.pc, t.logn, t.status, beta_max, stages);
+    g_launches++;
+    return cudaGetLastError();
+  }
   if (beta_max >= 1 && beta_max <= 4 && (1 << t.logn) % kIpChunk == 0) {
     // streaming kernel, one or two CTAs per SM.  Two stages per CTA where each stage holds
     // the ModUp values and the keys (with the producer warp refilling a stage as soon as it

@@ -239,6 +239,7 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
     if (has_ip(it)) {
       ipq.gather_own |= k.galois_own != 1u;
       ipq.gather_ext |= k.galois_ext != 1u;
+      ipq.add_c1 |= k.addp && k.add_c1;
       Seg a = seg(nullptr, U, level, 0, (int)i);
       a.t0 = 0;
       a.key_row0 = 0;
@@ -287,6 +288,7 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
   }
   ipp.gather_own = ipq.gather_own;
   ipp.gather_ext = ipq.gather_ext;
+  ipp.add_c1 = ipq.add_c1;
   // complementary pipelining (Section IV-B): the q-limb inner product on an auxiliary
   // branch beside ModDown's special-limb chain; otherwise one launch over all limbs
   const bool has_md = !m2.segs.empty();
@@ -347,7 +349,7 @@ static cudaError_t launch_stage(fhe_ctx *c, const Stage &st, const SegList &sl, 
     case Stage::NTT: return launch_ntt_pass(c->tabs, st.column, st.fwd, st.pro, st.epi, sl, q);
     case Stage::NTT1: return launch_ntt_single(c->tabs, st.fwd, st.pro, st.epi, sl, *sl2, q);
     case Stage::EW: return launch_ew(c->tabs, st.ewop, sl, q);
-    case Stage::IP: return launch_ip(c->tabs, sl, st.gather_own, st.gather_ext, c->dnum, q);
+    case Stage::IP: return launch_ip(c->tabs, sl, st.gather_own, st.gather_ext, st.add_c1, c->dnum, q);
     case Stage::IPN: return launch_ip_intt(c->tabs, sl, std::min(c->dnum, 4), q);
     case Stage::BCONV:
       return c->bconv_mode == FHE_BCONV_TC ? launch_bconv_tc(c->tabs, ba, st.max_in, st.max_out, q, c->tabs.tc_k)

@@ -37,6 +37,7 @@ struct Stage {
   int pro = 0, epi = 0, ewop = 0;
   bool aux = false;
   bool gather_own = false, gather_ext = false;
+  bool add_c1 = false;  // IP: some item adds its pass-through polynomial to both halves
   int max_in = 0, max_out = 0;
   std::vector<fhe::Seg> segs;
   std::vector<fhe::Seg> segs2;

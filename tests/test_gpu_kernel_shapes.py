@@ -159,12 +159,14 @@ def test_kernel_shape_validation(fhe_lib):
     P = inputs.workload_params("hmult_relin_rescale_N4096_L4")
     ctx = binding.Context.from_params(P)
     assert ctx.kernel_shape() == {"fuse_ip_moddown": 0, "bconv_tc_ctas": 4, "ntt_stream_stages": 3,
-                                  "ntt_stream_ctas": 3, "bconv_tc_pipeline": 0}
+                                  "ntt_stream_ctas": 3, "bconv_tc_pipeline": 0, "ip_staged_gather": 1,
+                                  "ip_staged_ctas": 2}
     with pytest.raises(binding.FheError) as e:
         ctx.set_kernel_shape(fuse_ip_moddown=1)  # the fused kernel is 2^16-only
     assert e.value.code == binding.FHE_EUNSUPPORTED
     for bad in ({"bconv_tc_ctas": 0}, {"bconv_tc_ctas": 5}, {"ntt_stream_stages": 1}, {"ntt_stream_ctas": 4},
-                {"fuse_ip_moddown": 2}, {"bconv_tc_pipeline": 2}):
+                {"fuse_ip_moddown": 2}, {"bconv_tc_pipeline": 2}, {"ip_staged_gather": 2},
+                {"ip_staged_gather": -1}, {"ip_staged_ctas": 0}, {"ip_staged_ctas": 3}):
         with pytest.raises(binding.FheError) as e:
             ctx.set_kernel_shape(**bad)
         assert e.value.code == binding.FHE_EINVAL
@@ -232,4 +234,63 @@ def test_pipelined_tc_bconv_twelve_limb_digits(fhe_lib):
     ctx.set_relin_key(dev(key))
     d = inputs.uniform_residues(g, P.q, P.N)
     assert np.array_equal(host(ctx, ctx.keyswitch(dev(d), P.L)), oracle.keyswitch(OP, d, P.L, key))
+    ctx.close()
+
+
+SHAPES_HOISTED = [dict(ip_staged_gather=1, ip_staged_ctas=2), dict(ip_staged_gather=1, ip_staged_ctas=1),
+                  dict(ip_staged_gather=0)]
+
+
+@pytest.mark.parametrize("staged", range(len(SHAPES_HOISTED)))
+@pytest.mark.parametrize("name,level,rots", [("hmult_relin_rescale_N4096_L4", 4, [0, 1, 2, 5, 15, -1]),
+                                             ("hmult_relin_rescale_N4096_L4", 1, [3, 2047]),
+                                             ("hrotate_N65536_L24_tc", 24, [0, 1, 7, 100]),
+                                             ("hrotate_N65536_L24_tc", 11, [1, -3])])
+def test_hoisted_inner_product_both_gathers(fhe_lib, staged, name, level, rots):
+    """Hoisted rotations (sigma applied to the extended digits) through the staged-block kernel
+    (one or two CTAs per SM) and through the gathering one: each equals the oracle bit for bit, at digit counts 1..3 and
+    with the identity rotation in the batch (sigma_1 beside proper automorphisms)."""
+    from paper_2512_18345_gb300 import binding
+    P = inputs.workload_params(name)
+    OP = oracle.OracleParams.from_params(P)
+    ctx = binding.Context.from_params(P)
+    ctx.set_kernel_shape(**SHAPES_HOISTED[staged])
+    g = inputs.rng(3700 + level + 17 * staged)
+    keys = [None if r % (P.N // 2) == 0 else rand_key(P, g) for r in rots]
+    for r, k in zip(rots, keys):
+        if k is not None:
+            ctx.set_rot_key(r, dev(k))
+    ct = np.stack([inputs.uniform_residues(g, P.q[:level], P.N) for _ in range(2)])
+    ct[:, :, : P.N // 8] = np.array(P.q[:level], dtype=np.uint32)[None, :, None] - 1  # the largest residues
+    outs = ctx.rotate_hoisted(dev(ct), level, rots)
+    want = oracle.rotate_hoisted(OP, ct, level, rots, keys)
+    for i, r in enumerate(rots):
+        assert np.array_equal(host(ctx, outs[i]), want[i]), f"rotation {r}"
+    ctx.close()
+
+
+@pytest.mark.parametrize("staged", range(len(SHAPES_HOISTED)))
+def test_double_hoisted_level_both_gathers(fhe_lib, staged):
+    """A double-hoisted CoeffToSlot level (baby-step inner products over the extended basis,
+    giant steps on the extended sums) with either hoisted inner product."""
+    from oracle import bootstrap_lt as blt
+    from paper_2512_18345_gb300 import binding
+    name = "cts_stc_N4096_L8"
+    P = inputs.workload_params(name)
+    OP = oracle.OracleParams.from_params(P)
+    W = inputs.WORKLOADS[name]
+    plan = inputs.transform_plans(P.N, W["levels"], "cts")[1]
+    level = W["cts_level"] - 1
+    g = inputs.rng(3800 + staged)
+    ctx = binding.Context.from_params(P)
+    ctx.set_kernel_shape(**SHAPES_HOISTED[staged])
+    keys = {}
+    for r in plan.rotations():
+        keys[r] = rand_key(P, g)
+        ctx.set_rot_key(r, dev(keys[r]))
+    ct = np.stack([inputs.uniform_residues(g, P.q[:level], P.N) for _ in range(2)])
+    xp = tuple(P.q[:level]) + tuple(P.p)
+    diags = np.stack([inputs.uniform_residues(g, xp, P.N) for _ in range(plan.n_diag)])
+    got = host(ctx, ctx.linear_transform_dh(dev(ct), level, plan.baby, plan.giant, dev(diags), plan.idx))
+    assert np.array_equal(got, blt.lt_double_hoisted(OP, ct, level, plan.baby, plan.giant, diags, plan.idx, keys))
     ctx.close()
