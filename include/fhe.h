@@ -181,8 +181,11 @@ FHE_API int fhe_ctx_set_ntt(fhe_ctx *ctx, int flags);
  *     digit value is a shared-memory read; 0 gathers them with 4-byte global
  *     loads.  Launches that add the pass-through polynomial to both halves
  *     (relinearisation) use the gathering kernel either way;
- *   ip_staged_ctas: resident CTAs per SM of that staged kernel (1: one CTA
- *     with up to four stages in 227 KB; 2: two CTAs of up to 113 KB).
+ *   ip_staged_ctas, ip_staged_depth: resident CTAs per SM (1: one CTA of up
+ *     to 227 KB of shared memory; 2: two of up to 113 KB) and stages per warp
+ *     (2..4; 0: 2) of that staged kernel, whose warps each run their own
+ *     pipeline; a CTA has as many warps as its shared memory holds, at most
+ *     16 per SM.
  * Programs and plans built after the call use the new shape.  FHE_EINVAL for a
  * value out of range; FHE_EUNSUPPORTED for fuse_ip_moddown at N != 2^16. */
 typedef struct {
@@ -193,6 +196,7 @@ typedef struct {
   int bconv_tc_pipeline;
   int ip_staged_gather;
   int ip_staged_ctas;
+  int ip_staged_depth;
 } fhe_kernel_shape;
 FHE_API int fhe_ctx_set_kernel_shape(fhe_ctx *ctx, const fhe_kernel_shape *shape);
 FHE_API int fhe_ctx_get_kernel_shape(const fhe_ctx *ctx, fhe_kernel_shape *out);

@@ -67,7 +67,7 @@ class KernelShape(ctypes.Structure):
     _fields_ = [("fuse_ip_moddown", ctypes.c_int), ("bconv_tc_ctas", ctypes.c_int),
                 ("ntt_stream_stages", ctypes.c_int), ("ntt_stream_ctas", ctypes.c_int),
                 ("bconv_tc_pipeline", ctypes.c_int), ("ip_staged_gather", ctypes.c_int),
-                ("ip_staged_ctas", ctypes.c_int)]
+                ("ip_staged_ctas", ctypes.c_int), ("ip_staged_depth", ctypes.c_int)]
 
 
 class TuneResult(ctypes.Structure):
@@ -329,8 +329,8 @@ class Context:
 
     def set_kernel_shape(self, **kw) -> None:
         """Change some fields of the kernel shape (fuse_ip_moddown, bconv_tc_ctas,
-        ntt_stream_stages, ntt_stream_ctas, bconv_tc_pipeline, ip_staged_gather, ip_staged_ctas); the others keep their
-        values."""
+        ntt_stream_stages, ntt_stream_ctas, bconv_tc_pipeline, ip_staged_gather, ip_staged_ctas,
+        ip_staged_depth); the others keep their values."""
         cur = self.kernel_shape()
         unknown = set(kw) - set(cur)
         if unknown:

@@ -333,6 +333,7 @@ static bool tune_parse(const char *rest, const fhe_kernel_shape &dflt, fhe_tune_
   }
   k.ip_staged_gather = dflt.ip_staged_gather;  // not tuned (key switches read their digits directly)
   k.ip_staged_ctas = dflt.ip_staged_ctas;
+  k.ip_staged_depth = dflt.ip_staged_depth;
   if (k.fuse_ip_moddown < 0 || k.fuse_ip_moddown > 1 || k.bconv_tc_ctas < 1 || k.bconv_tc_ctas > 4 ||
       k.ntt_stream_stages < 2 || k.ntt_stream_stages > 3 || k.ntt_stream_ctas < 1 || k.ntt_stream_ctas > 3 ||
       k.bconv_tc_pipeline < 0 || k.bconv_tc_pipeline > 1)

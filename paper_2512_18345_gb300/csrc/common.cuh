@@ -107,6 +107,11 @@ struct SegList {
   const Seg *dev;         // if non-null: segments in device memory
   const int2 *vmap;       // optional [total] (segment, limb within) for device lists
   const KsArgs *ksdev;    // if non-null: per-item arguments in device memory
+  // optional limb-major order of an inline list, read by the hoisted inner product (0 groups:
+  // list order): group g is lm_count[g] consecutive segments from lm_first[g], all of one size
+  // and first extended-basis index, whose limbs are taken limb by limb across the segments
+  int lm_groups;
+  int lm_first[4], lm_count[4];
   Seg seg[kMaxSeg];
   KsArgs ks[kMaxInlineItems];
 };

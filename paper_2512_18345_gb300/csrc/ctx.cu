@@ -269,6 +269,7 @@ static int build_tables(fhe_ctx *c) {
   c->tabs.bconv_tc_pipe = 0;
   c->tabs.ip_staged = 1;
   c->tabs.ip_staged_ctas = 2;
+  c->tabs.ip_staged_depth = 0;
   c->tabs.status = c->d_status;
   return FHE_OK;
 }
@@ -549,11 +550,13 @@ extern "C" int fhe_ctx_set_kernel_shape(fhe_ctx *c, const fhe_kernel_shape *sh) 
   if ((sh->fuse_ip_moddown != 0 && sh->fuse_ip_moddown != 1) || sh->bconv_tc_ctas < 1 || sh->bconv_tc_ctas > 4 ||
       sh->ntt_stream_stages < 2 || sh->ntt_stream_stages > 3 || sh->ntt_stream_ctas < 1 || sh->ntt_stream_ctas > 3 ||
       (sh->bconv_tc_pipeline != 0 && sh->bconv_tc_pipeline != 1) ||
-      (sh->ip_staged_gather != 0 && sh->ip_staged_gather != 1) || sh->ip_staged_ctas < 1 || sh->ip_staged_ctas > 2)
+      (sh->ip_staged_gather != 0 && sh->ip_staged_gather != 1) || sh->ip_staged_ctas < 1 || sh->ip_staged_ctas > 2 ||
+      sh->ip_staged_depth < 0 || sh->ip_staged_depth == 1 || sh->ip_staged_depth > 4)
     return fhe_fail(FHE_EINVAL, "fhe_ctx_set_kernel_shape: fuse %d (0, 1), bconv_tc_ctas %d (1..4), stages %d (2..3), "
-                    "stream ctas %d (1..3), pipeline %d (0, 1), staged gather %d (0, 1), staged ctas %d (1, 2)",
-                    sh->fuse_ip_moddown, sh->bconv_tc_ctas, sh->ntt_stream_stages, sh->ntt_stream_ctas,
-                    sh->bconv_tc_pipeline, sh->ip_staged_gather, sh->ip_staged_ctas);
+                    "stream ctas %d (1..3), pipeline %d (0, 1), staged gather %d (0, 1), staged ctas %d (1, 2), "
+                    "staged depth %d (0, 2..4)", sh->fuse_ip_moddown, sh->bconv_tc_ctas, sh->ntt_stream_stages,
+                    sh->ntt_stream_ctas, sh->bconv_tc_pipeline, sh->ip_staged_gather, sh->ip_staged_ctas,
+                    sh->ip_staged_depth);
   if (sh->fuse_ip_moddown && c->logn != 16)
     return fhe_fail(FHE_EUNSUPPORTED, "fhe_ctx_set_kernel_shape: the fused inner product needs N = 2^16");
   c->fuse_ip_md = sh->fuse_ip_moddown;
@@ -563,6 +566,7 @@ extern "C" int fhe_ctx_set_kernel_shape(fhe_ctx *c, const fhe_kernel_shape *sh) 
   c->tabs.bconv_tc_pipe = sh->bconv_tc_pipeline;
   c->tabs.ip_staged = sh->ip_staged_gather;
   c->tabs.ip_staged_ctas = sh->ip_staged_ctas;
+  c->tabs.ip_staged_depth = sh->ip_staged_depth;
   return FHE_OK;
 }
 
@@ -575,6 +579,7 @@ extern "C" int fhe_ctx_get_kernel_shape(const fhe_ctx *c, fhe_kernel_shape *out)
   out->bconv_tc_pipeline = c->tabs.bconv_tc_pipe;
   out->ip_staged_gather = c->tabs.ip_staged;
   out->ip_staged_ctas = c->tabs.ip_staged_ctas;
+  out->ip_staged_depth = c->tabs.ip_staged_depth;
   return FHE_OK;
 }
 

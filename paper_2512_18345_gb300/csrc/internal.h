@@ -68,6 +68,7 @@ struct DevTables {
   int bconv_tc_pipe;       // the tensor-core BConv with two accumulators per CTA (MMA beside epilogue)
   int ip_staged;           // hoisted inner product: digits' permuted blocks staged (ip_hoisted.cuh)
   int ip_staged_ctas;      // resident CTAs per SM of that kernel (1 or 2)
+  int ip_staged_depth;     // its stages per warp (2..4; 0: 2)
   int tc_k;                // K of the context's tensor-core BConv tables (48 or 64; 0: none)
 };
 

@@ -242,22 +242,32 @@ cudaError_t launch_ip(const DevTables &t, const SegList &sl, bool gather_own, bo
   TraceScope ts(t, "inner_product", s);
   const bool go = gather_own, ge = gather_ext;
   if (ge && t.ip_staged && !add_c1 && beta_max >= 1 && beta_max <= 4 && (1 << t.logn) % kIpChunk == 0) {
-    // hoisted: every row's permuted 32-coefficient blocks staged in shared memory (ip_hoisted.cuh);
-    // as many stages (up to four) as fit one or two CTAs per SM
+    // hoisted: every row's permuted 32-coefficient blocks staged in shared memory by each warp
+    // for itself (ip_hoisted.cuh): one or two CTAs per SM, each warp with D stages (2..4; by
+    // default 2), as many warps as the shared memory holds (at most 16 per SM)
     const int ctas = std::max(1, std::min(2, t.ip_staged_ctas));
-    const int per_stage = ip_hoisted_stage_words(beta_max) * 4 + 16 + (int)sizeof(IhUnit);
-    const int stages = std::min(4, ((ctas == 2 ? 113 : 227) * 1024 - 256) / per_stage);
-    static PerDeviceOnce configured;
-    const cudaError_t e = configured.run([] {
-      return cudaFuncSetAttribute(k_ip_hoisted, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    const int budget = (ctas == 2 ? 113 : 227) * 1024;
+    const int ws = ip_hoisted_stage_words(beta_max) * 4;  // one stage of one warp
+    int D = t.ip_staged_depth >= 2 && t.ip_staged_depth <= 4 ? t.ip_staged_depth : 2;
+    while (D > 2 && budget / (D * ws) < 1) D--;
+    const int warps = std::max(1, std::min(kIhMaxWarps / ctas, budget / (D * ws)));
+    static PerDeviceOnce configured[3];
+    const cudaError_t e = configured[D - 2].run([D] {
+      constexpr int kMax = 227 * 1024;
+      return D == 2   ? cudaFuncSetAttribute(k_ip_hoisted<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMax)
+             : D == 3 ? cudaFuncSetAttribute(k_ip_hoisted<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMax)
+                      : cudaFuncSetAttribute(k_ip_hoisted<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMax);
     });
     if (e != cudaSuccess) return e;
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int units = sl.total * ((1 << t.logn) / kIpChunk);
-    const unsigned grid = (unsigned)std::min(units, ctas * sms);
-    k_ip_hoisted<<<grid, kIpThreads + 32, stages * per_stage, s>>>(sl, t.pc, t.logn, t.status, beta_max, stages);
+    const int wunits = sl.total * ((1 << t.logn) / kIhUnit);
+    const unsigned grid = (unsigned)std::min((wunits + warps - 1) / warps, ctas * sms);
+    const int smem = warps * D * ws;
+    if (D == 2) k_ip_hoisted<2><<<grid, warps * 32, smem, s>>>(sl, t.pc, t.logn, beta_max);
+    else if (D == 3) k_ip_hoisted<3><<<grid, warps * 32, smem, s>>>(sl, t.pc, t.logn, beta_max);
+    else k_ip_hoisted<4><<<grid, warps * 32, smem, s>>>(sl, t.pc, t.logn, beta_max);
     g_launches++;
     return cudaGetLastError();
   }

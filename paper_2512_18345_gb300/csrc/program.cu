@@ -388,6 +388,24 @@ int run_program_inline(fhe_ctx *c, const Program &P, cudaStream_t s) {
       sl2.total += x.n;
     }
     for (size_t i = 0; i < P.ks.size(); i++) sl.ks[i] = sl2.ks[i] = P.ks[i];
+    if (st.kind == Stage::IP && st.gather_ext) {
+      // the hoisted inner product takes the limbs limb by limb across runs of like segments
+      // (the rotations of a hoisted set, which read the same digit limbs), at most four runs
+      int g = 0;
+      bool ok = true;
+      for (int i = 0; i < sl.nseg && ok; i++) {
+        const bool same = i > 0 && sl.seg[i].n == sl.seg[i - 1].n && sl.seg[i].t0 == sl.seg[i - 1].t0;
+        if (same) {
+          sl.lm_count[g - 1]++;
+        } else if (g < 4) {
+          sl.lm_first[g] = i;
+          sl.lm_count[g++] = 1;
+        } else {
+          ok = false;
+        }
+      }
+      sl.lm_groups = ok ? g : 0;
+    }
     for (const BconvGroup &g : st.groups) ba.g[ba.ngroups++] = g;
     ba.lazy = 1;  // every conversion of a program feeds a forward NTT
     cudaError_t e = launch_stage(c, st, sl, ba, s, 0, &sl2);
@@ -427,15 +445,22 @@ int upload_program(fhe_ctx *c, const Program &P, DevProgram &D) {
     // limb map: transform stages list their limbs grouped by prime (stable), so that the
     // streaming passes' consecutive units share twiddles; the order of limbs within a launch
     // does not change any result, and NTT1's two lists get the same permutation (same
-    // segment sizes and primes)
+    // segment sizes and primes); a hoisted inner product lists its limbs by extended-basis
+    // index (stable), so that the rotations of a hoisted set that read the same digit limbs sit
+    // side by side
     const bool by_prime = st.kind == Stage::NTT || st.kind == Stage::NTT1;
-    auto fill_map = [by_prime](const std::vector<Seg> &segs, int2 *m) {
+    const bool by_limb = st.kind == Stage::IP && st.gather_ext;
+    auto fill_map = [by_prime, by_limb](const std::vector<Seg> &segs, int2 *m) {
       std::vector<int2> v;
       for (size_t sidx = 0; sidx < segs.size(); sidx++)
         for (int w = 0; w < segs[sidx].n; w++) v.push_back(make_int2((int)sidx, w));
       if (by_prime)
         std::stable_sort(v.begin(), v.end(), [&segs](const int2 &a, const int2 &b) {
           return segs[a.x].prime + a.y < segs[b.x].prime + b.y;
+        });
+      if (by_limb)
+        std::stable_sort(v.begin(), v.end(), [&segs](const int2 &a, const int2 &b) {
+          return segs[a.x].t0 + a.y < segs[b.x].t0 + b.y;
         });
       std::copy(v.begin(), v.end(), m);
     };

@@ -160,13 +160,14 @@ def test_kernel_shape_validation(fhe_lib):
     ctx = binding.Context.from_params(P)
     assert ctx.kernel_shape() == {"fuse_ip_moddown": 0, "bconv_tc_ctas": 4, "ntt_stream_stages": 3,
                                   "ntt_stream_ctas": 3, "bconv_tc_pipeline": 0, "ip_staged_gather": 1,
-                                  "ip_staged_ctas": 2}
+                                  "ip_staged_ctas": 2, "ip_staged_depth": 0}
     with pytest.raises(binding.FheError) as e:
         ctx.set_kernel_shape(fuse_ip_moddown=1)  # the fused kernel is 2^16-only
     assert e.value.code == binding.FHE_EUNSUPPORTED
     for bad in ({"bconv_tc_ctas": 0}, {"bconv_tc_ctas": 5}, {"ntt_stream_stages": 1}, {"ntt_stream_ctas": 4},
                 {"fuse_ip_moddown": 2}, {"bconv_tc_pipeline": 2}, {"ip_staged_gather": 2},
-                {"ip_staged_gather": -1}, {"ip_staged_ctas": 0}, {"ip_staged_ctas": 3}):
+                {"ip_staged_gather": -1}, {"ip_staged_ctas": 0}, {"ip_staged_ctas": 3},
+                {"ip_staged_depth": 1}, {"ip_staged_depth": 5}, {"ip_staged_depth": -1}):
         with pytest.raises(binding.FheError) as e:
             ctx.set_kernel_shape(**bad)
         assert e.value.code == binding.FHE_EINVAL
@@ -238,7 +239,8 @@ def test_pipelined_tc_bconv_twelve_limb_digits(fhe_lib):
 
 
 SHAPES_HOISTED = [dict(ip_staged_gather=1, ip_staged_ctas=2), dict(ip_staged_gather=1, ip_staged_ctas=1),
-                  dict(ip_staged_gather=0)]
+                  dict(ip_staged_gather=1, ip_staged_ctas=2, ip_staged_depth=3),
+                  dict(ip_staged_gather=1, ip_staged_ctas=1, ip_staged_depth=4), dict(ip_staged_gather=0)]
 
 
 @pytest.mark.parametrize("staged", range(len(SHAPES_HOISTED)))
