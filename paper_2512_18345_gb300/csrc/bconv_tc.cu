@@ -166,6 +166,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_bconv_tc(const __grid_constan
 
   const size_t N = (size_t)1 << logn;
   const int total = tiles_per_group * a.ngroups;
+  const int ltg = __ffs(tiles_per_group) - 1;  // tiles_per_group = N / 128, a power of two
   const int per_cta = (total + gridDim.x - 1) / gridDim.x;
   const int t0 = blockIdx.x * per_cta, t1 = min(total, t0 + per_cta);
   int cur_group = -1, npad = 0, n_in = 0, n_out = 0;
@@ -187,8 +188,8 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_bconv_tc(const __grid_constan
   bool prefetched = false;  // y holds the current tile's inputs
   bool big_primes = true;   // the current group's output primes all exceed 2^30
   for (int tile = t0; tile < t1 && ok; tile++) {
-    const int grp = tile / tiles_per_group;
-    const size_t n0 = (size_t)(tile % tiles_per_group) * kTcM;
+    const int grp = tile >> ltg;
+    const size_t n0 = (size_t)(tile & (tiles_per_group - 1)) * kTcM;
     if (grp != cur_group) {  // load this group's table and output constants
       cur_group = grp;
       gp = a.dev ? &a.dev[grp] : &a.g[grp];
@@ -229,8 +230,8 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_bconv_tc(const __grid_constan
       }
     }
     // prefetch the next tile's inputs when it belongs to the same group
-    prefetched = tile + 1 < t1 && (tile + 1) / tiles_per_group == grp;
-    if (prefetched) load_inputs(gp, n_in, (size_t)((tile + 1) % tiles_per_group) * kTcM);
+    prefetched = tile + 1 < t1 && ((tile + 1) >> ltg) == grp;
+    if (prefetched) load_inputs(gp, n_in, (size_t)((tile + 1) & (tiles_per_group - 1)) * kTcM);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
     __syncthreads();
@@ -339,6 +340,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_bconv_tc_pipe(const __grid_co
 
   const size_t N = (size_t)1 << logn;
   const int total = tiles_per_group * a.ngroups;
+  const int ltg = __ffs(tiles_per_group) - 1;  // tiles_per_group = N / 128, a power of two
   const int per_cta = (total + gridDim.x - 1) / gridDim.x;
   const int t0 = blockIdx.x * per_cta, t1 = min(total, t0 + per_cta);
   int cur_group = -1, n_in = 0, n_out = 0;
@@ -371,7 +373,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_bconv_tc_pipe(const __grid_co
       return;
     }
     tc_fence_after();
-    const size_t n0 = (size_t)(p % tiles_per_group) * kTcM;
+    const size_t n0 = (size_t)(p & (tiles_per_group - 1)) * kTcM;
     const int q4 = warp & 3;
     const uint32_t n = (uint32_t)(n0 + (size_t)q4 * 32 + (tid & 31));
     const uint32_t tbase = taddr0 + (uint32_t)b * ncols + ((uint32_t)(q4 * 32) << 16);
@@ -382,8 +384,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_bconv_tc_pipe(const __grid_co
     else tc_reduce_outputs<false>(tbase, (warp >> 2) ? H : 0, o_end, sO, gn, big_primes);
   };
   for (int tile = t0; tile < t1 && ok; tile++) {
-    const int grp = tile / tiles_per_group;
-    const size_t n0 = (size_t)(tile % tiles_per_group) * kTcM;
+    const int grp = tile >> ltg;
+    const size_t n0 = (size_t)(tile & (tiles_per_group - 1)) * kTcM;
     if (grp != cur_group) {
       if (pending >= 0) {  // drain: the table and output constants are about to change
         epilogue(pending);
@@ -426,8 +428,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_bconv_tc_pipe(const __grid_co
                        __byte_perm(y1, 0x64006400u, 0x7150), __byte_perm(y1, 0x64006400u, 0x7352));
       }
     }
-    prefetched = tile + 1 < t1 && (tile + 1) / tiles_per_group == grp;
-    if (prefetched) load_inputs(gp, n_in, (size_t)((tile + 1) % tiles_per_group) * kTcM);
+    prefetched = tile + 1 < t1 && ((tile + 1) >> ltg) == grp;
+    if (prefetched) load_inputs(gp, n_in, (size_t)((tile + 1) & (tiles_per_group - 1)) * kTcM);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
     __syncthreads();
