@@ -150,14 +150,24 @@ FHE_API int fhe_ctx_set_pipelining(fhe_ctx *ctx, int on);
  *     of eight consumer warps, which keep their twiddles in registers across
  *     consecutive tiles of the same prime (N = 2^16; the gather, reduce and
  *     rescale forms keep the two-pass kernels).  With FHE_NTT_SINGLE_PASS, the
- *     transforms the single-pass kernel covers use it and the others stream.
+ *     transforms the single-pass kernel covers use it and the others stream;
+ *   FHE_NTT_PERSIST: the transforms the single-pass kernel covers run as one
+ *     persistent, cooperative launch each (every CTA resident): the CTAs walk
+ *     the first pass's tiles, meet at a grid-wide barrier (bounded; an expired
+ *     wait sets status bit 4 and fhe_ctx_sync reports FHE_ETIMEOUT as for
+ *     the other waits), then walk the second pass's tiles; the global round
+ *     trip stays, the second launch's ramp and the first one's tail go
+ *     (N = 2^16; combines with no other flag).
  * Results are identical in every mode.  Programs and plans built after the call
- * use the new mode.  FHE_EUNSUPPORTED for FHE_NTT_STREAM at N != 2^16, for FHE_NTT_SINGLE_PASS at N != 2^16 or on
- * a device that cannot hold a 16-CTA cluster of the kernel; FHE_EINVAL for
- * unknown flags.  fhe_autotune with FHE_TUNE_NTT measures the modes. */
+ * use the new mode.  FHE_EUNSUPPORTED for FHE_NTT_STREAM or FHE_NTT_PERSIST at
+ * N != 2^16, for FHE_NTT_SINGLE_PASS at N != 2^16 or on a device that cannot
+ * hold a 16-CTA cluster of the kernel; FHE_EINVAL for unknown flags and for
+ * FHE_NTT_PERSIST with another flag.  fhe_autotune with FHE_TUNE_NTT measures
+ * the modes. */
 #define FHE_NTT_OTF 1
 #define FHE_NTT_SINGLE_PASS 2
 #define FHE_NTT_STREAM 4
+#define FHE_NTT_PERSIST 8
 FHE_API int fhe_ctx_set_ntt(fhe_ctx *ctx, int flags);
 
 /* Kernel shapes (results are identical for every shape; fhe_autotune with

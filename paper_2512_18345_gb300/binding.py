@@ -26,7 +26,7 @@ FHE_PLAN_GRAPH = 1
 FHE_TUNE_BCONV = 1
 FHE_TUNE_NTT = 2
 FHE_TUNE_SHAPE = 4
-FHE_NTT_OTF, FHE_NTT_SINGLE_PASS, FHE_NTT_STREAM = 1, 2, 4
+FHE_NTT_OTF, FHE_NTT_SINGLE_PASS, FHE_NTT_STREAM, FHE_NTT_PERSIST = 1, 2, 4, 8
 
 # every entry point declared in include/fhe.h
 EXPORTS = (
@@ -319,7 +319,7 @@ class Context:
         check(lib().fhe_ctx_set_memory_limit(self.h, int(nbytes)))
 
     def set_ntt(self, flags: int) -> None:
-        """NTT kernel variants: 0 or FHE_NTT_OTF | FHE_NTT_SINGLE_PASS | FHE_NTT_STREAM flags."""
+        """NTT kernel variants: 0, FHE_NTT_OTF | FHE_NTT_SINGLE_PASS | FHE_NTT_STREAM flags, or FHE_NTT_PERSIST."""
         check(lib().fhe_ctx_set_ntt(self.h, int(flags)))
 
     def kernel_shape(self) -> dict:

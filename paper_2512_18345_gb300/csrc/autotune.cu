@@ -104,7 +104,7 @@ extern "C" int fhe_autotune(fhe_ctx *c, int level, int n_items, int flags, fhe_t
   int rc = FHE_OK, tried = 0;
   const int saved_ip = c->tabs.ip_ctas_per_sm, saved_comp = c->comp_pipe;
   const int saved_ntt = (c->tabs.ntt_otf ? FHE_NTT_OTF : 0) | (c->tabs.ntt_single ? FHE_NTT_SINGLE_PASS : 0) |
-                        (c->tabs.ntt_stream ? FHE_NTT_STREAM : 0);
+                        (c->tabs.ntt_stream ? FHE_NTT_STREAM : 0) | (c->tabs.ntt_persist ? FHE_NTT_PERSIST : 0);
   fhe_kernel_shape saved_shape;
   fhe_ctx_get_kernel_shape(c, &saved_shape);
   fhe_tune_result by_ip[2];  // fastest schedule with one / two inner-product CTAs per SM
@@ -189,7 +189,7 @@ extern "C" int fhe_autotune(fhe_ctx *c, int level, int n_items, int flags, fhe_t
     c->comp_pipe = best.comp_pipe;
     const double base = best.us_per_ks;
     for (int m : {0, FHE_NTT_OTF, FHE_NTT_SINGLE_PASS, FHE_NTT_SINGLE_PASS | FHE_NTT_OTF, FHE_NTT_STREAM,
-                  FHE_NTT_STREAM | FHE_NTT_OTF, FHE_NTT_STREAM | FHE_NTT_SINGLE_PASS}) {
+                  FHE_NTT_STREAM | FHE_NTT_OTF, FHE_NTT_STREAM | FHE_NTT_SINGLE_PASS, FHE_NTT_PERSIST}) {
       if (m == saved_ntt || fhe_ctx_set_ntt(c, m) != FHE_OK) continue;
       fhe_plan *p = nullptr;
       rc = fhe_batch_plan(c, items.data(), n_items, FHE_PLAN_GRAPH, &p);
@@ -339,7 +339,7 @@ static bool tune_parse(const char *rest, const fhe_kernel_shape &dflt, fhe_tune_
       k.bconv_tc_pipeline < 0 || k.bconv_tc_pipeline > 1)
     return false;
   if (t.comp_pipe != 0 && t.comp_pipe != 1) return false;
-  if (t.ntt_mode & ~(FHE_NTT_OTF | FHE_NTT_SINGLE_PASS | FHE_NTT_STREAM)) return false;
+  if (t.ntt_mode & ~(FHE_NTT_OTF | FHE_NTT_SINGLE_PASS | FHE_NTT_STREAM | FHE_NTT_PERSIST)) return false;
   if (t.lanes < 1 || t.lanes > 4 || t.ip_ctas_per_sm < 1 || t.ip_ctas_per_sm > 2 ||
       (t.bconv_mode != FHE_BCONV_SCALAR && t.bconv_mode != FHE_BCONV_TC) || t.max_group < 0)
     return false;

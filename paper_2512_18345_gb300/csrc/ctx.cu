@@ -243,6 +243,8 @@ static int build_tables(fhe_ctx *c) {
                                                           c->tabs.tc_k)));
   CUDA_OR_FAIL(upload(&c->d_status, std::vector<unsigned int>(1, 0u)));
   c->tabs.status = c->d_status;
+  CUDA_OR_FAIL(upload(&c->d_gbar, std::vector<unsigned int>((size_t)fhe::kGbarSlots * 8, 0u)));
+  c->tabs.gbar = c->d_gbar;
 
   // rescale: q_{l-1}^-1 mod q_i for every level l and i < l-1
   std::vector<uint2> rs((size_t)L * L, make_uint2(0, 0));
@@ -263,6 +265,7 @@ static int build_tables(fhe_ctx *c) {
   c->tabs.ntt_otf = 0;
   c->tabs.ntt_single = 0;
   c->tabs.ntt_stream = 0;
+  c->tabs.ntt_persist = 0;
   c->tabs.ntt_stream_stages = 3;
   c->tabs.ntt_stream_ctas = 3;
   c->tabs.bconv_tc_ctas = 4;
@@ -350,6 +353,7 @@ fhe_ctx::~fhe_ctx() {
   cudaFree(d_md_phinv);
   cudaFree(d_pinv);
   cudaFree(d_pmod);
+  cudaFree(d_gbar);
   cudaFree(d_mdT);
   cudaFree(d_mdmap);
   cudaFree(d_rs_qinv);
@@ -529,8 +533,12 @@ extern "C" int fhe_ctx_set_pipelining(fhe_ctx *c, int on) {
 
 extern "C" int fhe_ctx_set_ntt(fhe_ctx *c, int flags) {
   if (!c) return fhe_fail(FHE_EINVAL, "fhe_ctx_set_ntt: null");
-  if (flags & ~(FHE_NTT_OTF | FHE_NTT_SINGLE_PASS | FHE_NTT_STREAM))
+  if (flags & ~(FHE_NTT_OTF | FHE_NTT_SINGLE_PASS | FHE_NTT_STREAM | FHE_NTT_PERSIST))
     return fhe_fail(FHE_EINVAL, "fhe_ctx_set_ntt: flags 0x%x", flags);
+  if ((flags & FHE_NTT_PERSIST) && (flags & (FHE_NTT_OTF | FHE_NTT_SINGLE_PASS | FHE_NTT_STREAM)))
+    return fhe_fail(FHE_EINVAL, "fhe_ctx_set_ntt: FHE_NTT_PERSIST combines with no other flag (0x%x)", flags);
+  if ((flags & FHE_NTT_PERSIST) && c->logn != 16)
+    return fhe_fail(FHE_EUNSUPPORTED, "fhe_ctx_set_ntt: the persistent NTT needs N = 2^16");
   if ((flags & FHE_NTT_STREAM) && c->logn != 16)
     return fhe_fail(FHE_EUNSUPPORTED, "fhe_ctx_set_ntt: the streaming NTT passes need N = 2^16");
   if (flags & FHE_NTT_SINGLE_PASS) {
@@ -542,6 +550,7 @@ extern "C" int fhe_ctx_set_ntt(fhe_ctx *c, int flags) {
   c->tabs.ntt_otf = (flags & FHE_NTT_OTF) ? 1 : 0;
   c->tabs.ntt_single = (flags & FHE_NTT_SINGLE_PASS) ? 1 : 0;
   c->tabs.ntt_stream = (flags & FHE_NTT_STREAM) ? 1 : 0;
+  c->tabs.ntt_persist = (flags & FHE_NTT_PERSIST) ? 1 : 0;
   return FHE_OK;
 }
 

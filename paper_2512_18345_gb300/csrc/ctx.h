@@ -34,6 +34,7 @@ struct fhe_ctx {
   uint32_t *d_mdT = nullptr;                           // [L][K] (P/p_k) mod q_i
   int2 *d_mdmap = nullptr;                             // [L] (i, i)
   uint16_t *d_md_Btc = nullptr;
+  unsigned int *d_gbar = nullptr;                      // grid-barrier counters of the persistent NTT
   uint2 *d_pmod = nullptr;                             // [L] Shoup pairs of P mod q_i                        // tensor-core table of the ModDown conversion
   unsigned int *d_status = nullptr;                    // device status word (expired waits)
   uint2 *d_rs_qinv = nullptr;                          // [L][L]

@@ -50,6 +50,8 @@ struct Tracer {
   ~Tracer();
 };
 
+constexpr int kGbarSlots = 1024;  // grid-barrier counters of the persistent NTT per context
+
 struct DevTables {
   NttTables ntt;
   const PrimeC *pc;
@@ -57,11 +59,14 @@ struct DevTables {
   Tracer *tracer;          // null: no tracing
   unsigned int *status;    // device word, nonzero once a bounded device-side wait expired: bit 0
                            // tensor-core BConv, bit 1 inner product, bit 2 diagonal pass,
+                           // bit 3 streaming NTT, bit 4 persistent NTT's grid barrier,
                            // bit 7 the wait self-test
+  unsigned int *gbar;      // kGbarSlots grid-barrier counters (8 words apart) of the persistent NTT
   int ip_ctas_per_sm;      // resident CTAs per SM of the streaming inner product (1 or 2; autotuned)
   int ntt_otf;             // block passes form their register twiddles on the fly
   int ntt_single;          // 2^16-point transforms in one cluster launch instead of two passes
   int ntt_stream;          // the passes as persistent kernels fed by a producer warp (ntt_bulk.cuh)
+  int ntt_persist;         // both passes of a transform in one cooperative launch (k_nttp)
   int ntt_stream_stages;   // shared-memory stages per CTA of those kernels
   int ntt_stream_ctas;     // persistent CTAs per SM of those kernels (1..3)
   int bconv_tc_ctas;       // resident CTAs per SM of the tensor-core BConv (1..4)

@@ -182,8 +182,56 @@ bool ntt_single_pass_ok(const DevTables &t, int pro, int epi, bool fwd) {
   return (pro == PRO_PLAIN || pro == PRO_GATHER) && epi == EPI_SCALE;
 }
 
+// grid-barrier counters of the persistent transform: each launch takes the next slot (one
+// 32-byte sector each) and zeroes it on its stream first; two launches share a slot only
+// with kGbarSlots launches between them, none of which may still be running
+static std::atomic<unsigned> g_gbar_next{0};
+
+template <bool FWD, int PRO, int EPI>
+static cudaError_t nttp_go(const DevTables &t, const SegList &first, const SegList &second, cudaStream_t s) {
+  const int units = first.total * 16;
+  if (units == 0) return cudaSuccess;
+  if (!t.gbar) return cudaErrorInvalidValue;
+  constexpr int smem = ntt_twiddle_smem(true, 256);  // the larger of the two passes' tables
+  auto kern = k_nttp<FWD, PRO, EPI>;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNttThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const unsigned grid = (unsigned)std::min(units, per_sm * sms);  // every CTA resident at once
+  unsigned int *ctr = t.gbar + 8 * (g_gbar_next.fetch_add(1) % kGbarSlots);
+  if ((e = cudaMemsetAsync(ctr, 0, sizeof(unsigned int), s)) != cudaSuccess) return e;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeCooperative;
+  attr.val.cooperative = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kNttThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  TraceScope ts(t, FWD ? "nttp" : "inttp", s);
+  e = cudaLaunchKernelEx(&cfg, kern, first, second, t.ntt, ctr, t.status);
+  g_launches++;
+  return e;
+}
+
 cudaError_t launch_ntt_single(const DevTables &t, bool fwd, int pro, int epi, const SegList &first,
                               const SegList &second, cudaStream_t s) {
+  if (t.ntt_persist) {
+#define NTTP_CASE(FWDV, P, E) \
+  if (fwd == FWDV && pro == P && epi == E) return nttp_go<FWDV, P, E>(t, first, second, s);
+    NTTP_CASE(true, PRO_PLAIN, EPI_PLAIN)
+    NTTP_CASE(true, PRO_PLAIN, EPI_COMBINE)
+    NTTP_CASE(true, PRO_REDUCE, EPI_RESCALE)
+    NTTP_CASE(false, PRO_PLAIN, EPI_SCALE)
+    NTTP_CASE(false, PRO_GATHER, EPI_SCALE)
+#undef NTTP_CASE
+    return cudaErrorInvalidValue;
+  }
   const bool otf = t.ntt_otf != 0;
 #define NTT1_CASE(FWDV, P, E)                                                  \
   if (fwd == FWDV && pro == P && epi == E)                                     \
@@ -206,7 +254,7 @@ static bool same_limbs(const SegList &a, const SegList &b) {
 
 cudaError_t launch_ntt(const DevTables &t, bool fwd, int pro, int epi, const SegList &first, const SegList &second,
                        cudaStream_t s) {
-  if (t.ntt_single && ntt_single_pass_ok(t, pro, epi, fwd) && same_limbs(first, second))
+  if ((t.ntt_single || t.ntt_persist) && ntt_single_pass_ok(t, pro, epi, fwd) && same_limbs(first, second))
     return launch_ntt_single(t, fwd, pro, epi, first, second, s);
   cudaError_t e;
   if (fwd) {

@@ -412,4 +412,63 @@ __global__ void __cluster_dims__(16, 1, 1) __launch_bounds__(kNttThreads)
   cluster_wait();
 }
 
+// Grid-wide barrier of a cooperative launch (every CTA resident): thread 0 of each CTA
+// arrives on the launch's own zeroed counter and waits, bounded, until every CTA has; false
+// when the wait expired.  Writes before the barrier are visible to every CTA after it.
+__device__ __forceinline__ bool grid_barrier_bounded(unsigned int *ctr, unsigned int nblocks) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(ctr, 1u);
+    int ok = 0;
+    for (uint32_t it = 0; it < (1u << 22) && !ok; it++) {
+      unsigned int v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+      if (v >= nblocks) ok = 1;
+      else __nanosleep(64);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Both passes of a 2^16-point transform in one persistent, cooperative launch (a
+// measured alternative to the two launches and to the cluster kernel): the CTAs walk the
+// first pass's tiles exactly as the first launch's blocks would, meet at a grid-wide
+// barrier, then walk the second pass's tiles.  The passes, their segments and their
+// global round trip are the two-launch form's, so the results are identical; what goes is
+// the second launch's ramp and the first one's tail.  An expired barrier sets status bit 4
+// and skips the second pass.
+template <bool FWD, int PRO, int EPI>
+__global__ void __launch_bounds__(kNttThreads)
+    k_nttp(const __grid_constant__ SegList first, const __grid_constant__ SegList second, const NttTables tb,
+           unsigned int *ctr, unsigned int *status) {
+  constexpr int LOGN = 16;
+  using GB = NttGeom<LOGN, false>;
+  __shared__ uint32_t sm[GB::SMEM];  // both passes' tile (R = 8 on both sides at N = 2^16)
+  extern __shared__ uint2 tws[];     // the larger of the two passes' staged twiddles
+  const int units = first.total * 16;
+  for (int u = blockIdx.x; u < units; u += gridDim.x) {
+    int w;
+    const Seg &sg = seg_at(first, seg_find(first, u >> 4, w));
+    ntt_pass<LOGN, FWD, FWD, PRO, EPI_LAZY, false, SRC_GLOBAL, DST_GLOBAL>(sg, item_ks(first, sg), w, sg.prime + w, tb,
+                                                                         u & 15, sm, tws, nullptr);
+    __syncthreads();  // the tile and the staged twiddles are reused by the next unit
+  }
+  if (!grid_barrier_bounded(ctr, gridDim.x)) {
+    if (threadIdx.x == 0) atomicOr(status, 16u);
+    return;
+  }
+  for (int u = blockIdx.x; u < units; u += gridDim.x) {
+    int w;
+    const Seg &sg = seg_at(second, seg_find(second, u >> 4, w));
+    ntt_pass<LOGN, !FWD, FWD, PRO_PLAIN, EPI, false, SRC_GLOBAL, DST_GLOBAL>(sg, item_ks(second, sg), w, sg.prime + w,
+                                                                           tb, u & 15, sm, tws, nullptr);
+    __syncthreads();
+  }
+}
+
 }  // namespace fhe

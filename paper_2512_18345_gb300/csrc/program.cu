@@ -52,7 +52,7 @@ static Stage marker(Stage::Kind k) {
 // the two passes of one transform: one single-pass cluster stage when the context asks for
 // it and the kernel exists for the pair's prologue and epilogue, else two stages
 static void push_transform(fhe_ctx *c, Program &P, const Stage &first, const Stage &second) {
-  if (c->tabs.ntt_single && fhe::ntt_single_pass_ok(c->tabs, first.pro, second.epi, first.fwd)) {
+  if ((c->tabs.ntt_single || c->tabs.ntt_persist) && fhe::ntt_single_pass_ok(c->tabs, first.pro, second.epi, first.fwd)) {
     Stage f = first;
     f.kind = Stage::NTT1;
     f.epi = second.epi;
@@ -318,7 +318,7 @@ int build_program(fhe_ctx *c, const std::vector<Item> &items, bool fused, Progra
     }
     if (!fused) P.stages.push_back(msc);
     P.stages.push_back(mbc);
-    if (c->tabs.ntt_single && fhe::ntt_single_pass_ok(c->tabs, r1.pro, r2.epi, true)) {
+    if ((c->tabs.ntt_single || c->tabs.ntt_persist) && fhe::ntt_single_pass_ok(c->tabs, r1.pro, r2.epi, true)) {
       // the single-pass transform reads u's q-limbs in its epilogue: join before it
       if (split) P.stages.push_back(marker(Stage::JOIN_WAIT));
       push_transform(c, P, r1, r2);

@@ -1,5 +1,6 @@
 """NTT kernel variants (fhe_ctx_set_ntt): on-the-fly register twiddles in the
-block passes, the single-pass cluster transform and the streaming passes.  Every mode must give the
+block passes, the single-pass cluster transform, the streaming passes and the
+persistent cooperative two-pass transform.  Every mode must give the
 oracle's residues bit for bit: the stage entry points, a batched graph plan of
 mixed key switches, hoisted rotations, HMult + rescale and the double-hoisted
 transform."""
@@ -12,8 +13,9 @@ from paper_2512_18345_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-# 0, FHE_NTT_OTF, FHE_NTT_SINGLE_PASS, both; FHE_NTT_STREAM alone, with OTF, with SINGLE_PASS
-MODES = [0, 1, 2, 3, 4, 5, 6]
+# 0, FHE_NTT_OTF, FHE_NTT_SINGLE_PASS, both; FHE_NTT_STREAM alone, with OTF, with SINGLE_PASS;
+# FHE_NTT_PERSIST
+MODES = [0, 1, 2, 3, 4, 5, 6, 8]
 
 
 def dev(a):
@@ -119,7 +121,7 @@ def test_single_ops_each_mode(big, mode, fused):
     ctx.set_ntt(0)
 
 
-@pytest.mark.parametrize("mode", [1, 2, 3, 4, 6])
+@pytest.mark.parametrize("mode", [1, 2, 3, 4, 6, 8])
 def test_double_hoisted_level_each_mode(fhe_lib, mode):
     from paper_2512_18345_gb300 import binding
     name = "cts_stc_N65536_L48_a12"
@@ -155,7 +157,10 @@ def test_small_ring_modes(fhe_lib):
         ctx.set_ntt(binding.FHE_NTT_STREAM)
     assert e.value.code == binding.FHE_EUNSUPPORTED
     with pytest.raises(binding.FheError) as e:
-        ctx.set_ntt(8)
+        ctx.set_ntt(binding.FHE_NTT_PERSIST)
+    assert e.value.code == binding.FHE_EUNSUPPORTED
+    with pytest.raises(binding.FheError) as e:
+        ctx.set_ntt(16)
     assert e.value.code == binding.FHE_EINVAL
     ctx.set_ntt(binding.FHE_NTT_OTF)
     g = inputs.rng(1900)
@@ -203,3 +208,40 @@ def test_streaming_passes_ragged_unit_counts(big, n_limbs):
     assert np.array_equal(got[0][0], got[binding.FHE_NTT_STREAM][0])
     assert np.array_equal(got[binding.FHE_NTT_STREAM][0], oracle.ntt(a, primes))
     assert np.array_equal(got[binding.FHE_NTT_STREAM][1], a)
+
+
+def test_persistent_transform_rejects_other_flags(big):
+    from paper_2512_18345_gb300 import binding
+    P, OP, ctx = big
+    for other in (binding.FHE_NTT_OTF, binding.FHE_NTT_SINGLE_PASS, binding.FHE_NTT_STREAM):
+        with pytest.raises(binding.FheError) as e:
+            ctx.set_ntt(binding.FHE_NTT_PERSIST | other)
+        assert e.value.code == binding.FHE_EINVAL
+
+
+@pytest.mark.parametrize("n_limbs", [1, 7, 33, 130, 400])
+def test_persistent_transform_unit_counts(big, n_limbs):
+    """The persistent two-pass transform with fewer tiles than resident CTAs (1 limb: 16 tiles),
+    counts that do not divide among them and more limbs than one wave holds (400 limbs, 6400
+    tiles per pass), repeated primes and all-(q - 1) limbs: equal to the oracle and to the
+    two-pass kernels, forward and inverse, with no expired grid barrier."""
+    from paper_2512_18345_gb300 import binding
+    P, OP, ctx = big
+    g = inputs.rng(2300 + n_limbs)
+    idx = [(5 * i) % len(P.primes) for i in range(n_limbs)]
+    primes = [P.primes[i] for i in idx]
+    a = np.stack([inputs.uniform_residues(g, [p], P.N)[0] for p in primes])
+    a[-1] = primes[-1] - 1
+    got = {}
+    for mode in (0, binding.FHE_NTT_PERSIST):
+        ctx.set_ntt(mode)
+        t = dev(a)
+        ctx.ntt(t, idx)
+        f = host(ctx, t)
+        ctx.intt(t, idx)
+        got[mode] = (f, host(ctx, t))
+    ctx.set_ntt(0)
+    assert np.array_equal(got[binding.FHE_NTT_PERSIST][0], got[0][0])
+    assert np.array_equal(got[binding.FHE_NTT_PERSIST][1], a)
+    if n_limbs <= 33:
+        assert np.array_equal(got[0][0], oracle.ntt(a, primes))
