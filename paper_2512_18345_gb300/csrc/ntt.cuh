@@ -266,12 +266,29 @@ __device__ __forceinline__ void ntt_pass(const Seg &sg, const KsArgs &ks, int wi
         const int sig = 7 - kbit;    // stage within the pass; local index (c << sig) + (k_lo >> (kbit + 1))
         base = 16 * ((1 << sig) - 1) + (c << sig);  // hi round only (sig < 4)
       }
+      // the stage's 2^(3 - bit) staged twiddles are consecutive from an even base: fetch them
+      // in 16-byte pairs (the block pass's lo round uses its register twiddles instead)
+      constexpr int kMaxTw = 8;
+      uint2 ws[kMaxTw];
+      if (COLUMN || hi) {
+        const int cnt = 1 << (3 - bit);
+        if (cnt == 1) {
+          ws[0] = tws[base];
+        } else {
+#pragma unroll
+          for (int k2 = 0; k2 < cnt / 2; k2++) {
+            const uint4 w = *reinterpret_cast<const uint4 *>(tws + base + 2 * k2);
+            ws[2 * k2] = make_uint2(w.x, w.y);
+            ws[2 * k2 + 1] = make_uint2(w.z, w.w);
+          }
+        }
+      }
 #pragma unroll
       for (int e = 0; e < 16; e++) {
         if (e & (1 << bit)) continue;
         const int e2 = e | (1 << bit);
         // block pass lo round: register twiddle tl[2^m - 1 + (e >> (bit + 1))], m = 3 - bit
-        const uint2 W = (!COLUMN && !hi) ? tl[(1 << (3 - bit)) - 1 + (e >> (bit + 1))] : tws[base + (e >> (bit + 1))];
+        const uint2 W = (!COLUMN && !hi) ? tl[(1 << (3 - bit)) - 1 + (e >> (bit + 1))] : ws[e >> (bit + 1)];
         if (FWD) {
           const uint32_t t = red2(shoup_lazy(x[e2], W.x, W.y, q), q);
           const uint32_t u = red2(x[e], q);
@@ -369,7 +386,7 @@ __global__ void __launch_bounds__(kNttThreads, ntt_min_blocks<COLUMN, FWD, PRO, 
   // by all columns); the block pass needs, per stage sigma of its 8, the 16 2^sigma
   // twiddles of its 16 blocks, stored at 16 (2^sigma - 1).
   __shared__ uint32_t sm[R == 8 ? G::SMEM : 1];
-  extern __shared__ uint2 tws[];  // dynamic: ntt_twiddle_smem(COLUMN, S) bytes (+ the small table)
+  extern __shared__ __align__(16) uint2 tws[];  // dynamic: ntt_twiddle_smem(COLUMN, S) bytes (+ the small table)
 
   const int v = blockIdx.x / G::TILES, tile = blockIdx.x % G::TILES;
   int within;
@@ -393,7 +410,7 @@ __global__ void __cluster_dims__(16, 1, 1) __launch_bounds__(kNttThreads)
   using GB = NttGeom<LOGN, false>;
   __shared__ uint32_t sm[GB::SMEM];
   __shared__ uint32_t xfer[kTile];
-  extern __shared__ uint2 tws[];  // the larger of the two passes' staged twiddles
+  extern __shared__ __align__(16) uint2 tws[];  // the larger of the two passes' staged twiddles
   const int v = blockIdx.x / 16, tile = blockIdx.x % 16;
   int w1, w2;
   const Seg &s1 = seg_at(first, seg_find(first, v, w1));
@@ -449,7 +466,7 @@ __global__ void __launch_bounds__(kNttThreads)
   constexpr int LOGN = 16;
   using GB = NttGeom<LOGN, false>;
   __shared__ uint32_t sm[GB::SMEM];  // both passes' tile (R = 8 on both sides at N = 2^16)
-  extern __shared__ uint2 tws[];     // the larger of the two passes' staged twiddles
+  extern __shared__ __align__(16) uint2 tws[];     // the larger of the two passes' staged twiddles
   const int units = first.total * 16;
   for (int u = blockIdx.x; u < units; u += gridDim.x) {
     int w;
