@@ -67,8 +67,8 @@ struct IhLimb {
   bool mixed;              // some row in use is read through another element than gal[0]
 };
 
-// limb v of the launch: in the list's limb-major order when it has one (a device list's limb
-// map is already sorted by extended-basis index)
+// limb v of the launch: in the list's limb-major order when it has one (hoisted sets run as
+// single operations, whose lists are passed by value)
 __device__ __forceinline__ int ih_find(const SegList &sl, int v, int &within) {
   if (sl.lm_groups) {
     for (int g = 0; g < sl.lm_groups; g++) {

@@ -445,22 +445,15 @@ int upload_program(fhe_ctx *c, const Program &P, DevProgram &D) {
     // limb map: transform stages list their limbs grouped by prime (stable), so that the
     // streaming passes' consecutive units share twiddles; the order of limbs within a launch
     // does not change any result, and NTT1's two lists get the same permutation (same
-    // segment sizes and primes); a hoisted inner product lists its limbs by extended-basis
-    // index (stable), so that the rotations of a hoisted set that read the same digit limbs sit
-    // side by side
+    // segment sizes and primes)
     const bool by_prime = st.kind == Stage::NTT || st.kind == Stage::NTT1;
-    const bool by_limb = st.kind == Stage::IP && st.gather_ext;
-    auto fill_map = [by_prime, by_limb](const std::vector<Seg> &segs, int2 *m) {
+    auto fill_map = [by_prime](const std::vector<Seg> &segs, int2 *m) {
       std::vector<int2> v;
       for (size_t sidx = 0; sidx < segs.size(); sidx++)
         for (int w = 0; w < segs[sidx].n; w++) v.push_back(make_int2((int)sidx, w));
       if (by_prime)
         std::stable_sort(v.begin(), v.end(), [&segs](const int2 &a, const int2 &b) {
           return segs[a.x].prime + a.y < segs[b.x].prime + b.y;
-        });
-      if (by_limb)
-        std::stable_sort(v.begin(), v.end(), [&segs](const int2 &a, const int2 &b) {
-          return segs[a.x].t0 + a.y < segs[b.x].t0 + b.y;
         });
       std::copy(v.begin(), v.end(), m);
     };
