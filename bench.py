@@ -880,16 +880,19 @@ def main():
     # --- e2e: every step copies its inputs from pinned host memory and its results back,
     # inside the timed region, through the same public API.  Steps alternate between two
     # device buffer sets (each with its own plan), so the copies of neighbouring steps run
-    # on their own streams beside the current step's key switches.
-    h_in = [torch.from_numpy(c.view(np.int32)).pin_memory() for c in cts_np]
-    h_out = [torch.empty((2, level, P.N), dtype=torch.int32).pin_memory() for _ in range(B)]
-    sets = [(cts, outs, plan)]
-    cts1 = [binding.empty((2, level, P.N), dev) for _ in range(B)]
-    outs1 = [binding.empty((2, level, P.N), dev) for _ in range(B)]
-    items1 = [dict(op=binding.FHE_OP_ROTATE, level=level, rot=r, **{"in": c}, out=o)
-              for r, c, o in zip(rots, cts1, outs1)]
-    plan1 = ctx.batch_plan(items1, binding.FHE_PLAN_GRAPH)
-    sets.append((cts1, outs1, plan1))
+    # on their own streams beside the current step's key switches.  A step's ciphertexts sit
+    # in one contiguous buffer on each side (the items point into it), so each direction is
+    # one copy: the host link runs at about 170 GB/s each way for one large copy per
+    # direction, 158 GB/s for one copy per ciphertext.
+    h_in = torch.from_numpy(np.stack(cts_np).view(np.int32)).pin_memory()  # [B][2][level][N]
+    h_out = torch.empty((B, 2, level, P.N), dtype=torch.int32).pin_memory()
+    sets = []
+    for _ in range(2):
+        d_in = torch.empty((B, 2, level, P.N), dtype=torch.int32, device=f"cuda:{dev}")
+        d_out = torch.empty_like(d_in)
+        items_e = [dict(op=binding.FHE_OP_ROTATE, level=level, rot=r, **{"in": d_in[i]}, out=d_out[i])
+                   for i, r in enumerate(rots)]
+        sets.append((d_in, d_out, ctx.batch_plan(items_e, binding.FHE_PLAN_GRAPH)))
     s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
     ev_in = [torch.cuda.Event() for _ in range(2)]
     ev_done = [torch.cuda.Event() for _ in range(2)]
@@ -905,8 +908,7 @@ def main():
         d_in, d_out, pl = sets[k]
         with torch.cuda.stream(s_in):
             s_in.wait_event(ev_done[k])  # the set's previous step has read its inputs
-            for hi, di in zip(h_in, d_in):
-                di.copy_(hi, non_blocking=True)
+            d_in.copy_(h_in, non_blocking=True)
             ev_in[k].record(s_in)
         stream.wait_event(ev_in[k])
         stream.wait_event(ev_back[k])  # the set's previous results have been read back
@@ -914,8 +916,7 @@ def main():
         ev_done[k].record(stream)
         with torch.cuda.stream(s_out):
             s_out.wait_event(ev_done[k])
-            for ho, do in zip(h_out, d_out):
-                ho.copy_(do, non_blocking=True)
+            h_out.copy_(d_out, non_blocking=True)
             ev_back[k].record(s_out)
         if step_no[0] in join_at:  # close the warm-up and the timed region on the main stream
             stream.wait_event(ev_back[0])
@@ -934,12 +935,10 @@ def main():
     bytes_io = B * 2 * level * P.N * 4
 
     def h2d():
-        for hi, di in zip(h_in, cts1):
-            di.copy_(hi, non_blocking=True)
+        sets[1][0].copy_(h_in, non_blocking=True)
 
     def d2h():
-        for ho, do in zip(h_out, outs1):
-            ho.copy_(do, non_blocking=True)
+        h_out.copy_(sets[1][1], non_blocking=True)
 
     link = {"h2d_gbs": link_gbs(h2d), "d2h_gbs": link_gbs(d2h)}
 
@@ -958,9 +957,12 @@ def main():
         e2e_step()
     ms_e2e = timed(e2e_step, e2e_steps)
     torch.cuda.synchronize()
-    # the results read back equal both buffer sets' device results (same inputs and keys)
-    e2e_ok = all(torch.equal(ho, do.cpu()) and torch.equal(ho, d1.cpu()) for ho, do, d1 in zip(h_out, outs, outs1))
-    plan1.close()
+    # the results read back equal the headline plan's device results (same inputs and keys)
+    # and both buffer sets'
+    e2e_ok = all(torch.equal(h_out[i], outs[i].cpu()) for i in range(B)) and \
+        all(torch.equal(h_out, s[1].cpu()) for s in sets)
+    for s in sets:
+        s[2].close()
     e2e_val = job_throughput(B * e2e_steps, ws, ms_e2e)
 
     # --- the fourth and fifth workloads (reported beside the headline)
