@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kIhMaxWarps * 32, 1)
   const int n = my_runs ? (my_runs - 1) * kIhRun + min(kIhRun, total - (gw + (my_runs - 1) * nw) * kIhRun) : 0;
   // keys are read exactly once: evict them first, so that the digits, shared by every rotation
   // of the hoisted set, stay in L2
-  const uint64_t key_policy = l2_evict_first_policy(), digit_policy = l2_evict_last_policy();
+  const uint64_t key_policy = l2_evict_first_policy();
   const int eb = l >> 3, part = l & 7;               // staging: this lane's block and 16-byte piece
   const uint32_t pw = (uint32_t)(eb * 32 + 4 * part);  // that piece's word within a staged row
 
@@ -161,8 +161,7 @@ __global__ void __launch_bounds__(kIhMaxWarps * 32, 1)
         uint32_t sb = sb0;
         if (is.mixed) sb = galois_src(jb, is.gal[r], logn) >> 5;  // uniform over the warp
         const int slot = r < 4 ? r : beta_max;  // the pass-through row follows beta_max digit rows
-        cp_async16_hint(dbase + (uint32_t)(slot * kIhUnit + pw) * 4u, srow + ((size_t)sb << 5) + 4 * part,
-                        digit_policy);
+        cp_async_plain16(dbase + (uint32_t)(slot * kIhUnit + pw) * 4u, srow + ((size_t)sb << 5) + 4 * part);
       }
       const uint32_t *kp = is.key + c0 + pw;
 #pragma unroll
