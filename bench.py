@@ -374,6 +374,19 @@ def bench_bootstrap_lt(binding, inputs, dev, timed, hbm_peak, only=None, runs=0)
         mac_bytes = sum((pl.n_diag + 2 * len(pl.baby) * -(-len(pl.giant) // 4) + 2 * len(pl.giant)) *
                         (lv + P.K) * P.N * 4 for pl, lv in zip(plans, levels))
         mac_ms = stats.get("diag_mac", (0, 0.0))[1]
+        # the hoisted inner products' algorithmic bytes: per rotating baby step its key and its u
+        # over the extended basis, the shared digit set and pass-through once per level; per
+        # rotating giant step its key, its own digit set and its u
+        ip_words = 0
+        for pl, lv in zip(plans, levels):
+            beta, ext = P.beta(lv), lv + P.K
+            nb = sum(1 for r in pl.baby if r % (P.N // 2))
+            ng = sum(1 for r in pl.giant if r % (P.N // 2))
+            if nb:
+                ip_words += nb * (2 * beta + 2) * ext + beta * ext + lv
+            ip_words += ng * (3 * beta + 2) * ext
+        ip_bytes = ip_words * P.N * 4
+        ip_ms = stats.get("inner_product", (0, 0.0))[1]
         res[kind] = {
             "ms": ms, "levels": levels, "key_switches": n_ks, "ks_per_s": n_ks / (ms / 1e3),
             "diagonals": [pl.n_diag for pl in plans], "baby_giant": [[len(pl.baby), len(pl.giant)] for pl in plans],
@@ -381,6 +394,9 @@ def bench_bootstrap_lt(binding, inputs, dev, timed, hbm_peak, only=None, runs=0)
             "diag_mac": {"bytes": mac_bytes, "ms_traced": mac_ms,
                          "gbs": mac_bytes / (mac_ms / 1e3) / 1e9 if mac_ms else None,
                          "frac_of_measured_hbm": (mac_bytes / (mac_ms / 1e3) / 1e9) / hbm_peak if mac_ms else None},
+            "inner_product": {"bytes": ip_bytes, "ms_traced": ip_ms,
+                              "gbs": ip_bytes / (ip_ms / 1e3) / 1e9 if ip_ms else None,
+                              "frac_of_measured_hbm": (ip_bytes / (ip_ms / 1e3) / 1e9) / hbm_peak if ip_ms else None},
             "kernels_ms": {k2: round(v[1], 4) for k2, v in sorted(stats.items(), key=lambda kv: -kv[1][1])}}
         del pts, outs, resc
     ctx.close()
