@@ -262,27 +262,38 @@ struct GsumArgs {
   uint32_t *out;                     // [2][nlimb][N]
   int count, nlimb, level, L;
 };
+// Four consecutive coefficients per thread: 16-byte loads and stores for every operand but
+// the sigma-gathered c0 halves.
+constexpr int kGsumEpt = 4;
 __global__ void __launch_bounds__(256) k_gsum(const __grid_constant__ GsumArgs a, const PrimeC *pc, int logn) {
   const size_t N = (size_t)1 << logn;
-  const int per_limb = (int)(N / 256);
+  const int per_limb = (int)(N / (256 * kGsumEpt));
   const int i = blockIdx.x / per_limb;
-  const uint32_t n = (uint32_t)((blockIdx.x % per_limb) * 256 + threadIdx.x);
+  const uint32_t n = (uint32_t)((blockIdx.x % per_limb) * (256 * kGsumEpt) + threadIdx.x * kGsumEpt);
   const uint32_t q = pc[limb_prime(i, a.level, a.L)].q;
   const size_t poly = (size_t)a.nlimb * N, off = (size_t)i * N;
-  uint32_t a0 = 0, a1 = 0;
+  uint32_t a0[kGsumEpt] = {}, a1[kGsumEpt] = {};
+  auto add4 = [&](uint32_t (&acc)[kGsumEpt], const uint32_t *p) {
+    const uint4 w = __ldg(reinterpret_cast<const uint4 *>(p));
+    acc[0] = add_mod(acc[0], w.x, q);
+    acc[1] = add_mod(acc[1], w.y, q);
+    acc[2] = add_mod(acc[2], w.z, q);
+    acc[3] = add_mod(acc[3], w.w, q);
+  };
   for (int g = 0; g < a.count; g++) {
     const uint32_t *in = a.inner[g] + off;
     if (!a.v[g]) {
-      a0 = add_mod(a0, __ldg(in + n), q);
-      a1 = add_mod(a1, __ldg(in + poly + n), q);
+      add4(a0, in + n);
+      add4(a1, in + poly + n);
     } else {
-      a0 = add_mod(a0, __ldg(in + galois_src(n, a.galois[g], logn)), q);
-      a0 = add_mod(a0, __ldg(a.v[g] + off + n), q);
-      a1 = add_mod(a1, __ldg(a.v[g] + poly + off + n), q);
+#pragma unroll
+      for (int e = 0; e < kGsumEpt; e++) a0[e] = add_mod(a0[e], __ldg(in + galois_src(n + e, a.galois[g], logn)), q);
+      add4(a0, a.v[g] + off + n);
+      add4(a1, a.v[g] + poly + off + n);
     }
   }
-  a.out[off + n] = a0;
-  a.out[poly + off + n] = a1;
+  *reinterpret_cast<uint4 *>(a.out + off + n) = make_uint4(a0[0], a0[1], a0[2], a0[3]);
+  *reinterpret_cast<uint4 *>(a.out + poly + off + n) = make_uint4(a1[0], a1[1], a1[2], a1[3]);
 }
 
 // out[c][i][n] = sum_{g < count} in_g[c][i][n] mod q_i (the giant-step outputs), one thread
@@ -581,7 +592,7 @@ extern "C" int fhe_linear_transform_dh(fhe_ctx *c, const uint32_t *ct, int level
   ga.L = c->L;
   {
     TraceScope ts(c->tabs, "lt_gsum", s);
-    k_gsum<<<grid_x, 256, 0, s>>>(ga, c->d_pc, c->logn);
+    k_gsum<<<grid_x / kGsumEpt, 256, 0, s>>>(ga, c->d_pc, c->logn);
     note_launch();
     if (cudaGetLastError() != cudaSuccess) return fhe_fail(FHE_ECUDA, "%s: giant-step sum kernel", fn);
   }
