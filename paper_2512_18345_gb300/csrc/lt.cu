@@ -240,14 +240,19 @@ static cudaError_t launch_diag(fhe_ctx *c, const DiagArgs &da, cudaStream_t s) {
 __global__ void __launch_bounds__(256) k_lift(const uint32_t *ct, uint32_t *out, const uint2 *pmod, const PrimeC *pc,
                                               int level, int nlimb, int logn) {
   const size_t N = (size_t)1 << logn;
-  const int per_limb = (int)(N / 256);
+  const int per_limb = (int)(N / 1024);  // four consecutive coefficients per thread
   const int i = blockIdx.x / per_limb;
-  const size_t n = (size_t)(blockIdx.x % per_limb) * 256 + threadIdx.x;
+  const size_t n = (size_t)(blockIdx.x % per_limb) * 1024 + threadIdx.x * 4;
 #pragma unroll
   for (int c = 0; c < 2; c++) {
-    uint32_t v = 0;
-    if (i < level) v = shoup(__ldg(ct + ((size_t)c * level + i) * N + n), pmod[i], pc[i].q);
-    out[((size_t)c * nlimb + i) * N + n] = v;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (i < level) {
+      const uint4 x = __ldg(reinterpret_cast<const uint4 *>(ct + ((size_t)c * level + i) * N + n));
+      const uint2 pm = pmod[i];
+      const uint32_t q = pc[i].q;
+      v = make_uint4(shoup(x.x, pm, q), shoup(x.y, pm, q), shoup(x.z, pm, q), shoup(x.w, pm, q));
+    }
+    *reinterpret_cast<uint4 *>(out + ((size_t)c * nlimb + i) * N + n) = v;
   }
 }
 
@@ -492,7 +497,7 @@ extern "C" int fhe_linear_transform_dh(fhe_ctx *c, const uint32_t *ct, int level
   for (int b = 0; b < n_baby; b++) {
     if (gb[b] == 1u) {
       TraceScope ts(c->tabs, "lt_lift", s);
-      k_lift<<<grid_x, 256, 0, s>>>(ct, bab + b * xct, c->d_pmod, c->d_pc, level, n_ext, c->logn);
+      k_lift<<<grid_x / 4, 256, 0, s>>>(ct, bab + b * xct, c->d_pmod, c->d_pc, level, n_ext, c->logn);
       note_launch();
       if (cudaGetLastError() != cudaSuccess) return fhe_fail(FHE_ECUDA, "%s: lift kernel", fn);
       continue;
