@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(256) k_gsum(const __grid_constant__ GsumArgs a
 }
 
 // out[c][i][n] = sum_{g < count} in_g[c][i][n] mod q_i (the giant-step outputs), one thread
-// per coefficient of one limb of both polynomials
+// per four consecutive coefficients of one limb of both polynomials (16-byte accesses)
 struct SumArgs {
   const uint32_t *in[kMaxGiant];  // [2][level][N] each
   uint32_t *out;
@@ -310,16 +310,22 @@ struct SumArgs {
 };
 __global__ void __launch_bounds__(256) k_sum(const __grid_constant__ SumArgs a, const PrimeC *pc, int logn) {
   const size_t N = (size_t)1 << logn;
-  const int per_limb = (int)(N / 256);
+  const int per_limb = (int)(N / 1024);
   const int i = blockIdx.x / per_limb;
-  const size_t n = (size_t)(blockIdx.x % per_limb) * 256 + threadIdx.x;
+  const size_t n = (size_t)(blockIdx.x % per_limb) * 1024 + threadIdx.x * 4;
   const uint32_t q = pc[i].q;
   const size_t poly = (size_t)a.level * N;
 #pragma unroll
   for (int c = 0; c < 2; c++) {
-    uint32_t acc = 0;
-    for (int g = 0; g < a.count; g++) acc = add_mod(acc, __ldg(a.in[g] + c * poly + (size_t)i * N + n), q);
-    a.out[c * poly + (size_t)i * N + n] = acc;
+    uint32_t acc[4] = {0, 0, 0, 0};
+    for (int g = 0; g < a.count; g++) {
+      const uint4 w = __ldg(reinterpret_cast<const uint4 *>(a.in[g] + c * poly + (size_t)i * N + n));
+      acc[0] = add_mod(acc[0], w.x, q);
+      acc[1] = add_mod(acc[1], w.y, q);
+      acc[2] = add_mod(acc[2], w.z, q);
+      acc[3] = add_mod(acc[3], w.w, q);
+    }
+    *reinterpret_cast<uint4 *>(a.out + c * poly + (size_t)i * N + n) = make_uint4(acc[0], acc[1], acc[2], acc[3]);
   }
 }
 
@@ -430,7 +436,7 @@ extern "C" int fhe_linear_transform(fhe_ctx *c, const uint32_t *ct, int level, c
   sa.level = level;
   {
     TraceScope ts(c->tabs, "lt_sum", s);
-    k_sum<<<(unsigned)(level * (N / 256)), 256, 0, s>>>(sa, c->d_pc, c->logn);
+    k_sum<<<(unsigned)(level * (N / 1024)), 256, 0, s>>>(sa, c->d_pc, c->logn);
     note_launch();
     if (cudaGetLastError() != cudaSuccess) return fhe_fail(FHE_ECUDA, "fhe_linear_transform: sum kernel");
   }
